@@ -1,0 +1,1096 @@
+/*
+ * tron_oracle.c -- CPU FP64 oracle of the batched trust-region Newton solve and of the
+ * component ADMM of arXiv 2106.14995.
+ *
+ * TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark are the only users.  The product (CUDA) path never loads this code.
+ *
+ * Plain and slow on purpose: one problem at a time, textbook loops, sequential sums,
+ * compiled with -ffp-contract=off.  Each routine cites the passage it restates.
+ *
+ *   Algorithm 1 (Sec. 3)       outer loop: evaluate, Cauchy point, free set, PCG, back
+ *                              transform, projected search, convergence check
+ *   Figure 2 (Sec. 3)          core operations axpy/copy/dot/gemv/nrm2/scal/trtrs/ccf/ccfs/
+ *                              breakpt/gpstep/trqsol
+ *   Sec. 4.3                   complete (dense) Cholesky of A + alpha*I, left-looking
+ *   Sec. 4.4                   L^T kept explicitly in the upper triangle
+ *   Sec. 5.1                   convergence test ||grad_[l,u] f||_inf <= eps
+ *   Sec. 6.1, eq. exp-branch   branch objective, flows from eqs. pij-qji
+ *   Sec. 6.1                   component ADMM: generator and branch, then bus, then
+ *                              multipliers
+ *   Sec. 4.2 footnote          hs45 variant f = 120 - prod x_i, x_i <= i
+ *
+ * Steps the paper leaves open (acceptance test, radius update, search constants,
+ * Cholesky shift, CG tolerance, ADMM closed forms) follow the readings recorded in the
+ * design notes; their constants are the fields of ot_opts.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+void ot_default_opts(ot_opts* o) {
+  o->gtol = 1e-6;
+  o->max_outer = 500;
+  o->max_trials = 30;
+  o->mu0 = 0.01;
+  o->mu1 = 1.0;
+  o->interpf = 0.1;
+  o->extrapf = 10.0;
+  o->proj_shrink = 0.5;
+  o->eta0 = 1e-4;
+  o->eta1 = 0.25;
+  o->eta2 = 0.75;
+  o->sigma1 = 0.25;
+  o->sigma3 = 4.0;
+  o->delta_max = 1e10;
+  o->delta_min_rel = 1e-12;
+  o->cg_rtol = 0.1;
+  o->shift_frac = 1e-3;
+  o->max_shift = 30;
+  o->pad0 = 0;
+  o->ared_guard = 1e-13;
+}
+
+/* ------------------------------------------------------------ Figure 2 core operations */
+
+static double dot(int n, const double* x, const double* y, ot_counters* c) {
+  double s = 0.0;
+  for (int i = 0; i < n; i++) s += x[i] * y[i];
+  if (c) c->flops += 2.0 * n;
+  return s;
+}
+
+static double nrm2(int n, const double* x, ot_counters* c) {
+  double s = dot(n, x, x, c);
+  if (c) c->flops += 1.0;
+  return sqrt(s);
+}
+
+/* y <- A x, A row-major n x n with leading dimension lda */
+static void gemv(int n, const double* A, int lda, const double* x, double* y, ot_counters* c) {
+  for (int i = 0; i < n; i++) {
+    double s = 0.0;
+    for (int j = 0; j < n; j++) s += A[(size_t)i * lda + j] * x[j];
+    y[i] = s;
+  }
+  if (c) c->flops += 2.0 * n * n;
+}
+
+static double proj1(double v, double lo, double hi) {
+  if (v < lo) return lo;
+  if (v > hi) return hi;
+  return v;
+}
+
+/* gpstep: s <- P_[l,u](x + alpha w) - x */
+static void gpstep(int n, const double* x, double alpha, const double* w, const double* l,
+                   const double* u, double* s, ot_counters* c) {
+  for (int i = 0; i < n; i++) s[i] = proj1(x[i] + alpha * w[i], l[i], u[i]) - x[i];
+  if (c) c->flops += 3.0 * n;
+}
+
+/* breakpt: b_i = (u_i - x_i)/w_i if w_i > 0, (l_i - x_i)/w_i if w_i < 0, over the
+ * variables that can still move in direction w. */
+void ot_breakpt(int n, const double* x, const double* w, const double* l, const double* u,
+                int* nbrpt, double* brptmin, double* brptmax) {
+  int nb = 0;
+  double bmin = 0.0, bmax = 0.0;
+  for (int i = 0; i < n; i++) {
+    double b;
+    if (x[i] < u[i] && w[i] > 0.0) {
+      b = (u[i] - x[i]) / w[i];
+    } else if (x[i] > l[i] && w[i] < 0.0) {
+      b = (l[i] - x[i]) / w[i];
+    } else {
+      continue;
+    }
+    if (nb == 0) {
+      bmin = b;
+      bmax = b;
+    } else {
+      if (b < bmin) bmin = b;
+      if (b > bmax) bmax = b;
+    }
+    nb++;
+  }
+  *nbrpt = nb;
+  *brptmin = bmin;
+  *brptmax = bmax;
+}
+
+/* trqsol: sigma >= 0 with ||x + sigma p||_2 = delta (positive root of the quadratic) */
+static double trqsol_c(int n, const double* x, const double* p, double delta, ot_counters* c) {
+  double ptx = dot(n, p, x, c);
+  double ptp = dot(n, p, p, c);
+  double xtx = dot(n, x, x, c);
+  double dsq = delta * delta;
+  double rad = ptx * ptx + ptp * (dsq - xtx);
+  if (rad < 0.0) rad = 0.0;
+  rad = sqrt(rad);
+  if (c) c->flops += 12.0;
+  if (ptx >= 0.0) return (dsq - xtx) / (ptx + rad);
+  return (rad - ptx) / ptp;
+}
+
+double ot_trqsol(int n, const double* x, const double* p, double delta) {
+  return trqsol_c(n, x, p, delta, NULL);
+}
+
+/* trtrs with L: solve L y = b in place (L lower, row-major m x m), column oriented */
+static void trsv_lower(int m, const double* L, double* b, ot_counters* c) {
+  for (int j = 0; j < m; j++) {
+    b[j] = b[j] / L[(size_t)j * m + j];
+    for (int i = j + 1; i < m; i++) b[i] -= L[(size_t)i * m + j] * b[j];
+  }
+  if (c) c->flops += (double)m * m;
+}
+
+/* trtrs with L^T: solve L^T z = y in place, column oriented over the columns of L^T
+ * (which are the rows of L) */
+static void trsv_upper_t(int m, const double* L, double* z, ot_counters* c) {
+  for (int j = m - 1; j >= 0; j--) {
+    z[j] = z[j] / L[(size_t)j * m + j];
+    for (int i = 0; i < j; i++) z[i] -= L[(size_t)j * m + i] * z[j];
+  }
+  if (c) c->flops += (double)m * m;
+}
+
+/* ccf: left-looking unblocked Cholesky (Sec. 4.3).  On entry the lower triangle of L
+ * holds the matrix; on success it holds the factor and the strict upper triangle holds
+ * L^T (Sec. 4.4).  Returns 0, or j+1 if pivot j is not positive. */
+static int chol_left_c(int m, double* L, ot_counters* c) {
+  for (int j = 0; j < m; j++) {
+    for (int i = j; i < m; i++) {
+      double v = L[(size_t)i * m + j];
+      for (int k = 0; k < j; k++) v -= L[(size_t)i * m + k] * L[(size_t)j * m + k];
+      L[(size_t)i * m + j] = v;
+    }
+    if (c) c->flops += 2.0 * j * (m - j);
+    double piv = L[(size_t)j * m + j];
+    if (!(piv > 0.0)) return j + 1;
+    double d = sqrt(piv);
+    L[(size_t)j * m + j] = d;
+    for (int i = j + 1; i < m; i++) L[(size_t)i * m + j] = L[(size_t)i * m + j] / d;
+    if (c) c->flops += 1.0 + (m - j - 1);
+  }
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < i; j++) L[(size_t)j * m + i] = L[(size_t)i * m + j];
+  return 0;
+}
+
+int ot_chol_left(int m, double* A, int lda) {
+  /* dense helper for tests: factor the lower triangle of a row-major matrix in place */
+  double* L = (double*)malloc(sizeof(double) * (size_t)m * m + 8);
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < m; j++) L[(size_t)i * m + j] = A[(size_t)i * lda + j];
+  int r = chol_left_c(m, L, NULL);
+  if (r == 0)
+    for (int i = 0; i < m; i++)
+      for (int j = 0; j < m; j++) A[(size_t)i * lda + j] = L[(size_t)i * m + j];
+  free(L);
+  return r;
+}
+
+/* ccf + ccfs: factor A + alpha I = L L^T for the first alpha of the shift sequence
+ * alpha_0 = 0 if min A_ii > 0 else beta - min A_ii, alpha <- max(2 alpha, beta), with
+ * beta = shift_frac * max |A_ii| (Sec. 4.3: "for some alpha >= 0"). */
+static int chol_shifted_c(int m, const double* A, double* L, double frac, int max_shift,
+                          double* alpha_out, ot_counters* c) {
+  double maxd = 0.0, mind = A[0];
+  for (int i = 0; i < m; i++) {
+    double a = A[(size_t)i * m + i];
+    if (fabs(a) > maxd) maxd = fabs(a);
+    if (a < mind) mind = a;
+  }
+  double beta = frac * maxd;
+  if (beta == 0.0) beta = frac;
+  double alpha = (mind > 0.0) ? 0.0 : beta - mind;
+  for (int t = 0; t <= max_shift; t++) {
+    if (c) c->chol_calls++;
+    for (int i = 0; i < m; i++)
+      for (int j = 0; j <= i; j++) L[(size_t)i * m + j] = A[(size_t)i * m + j];
+    for (int i = 0; i < m; i++) L[(size_t)i * m + i] = A[(size_t)i * m + i] + alpha;
+    if (c) c->flops += m;
+    if (chol_left_c(m, L, c) == 0) {
+      if (alpha_out) *alpha_out = alpha;
+      return 0;
+    }
+    alpha = 2.0 * alpha;
+    if (alpha < beta) alpha = beta;
+  }
+  return 1;
+}
+
+int ot_chol_shifted(int m, const double* A, double* L, double shift_frac, int max_shift,
+                    double* alpha_out) {
+  return chol_shifted_c(m, A, L, shift_frac, max_shift, alpha_out, NULL);
+}
+
+double ot_pgnorm(int n, const double* x, const double* g, const double* l, const double* u) {
+  /* (grad_[l,u] f)_i = g_i inside, min(g_i,0) at l_i, max(g_i,0) at u_i (Sec. 5.1) */
+  double m = 0.0;
+  for (int i = 0; i < n; i++) {
+    double p = g[i];
+    if (x[i] <= l[i] && p > 0.0) p = 0.0;
+    if (x[i] >= u[i] && p < 0.0) p = 0.0;
+    double a = fabs(p);
+    if (a > m) m = a;
+  }
+  return m;
+}
+
+/* Steihaug-Toint truncated CG on the preconditioned system (Alg. 1 lines 8-9, Sec. 3):
+ * minimise 0.5 s'Ahat s + bhat's with Ahat = L^-1 A L^-T.  The trust region bounds the
+ * step in the original variables, w = L^-T s, by ||w||_2 <= delta (trqsol of Figure 2
+ * measures ||x + sigma w||_2); w is accumulated along the iterations as
+ * w += alpha L^-T p, the L^-T p being the backward solve that Ahat p needs anyway.
+ * Stops after m iterations, at the boundary, on negative curvature, or when the residual
+ * norm drops to rtol*||bhat||.  Returns 0 converged, 1 iteration cap, 2 boundary,
+ * 3 negative curvature; w receives the step L^-T s. */
+static int steihaug_c(int m, const double* A, const double* L, const double* bhat,
+                      double delta, double rtol, double* w, int* iters, ot_counters* c) {
+  double* res = (double*)malloc(sizeof(double) * (size_t)(5 * m + 8));
+  double* p = res + m;
+  double* q = p + m;
+  double* z = q + m;
+  double* wn = z + m;
+  for (int i = 0; i < m; i++) {
+    w[i] = 0.0;
+    res[i] = -bhat[i];
+    p[i] = res[i];
+  }
+  double rr = dot(m, res, res, c);
+  double tol = rtol * sqrt(rr);
+  int info = 1, it = 0;
+  while (it < m) {
+    if (sqrt(rr) <= tol) {
+      info = 0;
+      break;
+    }
+    /* Ahat p = L^-1 (A (L^-T p)) : backward solve, gemv, forward solve (Sec. 4.4) */
+    for (int i = 0; i < m; i++) z[i] = p[i];
+    trsv_upper_t(m, L, z, c);
+    gemv(m, A, m, z, q, c);
+    trsv_lower(m, L, q, c);
+    it++;
+    if (c) c->cg_iters++;
+    double kappa = dot(m, p, q, c);
+    if (kappa <= 0.0) {
+      double sigma = trqsol_c(m, w, z, delta, c);
+      for (int i = 0; i < m; i++) w[i] += sigma * z[i];
+      info = 3;
+      break;
+    }
+    double alpha = rr / kappa;
+    for (int i = 0; i < m; i++) wn[i] = w[i] + alpha * z[i];
+    if (nrm2(m, wn, c) >= delta) {
+      double sigma = trqsol_c(m, w, z, delta, c);
+      for (int i = 0; i < m; i++) w[i] += sigma * z[i];
+      info = 2;
+      break;
+    }
+    for (int i = 0; i < m; i++) {
+      w[i] = wn[i];
+      res[i] -= alpha * q[i];
+    }
+    double rrn = dot(m, res, res, c);
+    double beta = rrn / rr;
+    rr = rrn;
+    for (int i = 0; i < m; i++) p[i] = res[i] + beta * p[i];
+    if (c) c->flops += 6.0 * m + 2.0;
+  }
+  if (iters) *iters = it;
+  free(res);
+  return info;
+}
+
+int ot_steihaug(int m, const double* A, const double* L, const double* bhat, double delta,
+                double rtol, double* w, int* iters) {
+  return steihaug_c(m, A, L, bhat, delta, rtol, w, iters, NULL);
+}
+
+/* ------------------------------------------------------------------------ objectives */
+
+/* Dense quartic family: params = [Q (n x n, row-major) | c (n) | d (n)],
+ * f = 1/2 x'Qx + c'x + sum_i d_i x_i^4. */
+static int eval_dense(int n, const double* P, const double* x, double* f, double* g,
+                      double* H, ot_counters* c) {
+  const double* Q = P;
+  const double* cv = P + (size_t)n * n;
+  const double* d = cv + n;
+  double quad = 0.0, lin = 0.0, quart = 0.0;
+  for (int i = 0; i < n; i++) {
+    double qx = 0.0;
+    for (int j = 0; j < n; j++) qx += Q[(size_t)i * n + j] * x[j];
+    quad += x[i] * qx;
+    lin += cv[i] * x[i];
+    double x2 = x[i] * x[i];
+    quart += d[i] * x2 * x2;
+    if (g) g[i] = qx + cv[i] + 4.0 * d[i] * x2 * x[i];
+  }
+  *f = 0.5 * quad + lin + quart;
+  if (H) {
+    for (int i = 0; i < n; i++)
+      for (int j = 0; j < n; j++) H[(size_t)i * n + j] = Q[(size_t)i * n + j];
+    for (int i = 0; i < n; i++) H[(size_t)i * n + i] += 12.0 * d[i] * x[i] * x[i];
+  }
+  if (c) {
+    c->flops += 2.0 * n * n + 9.0 * n + 2.0;
+    if (g) c->flops += 5.0 * n;
+    if (H) c->flops += 4.0 * n;
+  }
+  return 0;
+}
+
+/* hs45 variant (Sec. 4.2 footnote): f = 120 - prod_i x_i */
+static int eval_hs45(int n, const double* x, double* f, double* g, double* H, ot_counters* c) {
+  double p = 1.0;
+  for (int i = 0; i < n; i++) p *= x[i];
+  *f = 120.0 - p;
+  if (g) {
+    for (int i = 0; i < n; i++) {
+      double q = 1.0;
+      for (int j = 0; j < n; j++)
+        if (j != i) q *= x[j];
+      g[i] = -q;
+    }
+  }
+  if (H) {
+    for (int i = 0; i < n; i++) {
+      for (int j = 0; j < n; j++) {
+        if (i == j) {
+          H[(size_t)i * n + j] = 0.0;
+          continue;
+        }
+        double q = 1.0;
+        for (int k = 0; k < n; k++)
+          if (k != i && k != j) q *= x[k];
+        H[(size_t)i * n + j] = -q;
+      }
+    }
+  }
+  if (c) {
+    c->flops += n + 1.0;
+    if (g) c->flops += (double)n * n;
+    if (H) c->flops += (double)n * n * n;
+  }
+  return 0;
+}
+
+/* Branch record (36 doubles): [0:8] gc_ij bc_ij g_ij b_ij gc_ji bc_ji g_ji b_ji,
+ * [8:16] multipliers, [16:24] targets, [24:32] penalties of the pairs
+ * (p_ij q_ij p_ji q_ji w_i w_j th_i th_j), [32] smax^2, [33] line penalty. */
+
+/* flows of eqs. pij-qji with w_i = v_i^2, w_j = v_j^2, wR = v_i v_j cos(th_i - th_j),
+ * wI = v_i v_j sin(th_i - th_j) (Sec. 6.1) */
+static void branch_pairs(const double* cf, const double* x, double cs, double sn, double* F) {
+  double vi = x[0], vj = x[1];
+  double wi = vi * vi, wj = vj * vj;
+  double wR = vi * vj * cs, wI = vi * vj * sn;
+  F[0] = cf[0] * wi - cf[2] * wR + cf[3] * wI;
+  F[1] = cf[1] * wi - cf[3] * wR - cf[2] * wI;
+  F[2] = cf[4] * wj - cf[6] * wR - cf[7] * wI;
+  F[3] = cf[5] * wj - cf[7] * wR + cf[6] * wI;
+  F[4] = wi;
+  F[5] = wj;
+  F[6] = x[2];
+  F[7] = x[3];
+}
+
+/* eq. exp-branch plus the line-limit penalty (rho_l/2) max(0, p^2 + q^2 - smax^2)^2 for
+ * both directions, with analytic gradient and Hessian */
+static int eval_branch(const double* P, const double* x, double* f, double* g, double* H,
+                       ot_counters* c) {
+  const double* cf = P;
+  const double* lam = P + 8;
+  const double* tg = P + 16;
+  const double* rh = P + 24;
+  double smax2 = P[32], rhol = P[33];
+  double vi = x[0], vj = x[1];
+  double sn = sin(x[2] - x[3]);
+  double cs = cos(x[2] - x[3]);
+  if (c) c->sincos++;
+  double wR = vi * vj * cs, wI = vi * vj * sn;
+  double F[8];
+  branch_pairs(cf, x, cs, sn, F);
+  double val = 0.0;
+  for (int k = 0; k < 8; k++) {
+    double r = F[k] - tg[k];
+    val += lam[k] * r + 0.5 * rh[k] * r * r;
+  }
+  for (int dir = 0; dir < 2; dir++) {
+    double p = F[2 * dir], q = F[2 * dir + 1];
+    double m = p * p + q * q - smax2;
+    if (m > 0.0) val += 0.5 * rhol * m * m;
+  }
+  *f = val;
+  if (c) c->flops += 30.0 + 8 * 5.0 + 2 * 9.0;
+  if (!g && !H) return 0;
+
+  /* first and second derivatives of w_i, w_j, wR, wI in the order (v_i, v_j, th_i, th_j) */
+  double dwi[4] = {2.0 * vi, 0.0, 0.0, 0.0};
+  double dwj[4] = {0.0, 2.0 * vj, 0.0, 0.0};
+  double dwR[4] = {vj * cs, vi * cs, -wI, wI};
+  double dwI[4] = {vj * sn, vi * sn, wR, -wR};
+  double Hwi[16] = {0}, Hwj[16] = {0}, HwR[16] = {0}, HwI[16] = {0};
+  Hwi[0] = 2.0;
+  Hwj[5] = 2.0;
+  /* wR = vi vj cos(ti - tj) */
+  HwR[0 * 4 + 1] = cs;
+  HwR[0 * 4 + 2] = -vj * sn;
+  HwR[0 * 4 + 3] = vj * sn;
+  HwR[1 * 4 + 2] = -vi * sn;
+  HwR[1 * 4 + 3] = vi * sn;
+  HwR[2 * 4 + 2] = -wR;
+  HwR[2 * 4 + 3] = wR;
+  HwR[3 * 4 + 3] = -wR;
+  /* wI = vi vj sin(ti - tj) */
+  HwI[0 * 4 + 1] = sn;
+  HwI[0 * 4 + 2] = vj * cs;
+  HwI[0 * 4 + 3] = -vj * cs;
+  HwI[1 * 4 + 2] = vi * cs;
+  HwI[1 * 4 + 3] = -vi * cs;
+  HwI[2 * 4 + 2] = -wI;
+  HwI[2 * 4 + 3] = wI;
+  HwI[3 * 4 + 3] = -wI;
+  for (int a = 0; a < 4; a++)
+    for (int b = 0; b < a; b++) {
+      HwR[a * 4 + b] = HwR[b * 4 + a];
+      HwI[a * 4 + b] = HwI[b * 4 + a];
+    }
+  /* each pair quantity F_k = ci*w_i + cj*w_j + cR*wR + cI*wI (+ theta for k = 6, 7) */
+  double coefs[8][4] = {
+      {cf[0], 0.0, -cf[2], cf[3]},  {cf[1], 0.0, -cf[3], -cf[2]}, {0.0, cf[4], -cf[6], -cf[7]},
+      {0.0, cf[5], -cf[7], cf[6]},  {1.0, 0.0, 0.0, 0.0},         {0.0, 1.0, 0.0, 0.0},
+      {0.0, 0.0, 0.0, 0.0},         {0.0, 0.0, 0.0, 0.0}};
+  double dF[8][4], HF[8][16];
+  for (int k = 0; k < 8; k++) {
+    for (int a = 0; a < 4; a++)
+      dF[k][a] = coefs[k][0] * dwi[a] + coefs[k][1] * dwj[a] + coefs[k][2] * dwR[a] +
+                 coefs[k][3] * dwI[a];
+    for (int e = 0; e < 16; e++)
+      HF[k][e] = coefs[k][0] * Hwi[e] + coefs[k][1] * Hwj[e] + coefs[k][2] * HwR[e] +
+                 coefs[k][3] * HwI[e];
+  }
+  dF[6][2] = 1.0;
+  dF[7][3] = 1.0;
+  double gg[4] = {0, 0, 0, 0}, HH[16];
+  for (int e = 0; e < 16; e++) HH[e] = 0.0;
+  for (int k = 0; k < 8; k++) {
+    double r = F[k] - tg[k];
+    double t = lam[k] + rh[k] * r;
+    for (int a = 0; a < 4; a++) gg[a] += t * dF[k][a];
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) HH[a * 4 + b] += rh[k] * dF[k][a] * dF[k][b] + t * HF[k][a * 4 + b];
+  }
+  for (int dir = 0; dir < 2; dir++) {
+    int kp = 2 * dir, kq = 2 * dir + 1;
+    double p = F[kp], q = F[kq];
+    double m = p * p + q * q - smax2;
+    if (!(m > 0.0)) continue;
+    double dm[4];
+    for (int a = 0; a < 4; a++) dm[a] = 2.0 * p * dF[kp][a] + 2.0 * q * dF[kq][a];
+    for (int a = 0; a < 4; a++) gg[a] += rhol * m * dm[a];
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) {
+        double d2m = 2.0 * dF[kp][a] * dF[kp][b] + 2.0 * p * HF[kp][a * 4 + b] +
+                     2.0 * dF[kq][a] * dF[kq][b] + 2.0 * q * HF[kq][a * 4 + b];
+        HH[a * 4 + b] += rhol * (dm[a] * dm[b] + m * d2m);
+      }
+  }
+  if (g)
+    for (int a = 0; a < 4; a++) g[a] = gg[a];
+  if (H)
+    for (int e = 0; e < 16; e++) H[e] = HH[e];
+  if (c) c->flops += 420.0;
+  return 0;
+}
+
+static int eval_c(int kind, int n, const double* P, const double* x, double* f, double* g,
+                  double* H, ot_counters* c) {
+  switch (kind) {
+    case OT_OBJ_DENSE: return eval_dense(n, P, x, f, g, H, c);
+    case OT_OBJ_HS45: return eval_hs45(n, x, f, g, H, c);
+    case OT_OBJ_BRANCH:
+      if (n != 4) return -1;
+      return eval_branch(P, x, f, g, H, c);
+    default: return -1;
+  }
+}
+
+int ot_eval(int kind, int n, const double* params, const double* x, double* f, double* g,
+            double* H) {
+  return eval_c(kind, n, params, x, f, g, H, NULL);
+}
+
+static int all_finite(int n, const double* v) {
+  for (int i = 0; i < n; i++)
+    if (!isfinite(v[i])) return 0;
+  return 1;
+}
+
+/* ----------------------------------------------------------------- Algorithm 1 (TRON) */
+
+int ot_tron_solve(int kind, int n, const double* params, const double* l, const double* u,
+                  double* x, double* delta_io, const ot_opts* o, double* f_out, double* pg_out,
+                  int32_t* iters_out, ot_counters* cnt) {
+  ot_counters local;
+  memset(&local, 0, sizeof(local));
+  ot_counters* c = cnt ? cnt : &local;
+  size_t nn = (size_t)n * n;
+  double* W = (double*)malloc(sizeof(double) * (3 * nn + 16 * (size_t)n + 16));
+  int* F = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+  double* H = W;
+  double* A = H + nn;
+  double* L = A + nn;
+  double* g = L + nn;
+  double* y = g + n;
+  double* s = y + n;
+  double* r = s + n;
+  double* w = r + n;
+  double* Hd = w + n;
+  double* d = Hd + n;
+  double* yt = d + n;
+  double* rF = yt + n;
+  double* bh = rF + n;
+  double* sh = bh + n;
+  double* mg = sh + n;
+  int status = OT_MAX_ITER;
+  int k = 0;
+  double f = NAN;
+  double delta = *delta_io;
+
+  for (int i = 0; i < n; i++) {
+    if (!(l[i] <= u[i])) {
+      status = OT_BAD_BOUNDS;
+      goto out_nopg;
+    }
+  }
+  /* Alg. 1 REQUIRE: x0 in [l,u]; project it */
+  for (int i = 0; i < n; i++) x[i] = proj1(x[i], l[i], u[i]);
+  if (eval_c(kind, n, params, x, &f, g, H, c) != 0) {
+    status = OT_NONFINITE;
+    goto out_nopg;
+  }
+  c->f_evals++;
+  c->gh_evals++;
+  if (!isfinite(f) || !all_finite(n, g) || !all_finite((int)nn, H)) {
+    status = OT_NONFINITE;
+    goto out;
+  }
+  if (!(delta > 0.0)) {
+    /* automatic initial radius: ||P[x - g] - x||, or 1 when that is zero */
+    for (int i = 0; i < n; i++) mg[i] = -g[i];
+    gpstep(n, x, 1.0, mg, l, u, s, c);
+    delta = nrm2(n, s, c);
+    if (delta == 0.0) delta = 1.0;
+  }
+  double alpha_c = 1.0;
+
+  for (;;) {
+    /* Alg. 1 lines 1 and 11: convergence at x^k (Sec. 5.1) */
+    double pg = ot_pgnorm(n, x, g, l, u);
+    if (pg <= o->gtol) {
+      status = OT_CONVERGED;
+      break;
+    }
+    if (k >= o->max_outer) {
+      status = OT_MAX_ITER;
+      break;
+    }
+    k++;
+    c->outer++;
+
+    /* ---- Alg. 1 line 4: Cauchy point x_c = P[x - alpha g] with a sufficient-decrease
+     * search on q(s) = g's + 1/2 s'Hs: q(s) <= mu0 g's and ||s|| <= mu1 delta. */
+    for (int i = 0; i < n; i++) mg[i] = -g[i];
+    double alpha = alpha_c;
+    int ok;
+    {
+      gpstep(n, x, alpha, mg, l, u, s, c);
+      gemv(n, H, n, s, Hd, c);
+      double gts = dot(n, g, s, c);
+      double q = gts + 0.5 * dot(n, s, Hd, c);
+      ok = (q <= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta);
+      c->cauchy_trials++;
+    }
+    if (ok) {
+      int nb;
+      double bmin, bmax;
+      ot_breakpt(n, x, mg, l, u, &nb, &bmin, &bmax);
+      c->flops += 2.0 * n;
+      for (int t = 0; t < o->max_trials; t++) {
+        if (!(alpha < bmax)) break;
+        double a2 = alpha * o->extrapf;
+        gpstep(n, x, a2, mg, l, u, s, c);
+        gemv(n, H, n, s, Hd, c);
+        double gts = dot(n, g, s, c);
+        double q = gts + 0.5 * dot(n, s, Hd, c);
+        c->cauchy_trials++;
+        if (!((q <= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta))) break;
+        alpha = a2;
+      }
+    } else {
+      for (int t = 0; t < o->max_trials; t++) {
+        alpha = alpha * o->interpf;
+        gpstep(n, x, alpha, mg, l, u, s, c);
+        gemv(n, H, n, s, Hd, c);
+        double gts = dot(n, g, s, c);
+        double q = gts + 0.5 * dot(n, s, Hd, c);
+        c->cauchy_trials++;
+        if ((q <= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta)) break;
+      }
+    }
+    alpha_c = alpha;
+    for (int i = 0; i < n; i++) y[i] = proj1(x[i] - alpha * g[i], l[i], u[i]);
+    c->flops += 2.0 * n;
+
+    /* ---- Alg. 1 lines 5-10, repeated on the current face: free set, shifted complete
+     * Cholesky, Steihaug PCG, back transform, projected search.  r is the model gradient
+     * g + H (y - x) at the current point y. */
+    for (int i = 0; i < n; i++) s[i] = y[i] - x[i];
+    gemv(n, H, n, s, Hd, c);
+    for (int i = 0; i < n; i++) r[i] = g[i] + Hd[i];
+    c->flops += 2.0 * n;
+    double rF0 = 0.0;
+    for (int pass = 0; pass < n; pass++) {
+      int m = 0;
+      for (int i = 0; i < n; i++)
+        if (l[i] < y[i] && y[i] < u[i]) F[m++] = i;
+      if (m == 0) break;
+      c->subspace_passes++;
+      for (int a = 0; a < m; a++) rF[a] = r[F[a]];
+      if (pass == 0) rF0 = nrm2(m, rF, c);
+      /* A = H_FF (Sec. 5.3 gather) */
+      for (int a = 0; a < m; a++)
+        for (int b = 0; b < m; b++) A[(size_t)a * m + b] = H[(size_t)F[a] * n + F[b]];
+      double shift;
+      if (chol_shifted_c(m, A, L, o->shift_frac, o->max_shift, &shift, c) != 0) {
+        status = OT_CHOL_FAIL;
+        goto out;
+      }
+      /* bhat = L^-1 r_F */
+      for (int a = 0; a < m; a++) bh[a] = rF[a];
+      trsv_lower(m, L, bh, c);
+      int cgit;
+      /* Alg. 1 lines 8-9: sh receives w_F = L^-T s */
+      int info = steihaug_c(m, A, L, bh, delta, o->cg_rtol, sh, &cgit, c);
+      for (int i = 0; i < n; i++) w[i] = 0.0;
+      for (int a = 0; a < m; a++) w[F[a]] = sh[a];
+      /* Alg. 1 line 10: projected search y+ = P[y + beta w], sufficient decrease of the
+       * model: r'd + 1/2 d'Hd <= mu0 r'd with d = y+ - y, beta halved on failure */
+      double beta = 1.0;
+      int found = 0;
+      for (int t = 0; t < o->max_trials; t++) {
+        c->proj_trials++;
+        gpstep(n, y, beta, w, l, u, d, c);
+        for (int i = 0; i < n; i++) yt[i] = proj1(y[i] + beta * w[i], l[i], u[i]);
+        gemv(n, H, n, d, Hd, c);
+        double rtd = dot(n, r, d, c);
+        double dHd = dot(n, d, Hd, c);
+        c->flops += 3.0;
+        if (rtd + 0.5 * dHd <= o->mu0 * rtd) {
+          found = 1;
+          break;
+        }
+        beta = beta * o->proj_shrink;
+      }
+      if (!found) break;
+      int newly_active = 0;
+      for (int a = 0; a < m; a++) {
+        int i = F[a];
+        if (!(l[i] < yt[i] && yt[i] < u[i])) newly_active = 1;
+      }
+      for (int i = 0; i < n; i++) {
+        y[i] = yt[i];
+        r[i] = r[i] + Hd[i];
+      }
+      c->flops += n;
+      for (int a = 0; a < m; a++) rF[a] = r[F[a]];
+      double rFn = nrm2(m, rF, c);
+      if (info == 2 || info == 3 || newly_active || rFn <= o->cg_rtol * rF0) break;
+    }
+
+    /* ---- acceptance and radius update on rho = (f(x) - f(y)) / (-q(y - x)) */
+    for (int i = 0; i < n; i++) s[i] = y[i] - x[i];
+    gemv(n, H, n, s, Hd, c);
+    double qs = dot(n, g, s, c) + 0.5 * dot(n, s, Hd, c);
+    double fy;
+    eval_c(kind, n, params, y, &fy, NULL, NULL, c);
+    c->f_evals++;
+    /* rho = ared / pred, both shifted by the rounding level of f (Conn, Gould and
+     * Toint, Trust-Region Methods, Sec. 17.4.2) so that reductions below the
+     * precision of f do not decide the step */
+    double pred = -qs;
+    double ared = f - fy;
+    double fl = o->ared_guard * (fabs(f) > 1.0 ? fabs(f) : 1.0);
+    double rho = (pred > 0.0 && isfinite(fy)) ? (ared + fl) / (pred + fl) : -INFINITY;
+    double snorm = nrm2(n, s, c);
+    c->flops += 5.0 + n;
+    if (rho > o->eta0) {
+      for (int i = 0; i < n; i++) x[i] = y[i];
+      f = fy;
+      eval_c(kind, n, params, x, &fy, g, H, c);
+      c->gh_evals++;
+      c->accepted++;
+      if (!all_finite(n, g) || !all_finite((int)nn, H)) {
+        status = OT_NONFINITE;
+        break;
+      }
+    }
+    if (rho < o->eta1) {
+      delta = o->sigma1 * (snorm < delta ? snorm : delta);
+    } else if (rho > o->eta2 && snorm >= 0.99 * delta) {
+      delta = o->sigma3 * delta;
+      if (delta > o->delta_max) delta = o->delta_max;
+    }
+    if (delta < o->delta_min_rel * (1.0 + nrm2(n, x, c))) {
+      status = OT_TR_TOO_SMALL;
+      break;
+    }
+  }
+out:
+  if (pg_out) *pg_out = isfinite(f) ? ot_pgnorm(n, x, g, l, u) : NAN;
+  goto done;
+out_nopg:
+  if (pg_out) *pg_out = NAN;
+done:
+  if (f_out) *f_out = f;
+  if (iters_out) *iters_out = k;
+  *delta_io = delta;
+  free(W);
+  free(F);
+  return status;
+}
+
+/* ------------------------------------------------------------------ batch, threaded */
+
+typedef struct batch_job {
+  int kind;
+  const int32_t* n;
+  const int64_t* poff;
+  const int64_t* voff;
+  const double *params, *l, *u;
+  double *x, *delta, *f, *pg;
+  int32_t *iters, *status;
+  const ot_opts* o;
+  int64_t begin, end;
+  ot_counters cnt;
+} batch_job;
+
+static void* batch_worker(void* arg) {
+  batch_job* j = (batch_job*)arg;
+  memset(&j->cnt, 0, sizeof(j->cnt));
+  for (int64_t p = j->begin; p < j->end; p++) {
+    int64_t vo = j->voff[p];
+    j->status[p] = ot_tron_solve(j->kind, j->n[p], j->params + j->poff[p], j->l + vo, j->u + vo,
+                                 j->x + vo, j->delta + p, j->o, j->f + p, j->pg + p,
+                                 j->iters + p, &j->cnt);
+  }
+  return NULL;
+}
+
+static void add_counters(ot_counters* a, const ot_counters* b) {
+  a->outer += b->outer;
+  a->accepted += b->accepted;
+  a->f_evals += b->f_evals;
+  a->gh_evals += b->gh_evals;
+  a->cauchy_trials += b->cauchy_trials;
+  a->proj_trials += b->proj_trials;
+  a->cg_iters += b->cg_iters;
+  a->chol_calls += b->chol_calls;
+  a->subspace_passes += b->subspace_passes;
+  a->sincos += b->sincos;
+  a->flops += b->flops;
+}
+
+void ot_tron_batch(int kind, int64_t nprob, const int32_t* n, const int64_t* poff,
+                   const int64_t* voff, const double* params, const double* l, const double* u,
+                   double* x, double* delta, const ot_opts* o, double* f, double* pg,
+                   int32_t* iters, int32_t* status, int nthreads, ot_counters* total) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  if ((int64_t)nthreads > nprob) nthreads = (int)(nprob > 0 ? nprob : 1);
+  batch_job* jobs = (batch_job*)calloc((size_t)nthreads, sizeof(batch_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+  int64_t chunk = (nprob + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; t++) {
+    batch_job* j = &jobs[t];
+    j->kind = kind;
+    j->n = n;
+    j->poff = poff;
+    j->voff = voff;
+    j->params = params;
+    j->l = l;
+    j->u = u;
+    j->x = x;
+    j->delta = delta;
+    j->f = f;
+    j->pg = pg;
+    j->iters = iters;
+    j->status = status;
+    j->o = o;
+    j->begin = t * chunk < nprob ? t * chunk : nprob;
+    j->end = (t + 1) * chunk < nprob ? (t + 1) * chunk : nprob;
+  }
+  if (nthreads == 1) {
+    batch_worker(&jobs[0]);
+  } else {
+    for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, batch_worker, &jobs[t]);
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+  }
+  if (total)
+    for (int t = 0; t < nthreads; t++) add_counters(total, &jobs[t].cnt);
+  free(jobs);
+  free(th);
+}
+
+/* --------------------------------------------------------------- component ADMM (6.1) */
+
+void ot_admm_branch_record(const ot_net* net, const ot_state* st, int k, double* rec) {
+  int i = net->br_from[k], j = net->br_to[k];
+  for (int a = 0; a < 8; a++) rec[a] = net->br_coef[8 * (size_t)k + a];
+  for (int a = 0; a < 8; a++) rec[8 + a] = st->br_lam[8 * (size_t)k + a];
+  for (int a = 0; a < 4; a++) rec[16 + a] = st->br_tilde[4 * (size_t)k + a];
+  rec[20] = st->bus_w[i];
+  rec[21] = st->bus_w[j];
+  rec[22] = st->bus_th[i];
+  rec[23] = st->bus_th[j];
+  for (int a = 0; a < 8; a++) rec[24 + a] = net->rho;
+  rec[32] = net->br_smax2[k];
+  rec[33] = net->rho_line;
+  rec[34] = 0.0;
+  rec[35] = 0.0;
+}
+
+static void branch_values_at(const double* cf, const double* x, double* val) {
+  double sn = sin(x[2] - x[3]);
+  double cs = cos(x[2] - x[3]);
+  branch_pairs(cf, x, cs, sn, val);
+}
+
+void ot_admm_init(const ot_net* net, ot_state* st) {
+  for (int k = 0; k < net->nbranch; k++) {
+    double* x = st->br_x + 4 * (size_t)k;
+    x[0] = 1.0;
+    x[1] = 1.0;
+    x[2] = 0.0;
+    x[3] = 0.0;
+    st->br_delta[k] = 1.0;
+    double* val = st->br_val + 8 * (size_t)k;
+    branch_values_at(net->br_coef + 8 * (size_t)k, x, val);
+    for (int a = 0; a < 8; a++) st->br_lam[8 * (size_t)k + a] = 0.0;
+    for (int a = 0; a < 4; a++) st->br_tilde[4 * (size_t)k + a] = val[a];
+  }
+  for (int b = 0; b < net->nbus; b++) {
+    st->bus_w[b] = 1.0;
+    st->bus_th[b] = 0.0;
+  }
+  for (int g = 0; g < net->ngen; g++) {
+    st->gen_pq[2 * g] = 0.5 * (net->gen_pmin[g] + net->gen_pmax[g]);
+    st->gen_pq[2 * g + 1] = 0.5 * (net->gen_qmin[g] + net->gen_qmax[g]);
+    st->gen_lam[2 * g] = 0.0;
+    st->gen_lam[2 * g + 1] = 0.0;
+    st->gen_tilde[2 * g] = st->gen_pq[2 * g];
+    st->gen_tilde[2 * g + 1] = st->gen_pq[2 * g + 1];
+  }
+}
+
+/* value of the bus-side copy of pair a of branch k */
+static double pair_tilde(const ot_net* net, const ot_state* st, int k, int a) {
+  switch (a) {
+    case 4: return st->bus_w[net->br_from[k]];
+    case 5: return st->bus_w[net->br_to[k]];
+    case 6: return st->bus_th[net->br_from[k]];
+    case 7: return st->bus_th[net->br_to[k]];
+    default: return st->br_tilde[4 * (size_t)k + a];
+  }
+}
+
+void ot_admm_run(const ot_net* net, ot_state* st, const ot_opts* o, int niters, int nthreads,
+                 double* hist_primal, double* hist_dual, int64_t* status_counts,
+                 ot_counters* total) {
+  int nb = net->nbus, nl = net->nbranch, ng = net->ngen;
+  double rho = net->rho;
+  /* bus incidence, ends and generators listed in increasing id (end id = 2 k + side) */
+  int* ep = (int*)calloc((size_t)nb + 1, sizeof(int));
+  int* gp = (int*)calloc((size_t)nb + 1, sizeof(int));
+  int* el = (int*)malloc(sizeof(int) * (size_t)(2 * nl + 1));
+  int* gl = (int*)malloc(sizeof(int) * (size_t)(ng + 1));
+  for (int k = 0; k < nl; k++) {
+    ep[net->br_from[k] + 1]++;
+    ep[net->br_to[k] + 1]++;
+  }
+  for (int g = 0; g < ng; g++) gp[net->gen_bus[g] + 1]++;
+  for (int b = 0; b < nb; b++) {
+    ep[b + 1] += ep[b];
+    gp[b + 1] += gp[b];
+  }
+  {
+    int* fill = (int*)calloc((size_t)nb + 1, sizeof(int));
+    for (int e = 0; e < 2 * nl; e++) {
+      int k = e / 2;
+      int bus = (e % 2 == 0) ? net->br_from[k] : net->br_to[k];
+      el[ep[bus] + fill[bus]++] = e;
+    }
+    memset(fill, 0, sizeof(int) * ((size_t)nb + 1));
+    for (int g = 0; g < ng; g++) {
+      int bus = net->gen_bus[g];
+      gl[gp[bus] + fill[bus]++] = g;
+    }
+    free(fill);
+  }
+  int32_t* n4 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
+  int64_t* poff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl + 1));
+  int64_t* voff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl + 1));
+  double* recs = (double*)malloc(sizeof(double) * 36 * (size_t)(nl + 1));
+  double* bl = (double*)malloc(sizeof(double) * 4 * (size_t)(nl + 1));
+  double* bu = (double*)malloc(sizeof(double) * 4 * (size_t)(nl + 1));
+  double* bf = (double*)malloc(sizeof(double) * (size_t)(nl + 1));
+  double* bpg = (double*)malloc(sizeof(double) * (size_t)(nl + 1));
+  int32_t* bit = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
+  int32_t* bst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
+  double* tprev = (double*)malloc(sizeof(double) * (size_t)(8 * nl + 2 * ng + 1));
+  const double twopi = 6.283185307179586476925286766559;
+  for (int k = 0; k < nl; k++) {
+    n4[k] = 4;
+    poff[k] = 36 * (int64_t)k;
+    voff[k] = 4 * (int64_t)k;
+    bl[4 * k + 0] = net->vmin;
+    bl[4 * k + 1] = net->vmin;
+    bl[4 * k + 2] = -twopi;
+    bl[4 * k + 3] = -twopi;
+    bu[4 * k + 0] = net->vmax;
+    bu[4 * k + 1] = net->vmax;
+    bu[4 * k + 2] = twopi;
+    bu[4 * k + 3] = twopi;
+  }
+
+  for (int it = 0; it < niters; it++) {
+    /* generator update: closed-form minimiser of the box-clipped scalar quadratics */
+    for (int g = 0; g < ng; g++) {
+      double pt = st->gen_tilde[2 * g], qt = st->gen_tilde[2 * g + 1];
+      double lp = st->gen_lam[2 * g], lq = st->gen_lam[2 * g + 1];
+      double p = (rho * pt - lp - net->gen_c1[g]) / (2.0 * net->gen_c2[g] + rho);
+      double q = qt - lq / rho;
+      st->gen_pq[2 * g] = proj1(p, net->gen_pmin[g], net->gen_pmax[g]);
+      st->gen_pq[2 * g + 1] = proj1(q, net->gen_qmin[g], net->gen_qmax[g]);
+    }
+    /* branch update: TRON on eq. exp-branch, warm started from the previous x, delta */
+    for (int k = 0; k < nl; k++) ot_admm_branch_record(net, st, k, recs + 36 * (size_t)k);
+    ot_tron_batch(OT_OBJ_BRANCH, nl, n4, poff, voff, recs, bl, bu, st->br_x, st->br_delta, o,
+                  bf, bpg, bit, bst, nthreads, total);
+    if (status_counts)
+      for (int k = 0; k < nl; k++)
+        if (bst[k] >= 0 && bst[k] < 6) status_counts[bst[k]]++;
+    for (int k = 0; k < nl; k++)
+      branch_values_at(net->br_coef + 8 * (size_t)k, st->br_x + 4 * (size_t)k,
+                       st->br_val + 8 * (size_t)k);
+    /* remember the bus-side copies for the dual residual */
+    for (int g = 0; g < ng; g++) {
+      tprev[2 * g] = st->gen_tilde[2 * g];
+      tprev[2 * g + 1] = st->gen_tilde[2 * g + 1];
+    }
+    for (int k = 0; k < nl; k++)
+      for (int a = 0; a < 8; a++) tprev[2 * ng + 8 * k + a] = pair_tilde(net, st, k, a);
+    /* bus update: minimise sum rho/2 (xt - a)^2 with a = x + lambda/rho subject to the
+     * bus balance equations (eqs. PowerBalanceReal/Reactive); x = a - D^-1 A' mu with
+     * (A D^-1 A') mu = A a - (p_d, q_d) */
+    for (int b = 0; b < nb; b++) {
+      double rhsP = -net->bus_pd[b], rhsQ = -net->bus_qd[b];
+      double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
+      for (int t = gp[b]; t < gp[b + 1]; t++) {
+        int g = gl[t];
+        rhsP += st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho;
+        rhsQ += st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho;
+        sinv += 1.0 / rho;
+      }
+      for (int t = ep[b]; t < ep[b + 1]; t++) {
+        int e = el[t], k = e / 2, side = e % 2;
+        const double* val = st->br_val + 8 * (size_t)k;
+        const double* lam = st->br_lam + 8 * (size_t)k;
+        int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
+        rhsP -= val[kp] + lam[kp] / rho;
+        rhsQ -= val[kq] + lam[kq] / rho;
+        sinv += 1.0 / rho;
+        Dw += rho;
+        awn += rho * (val[kw] + lam[kw] / rho);
+        athn += rho * (val[kt] + lam[kt] / rho);
+      }
+      double gsh = net->bus_gsh[b], bsh = net->bus_bsh[b];
+      double aw = Dw > 0.0 ? awn / Dw : st->bus_w[b];
+      rhsP -= gsh * aw;
+      rhsQ += bsh * aw;
+      double M11 = sinv, M22 = sinv, M12 = 0.0;
+      if (Dw > 0.0) {
+        M11 += gsh * gsh / Dw;
+        M22 += bsh * bsh / Dw;
+        M12 = -gsh * bsh / Dw;
+      }
+      double det = M11 * M22 - M12 * M12;
+      double mu1 = 0.0, mu2 = 0.0;
+      if (det != 0.0) {
+        mu1 = (M22 * rhsP - M12 * rhsQ) / det;
+        mu2 = (M11 * rhsQ - M12 * rhsP) / det;
+      }
+      for (int t = gp[b]; t < gp[b + 1]; t++) {
+        int g = gl[t];
+        st->gen_tilde[2 * g] = st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho - mu1 / rho;
+        st->gen_tilde[2 * g + 1] =
+            st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho - mu2 / rho;
+      }
+      for (int t = ep[b]; t < ep[b + 1]; t++) {
+        int e = el[t], k = e / 2, side = e % 2;
+        const double* val = st->br_val + 8 * (size_t)k;
+        const double* lam = st->br_lam + 8 * (size_t)k;
+        int kp = side ? 2 : 0, kq = kp + 1;
+        st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho + mu1 / rho;
+        st->br_tilde[4 * (size_t)k + kq] = val[kq] + lam[kq] / rho + mu2 / rho;
+      }
+      if (Dw > 0.0) {
+        st->bus_w[b] = aw - (-gsh * mu1 + bsh * mu2) / Dw;
+        st->bus_th[b] = athn / Dw;
+      }
+    }
+    /* multipliers lambda += rho (x - xt); primal ||x - xt||, dual rho ||xt - xt_prev|| */
+    double pr2 = 0.0, du2 = 0.0;
+    for (int g = 0; g < ng; g++) {
+      for (int a = 0; a < 2; a++) {
+        double xv = st->gen_pq[2 * g + a], xt = st->gen_tilde[2 * g + a];
+        st->gen_lam[2 * g + a] += rho * (xv - xt);
+        pr2 += (xv - xt) * (xv - xt);
+        double dd = xt - tprev[2 * g + a];
+        du2 += dd * dd;
+      }
+    }
+    for (int k = 0; k < nl; k++) {
+      for (int a = 0; a < 8; a++) {
+        double xv = st->br_val[8 * (size_t)k + a], xt = pair_tilde(net, st, k, a);
+        st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);
+        pr2 += (xv - xt) * (xv - xt);
+        double dd = xt - tprev[2 * ng + 8 * k + a];
+        du2 += dd * dd;
+      }
+    }
+    if (hist_primal) hist_primal[it] = sqrt(pr2);
+    if (hist_dual) hist_dual[it] = rho * sqrt(du2);
+  }
+  free(ep);
+  free(gp);
+  free(el);
+  free(gl);
+  free(n4);
+  free(poff);
+  free(voff);
+  free(recs);
+  free(bl);
+  free(bu);
+  free(bf);
+  free(bpg);
+  free(bit);
+  free(bst);
+  free(tprev);
+}

@@ -1,0 +1,593 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU).
+
+Each test checks the oracle against something the paper or the mathematics fixes: the
+hs45 solution printed in Sec. 4.2, closed-form minimisers, brute force on tiny
+problems, library factorizations and roots, finite differences and autograd of the
+branch objective, complex power flow, and KKT conditions of the ADMM closed forms.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_14995_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ core operations
+
+def test_chol_matches_numpy():
+    rng = np.random.default_rng(0)
+    for m in (1, 2, 5, 17, 32):
+        G = rng.standard_normal((m, m))
+        A = G @ G.T + m * np.eye(m)
+        L = oracle.chol(A)
+        np.testing.assert_allclose(L, np.linalg.cholesky(A), rtol=1e-12, atol=1e-12)
+
+
+def test_chol_rejects_indefinite():
+    A = np.diag([1.0, -1.0, 2.0])
+    assert oracle.chol(A) is None
+
+
+def test_chol_shifted_factor_and_mirror():
+    rng = np.random.default_rng(1)
+    for m in (3, 8, 20):
+        G = rng.standard_normal((m, m))
+        U, _ = np.linalg.qr(G)
+        ev = rng.uniform(0.5, 2.0, m)
+        ev[0] = -1.0  # indefinite by construction
+        A = (U * ev) @ U.T
+        A = 0.5 * (A + A.T)
+        L, alpha = oracle.chol_shifted(A)
+        assert L is not None and alpha > 0
+        Lo = np.tril(L)
+        np.testing.assert_allclose(Lo @ Lo.T, A + alpha * np.eye(m), rtol=1e-10, atol=1e-10)
+        # L^T mirrored into the strict upper triangle (Sec. 4.4)
+        np.testing.assert_array_equal(np.triu(L, 1), np.triu(Lo.T, 1))
+        # positive definite input: no shift
+        Apd = G @ G.T + np.eye(m)
+        L2, a2 = oracle.chol_shifted(Apd)
+        assert a2 == 0.0
+        np.testing.assert_allclose(np.tril(L2), np.linalg.cholesky(Apd), rtol=1e-12, atol=1e-12)
+
+
+def test_chol_shift_sequence_first_success():
+    # the shift is the first of alpha0 = beta - min A_ii, then max(2 alpha, beta) ...
+    # that makes A + alpha I positive definite; check minimality within the sequence
+    A = np.array([[1.0, 2.0], [2.0, 1.0]])  # eigenvalues -1, 3
+    L, alpha = oracle.chol_shifted(A, shift_frac=1e-3)
+    beta = 1e-3 * 1.0
+    seq = [0.0]  # min diag > 0 -> alpha0 = 0
+    while len(seq) < 40:
+        seq.append(max(2 * seq[-1], beta))
+    ok = [a for a in seq if np.all(np.linalg.eigvalsh(A + a * np.eye(2)) > 0)]
+    assert alpha == ok[0]
+
+
+def test_trqsol_is_positive_root():
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        n = rng.integers(1, 10)
+        x = rng.standard_normal(n) * 0.1
+        p = rng.standard_normal(n)
+        delta = np.linalg.norm(x) + rng.uniform(0.1, 2.0)
+        sig = oracle.trqsol(x, p, delta)
+        roots = np.roots([p @ p, 2 * x @ p, x @ x - delta * delta])
+        pos = max(r.real for r in roots)
+        assert sig >= 0
+        assert abs(sig - pos) <= 1e-12 * max(1.0, abs(pos))
+        assert abs(np.linalg.norm(x + sig * p) - delta) <= 1e-12 * delta
+
+
+def test_pgnorm_definition_cases():
+    l = np.array([0.0, 0.0, 0.0, 0.0, -1.0])
+    u = np.array([1.0, 1.0, 1.0, 1.0, -1.0])
+    x = np.array([0.0, 0.0, 1.0, 0.5, -1.0])
+    g = np.array([2.0, -3.0, -4.0, 0.7, 9.0])
+    # at lower with g > 0 -> 0; at lower with g < 0 -> |g|; at upper with g < 0 -> 0;
+    # interior -> |g|; fixed variable (l = u) -> 0
+    assert oracle.pgnorm(x, g, l, u) == 3.0
+    g2 = np.array([2.0, 0.0, -4.0, -0.7, -9.0])
+    assert oracle.pgnorm(x, g2, l, u) == 0.7
+
+
+def test_breakpt_cases():
+    x = np.array([0.0, 0.5, 1.0, 0.2])
+    l = np.zeros(4)
+    u = np.ones(4)
+    w = np.array([1.0, -0.25, 1.0, 0.0])
+    nb, bmin, bmax = oracle.breakpt(x, w, l, u)
+    # var0: (1-0)/1 = 1; var1: (0-0.5)/-0.25 = 2; var2 at u moving up: blocked; var3: w=0
+    assert nb == 2 and bmin == 1.0 and bmax == 2.0
+
+
+def test_steihaug_one_iteration_on_pd():
+    # Sec. 4.3: with the complete factor of a positive definite A, Ahat = I and CG
+    # finishes in one iteration; the step is the Newton step -A^-1 r when inside.
+    rng = np.random.default_rng(3)
+    m = 12
+    G = rng.standard_normal((m, m))
+    A = G @ G.T + np.eye(m)
+    L, alpha = oracle.chol_shifted(A)
+    assert alpha == 0.0
+    r = rng.standard_normal(m)
+    bhat = np.linalg.solve(np.tril(L), r)
+    w, info, it = oracle.steihaug(A, L, bhat, delta=1e6)
+    assert it == 1 and info in (0, 1)
+    np.testing.assert_allclose(w, -np.linalg.solve(A, r), rtol=1e-9, atol=1e-12)
+    # boundary: the step is the Newton direction cut at ||w|| = delta
+    newton = -np.linalg.solve(A, r)
+    delta = 0.3 * np.linalg.norm(newton)
+    w2, info2, _ = oracle.steihaug(A, L, bhat, delta=delta)
+    assert info2 == 2
+    assert abs(np.linalg.norm(w2) - delta) < 1e-12 * delta
+    np.testing.assert_allclose(w2 / np.linalg.norm(w2), newton / np.linalg.norm(newton),
+                               rtol=1e-9, atol=1e-12)
+
+
+def test_steihaug_negative_curvature_goes_to_boundary():
+    A = np.diag([2.0, -1.0])
+    L = np.diag([1.0, 1.0])  # identity preconditioner
+    L_full = L.copy()
+    bhat = np.array([0.0, 1.0])  # gradient only along the negative-curvature direction
+    w, info, _ = oracle.steihaug(A, L_full, bhat, delta=0.5)
+    assert info == 3
+    np.testing.assert_allclose(w, [0.0, -0.5], atol=1e-15)
+
+
+# ------------------------------------------------------------------------- objectives
+
+def test_dense_eval_closed_form():
+    rng = np.random.default_rng(4)
+    n = 7
+    rec, _, _, _ = synth.dense_records(rng, 1, n)
+    Q = rec[0, :n * n].reshape(n, n)
+    c = rec[0, n * n:n * n + n]
+    d = rec[0, n * n + n:]
+    x = rng.standard_normal(n)
+    f, g, H = oracle.eval_obj(oracle.OBJ_DENSE, rec[0], x)
+    assert abs(f - (0.5 * x @ Q @ x + c @ x + d @ x ** 4)) < 1e-12 * max(1, abs(f))
+    np.testing.assert_allclose(g, Q @ x + c + 4 * d * x ** 3, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(H, Q + np.diag(12 * d * x ** 2), rtol=1e-12, atol=1e-12)
+
+
+def _branch_points(rng, k):
+    out = []
+    for _ in range(k):
+        out.append(np.array([rng.uniform(0.9, 1.1), rng.uniform(0.9, 1.1),
+                             rng.uniform(-1, 1), rng.uniform(-1, 1)]))
+    return out
+
+
+def test_branch_gradient_hessian_finite_differences():
+    d = synth.branch_batch(16, seed_index=5)
+    rng = np.random.default_rng(5)
+    for p in range(16):
+        rec = d["params"][p].copy()
+        if p % 2:
+            rec[32] = 0.01  # force the line-limit term active
+        for x in _branch_points(rng, 3):
+            f, g, H = oracle.eval_obj(oracle.OBJ_BRANCH, rec, x)
+            h = 1e-6
+            gfd = np.zeros(4)
+            Hfd = np.zeros((4, 4))
+            for i in range(4):
+                e = np.zeros(4)
+                e[i] = h
+                fp, gp, _ = oracle.eval_obj(oracle.OBJ_BRANCH, rec, x + e)
+                fm, gm, _ = oracle.eval_obj(oracle.OBJ_BRANCH, rec, x - e)
+                gfd[i] = (fp - fm) / (2 * h)
+                Hfd[:, i] = (gp - gm) / (2 * h)
+            scale = max(1.0, np.abs(g).max())
+            assert np.abs(g - gfd).max() < 1e-6 * scale
+            hs = max(1.0, np.abs(H).max())
+            assert np.abs(H - Hfd).max() < 1e-6 * hs
+            np.testing.assert_allclose(H, H.T, rtol=0, atol=1e-9 * hs)
+
+
+def test_branch_matches_torch_autograd():
+    torch = pytest.importorskip("torch")
+    d = synth.branch_batch(8, seed_index=6)
+    rng = np.random.default_rng(6)
+
+    def f_torch(rec, x):
+        cf, lam, tg, rh = rec[0:8], rec[8:16], rec[16:24], rec[24:32]
+        vi, vj, ti, tj = x[0], x[1], x[2], x[3]
+        wi, wj = vi * vi, vj * vj
+        wR = vi * vj * torch.cos(ti - tj)
+        wI = vi * vj * torch.sin(ti - tj)
+        # eqs. pij-qji written out independently of the oracle's coefficient table
+        pij = cf[0] * wi - cf[2] * wR + cf[3] * wI
+        qij = cf[1] * wi - cf[3] * wR - cf[2] * wI
+        pji = cf[4] * wj - cf[6] * wR - cf[7] * wI
+        qji = cf[5] * wj - cf[7] * wR + cf[6] * wI
+        F = torch.stack([pij, qij, pji, qji, wi, wj, ti, tj])
+        r = F - tg
+        val = (lam * r + 0.5 * rh * r * r).sum()
+        for a, b in ((pij, qij), (pji, qji)):
+            m = a * a + b * b - rec[32]
+            val = val + 0.5 * rec[33] * torch.clamp(m, min=0.0) ** 2
+        return val
+
+    for p in range(8):
+        rec = d["params"][p].copy()
+        if p % 2:
+            rec[32] = 0.02
+        rt = torch.tensor(rec, dtype=torch.float64)
+        for x in _branch_points(rng, 3):
+            xt = torch.tensor(x, dtype=torch.float64, requires_grad=True)
+            ft = f_torch(rt, xt)
+            gt, = torch.autograd.grad(ft, xt, create_graph=True)
+            Ht = torch.stack([torch.autograd.grad(gt[i], xt, retain_graph=True)[0]
+                              for i in range(4)])
+            f, g, H = oracle.eval_obj(oracle.OBJ_BRANCH, rec, x)
+            assert abs(f - ft.item()) <= 1e-10 * max(1, abs(f))
+            np.testing.assert_allclose(g, gt.detach().numpy(), rtol=1e-10, atol=1e-9)
+            np.testing.assert_allclose(H, Ht.detach().numpy(), rtol=1e-10, atol=1e-8)
+
+
+def test_branch_flows_match_complex_power():
+    """p_ij + j q_ij = V_i conj(I_ij) for the pi-model with series y and charging bc."""
+    rng = np.random.default_rng(7)
+    r, x, bc, _ = synth.random_lines(rng, 20)
+    coef = synth.line_coefficients(r, x, bc)
+    for k in range(20):
+        rec = np.zeros(36)
+        rec[0:8] = coef[k]
+        rec[24:32] = 1.0  # unit penalties, zero multipliers and targets:
+        # f = 1/2 sum F_k^2 ; recover the flows through f at a point and its gradient
+        vi, vj = rng.uniform(0.9, 1.1, 2)
+        ti, tj = rng.uniform(-0.5, 0.5, 2)
+        Vi = vi * np.exp(1j * ti)
+        Vj = vj * np.exp(1j * tj)
+        y = 1.0 / (r[k] + 1j * x[k])
+        Iij = y * (Vi - Vj) + 1j * bc[k] / 2 * Vi
+        Iji = y * (Vj - Vi) + 1j * bc[k] / 2 * Vj
+        Sij = Vi * np.conj(Iij)
+        Sji = Vj * np.conj(Iji)
+        want = np.array([Sij.real, Sij.imag, Sji.real, Sji.imag])
+        # f = 1/2 (sum flows^2 + vi^4 + vj^4 + ti^2 + tj^2); subtract the voltage terms
+        f, _, _ = oracle.eval_obj(oracle.OBJ_BRANCH, rec, np.array([vi, vj, ti, tj]))
+        rest = 0.5 * (vi ** 4 + vj ** 4 + ti ** 2 + tj ** 2)
+        assert abs((f - rest) - 0.5 * (want ** 2).sum()) < 1e-12
+        # and flow by flow: a unit multiplier on one pair returns that flow
+        for a in range(4):
+            rec2 = np.zeros(36)
+            rec2[0:8] = coef[k]
+            rec2[8 + a] = 1.0
+            f2, _, _ = oracle.eval_obj(oracle.OBJ_BRANCH, rec2, np.array([vi, vj, ti, tj]))
+            assert abs(f2 - want[a]) < 1e-12
+
+
+# ---------------------------------------------------------------------------- TRON
+
+def _solve(kind, rec, l, u, x0, **over):
+    return oracle.tron_solve(kind, rec, l, u, x0, 1.0, oracle.default_opts(**over))
+
+
+def test_hs45_printed_solution():
+    """Sec. 4.2 footnote: the solution of f = 120 - prod x_i, x_i <= i is x*_i = i."""
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "hs45.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 7
+    for row in rows:
+        n = int(row[0])
+        fstar = float(row[1])
+        xstar = np.array([float(v) for v in row[2:]])
+        d = synth.hs45_batch(1, n)
+        r = oracle.tron_solve(oracle.OBJ_HS45, None, d["l"][0], d["u"][0], d["x0"][0], 1.0)
+        assert r["status"] == oracle.CONVERGED
+        np.testing.assert_allclose(r["x"], xstar, rtol=0, atol=1e-9)
+        assert abs(r["f"] - fstar) <= 1e-9 * max(1, abs(fstar))
+        assert fstar == 120 - math.factorial(n)
+
+
+def test_separable_quadratic_closed_form():
+    rng = np.random.default_rng(8)
+    for n in (1, 3, 8, 32):
+        for _ in range(5):
+            rec, l, u, x0 = synth.dense_records(rng, 1, n, quartic=0.0, diag_only=True)
+            q = np.diag(rec[0, :n * n].reshape(n, n))
+            c = rec[0, n * n:n * n + n]
+            want = np.clip(-c / q, l[0], u[0])
+            r = _solve(oracle.OBJ_DENSE, rec[0], l[0], u[0], x0[0])
+            assert r["status"] == oracle.CONVERGED and r["pg"] <= 1e-6
+            np.testing.assert_allclose(r["x"], want, rtol=0, atol=1e-6)
+            fwant = 0.5 * (q * want * want).sum() + c @ want
+            assert abs(r["f"] - fwant) <= 1e-8 * max(1.0, abs(fwant))
+
+
+def _bisect(fun, a, b, it=200):
+    fa = fun(a)
+    for _ in range(it):
+        m = 0.5 * (a + b)
+        fm = fun(m)
+        if (fm > 0) == (fa > 0):
+            a, fa = m, fm
+        else:
+            b = m
+    return 0.5 * (a + b)
+
+
+def test_separable_quartic_closed_form():
+    rng = np.random.default_rng(9)
+    for n in (2, 5, 16):
+        rec, l, u, x0 = synth.dense_records(rng, 1, n, quartic=0.1, diag_only=True)
+        q = np.diag(rec[0, :n * n].reshape(n, n))
+        c = rec[0, n * n:n * n + n]
+        want = np.zeros(n)
+        for i in range(n):
+            # unique real root of q x + c + 0.4 x^3 (strictly increasing), then clip
+            root = _bisect(lambda t: q[i] * t + c[i] + 0.4 * t ** 3, -100.0, 100.0)
+            want[i] = min(max(root, l[0, i]), u[0, i])
+        r = _solve(oracle.OBJ_DENSE, rec[0], l[0], u[0], x0[0])
+        assert r["status"] == oracle.CONVERGED
+        np.testing.assert_allclose(r["x"], want, rtol=0, atol=1e-6)
+
+
+def test_dense_convex_vs_lbfgsb():
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    d = synth.dense_batch(12, 32, seed_index=1)
+    for p in range(12):
+        rec = d["params"][p]
+        n = 32
+        Q = rec[:n * n].reshape(n, n)
+        c = rec[n * n:n * n + n]
+        dd = rec[n * n + n:]
+
+        def fg(x):
+            return (0.5 * x @ Q @ x + c @ x + dd @ x ** 4, Q @ x + c + 4 * dd * x ** 3)
+
+        res = scipy_opt.minimize(fg, d["x0"][p], jac=True, method="L-BFGS-B",
+                                 bounds=list(zip(d["l"][p], d["u"][p])),
+                                 options=dict(gtol=1e-12, ftol=1e-15, maxiter=10000))
+        r = _solve(oracle.OBJ_DENSE, rec, d["l"][p], d["u"][p], d["x0"][p])
+        assert r["status"] == oracle.CONVERGED
+        np.testing.assert_allclose(r["x"], res.x, rtol=0, atol=1e-6)
+        assert abs(r["f"] - res.fun) <= 1e-8 * max(1.0, abs(res.fun))
+
+
+def test_two_variable_bruteforce_grid():
+    """Nonconvex 2-variable problems: the oracle's answer is a local minimiser on the
+    box (no lower value in a grid neighbourhood) and the global one when the grid's
+    best point lies in its basin (checked from that start)."""
+    rng = np.random.default_rng(10)
+    ng = 2001
+    for trial in range(6):
+        A = rng.standard_normal((2, 2))
+        Q = 0.5 * (A + A.T) * 4.0  # indefinite in general
+        c = rng.normal(0, 2, 2)
+        dq = np.array([0.3, 0.3])
+        rec = np.concatenate([Q.ravel(), c, dq])
+        l = np.array([-2.0, -1.5])
+        u = np.array([1.5, 2.0])
+        X, Y = np.meshgrid(np.linspace(l[0], u[0], ng), np.linspace(l[1], u[1], ng),
+                           indexing="ij")
+        F = (0.5 * (Q[0, 0] * X * X + 2 * Q[0, 1] * X * Y + Q[1, 1] * Y * Y) + c[0] * X
+             + c[1] * Y + dq[0] * X ** 4 + dq[1] * Y ** 4)
+        i, j = np.unravel_index(np.argmin(F), F.shape)
+        xg = np.array([X[i, j], Y[i, j]])
+        r = _solve(oracle.OBJ_DENSE, rec, l, u, xg)
+        assert r["status"] == oracle.CONVERGED
+        h = (u - l) / (ng - 1)
+        assert np.all(np.abs(r["x"] - xg) <= 1.01 * h)
+        assert r["f"] <= F[i, j] + 1e-12
+        # from the centre: a KKT point that no grid point near it improves on
+        r2 = _solve(oracle.OBJ_DENSE, rec, l, u, np.zeros(2))
+        assert r2["status"] == oracle.CONVERGED
+        ii = int(round((r2["x"][0] - l[0]) / h[0]))
+        jj = int(round((r2["x"][1] - l[1]) / h[1]))
+        win = F[max(ii - 5, 0):ii + 6, max(jj - 5, 0):jj + 6]
+        assert r2["f"] <= win.min() + 1e-9
+
+
+def test_kkt_on_dense_workload_sample():
+    d = synth.dense_batch(64, 32, seed_index=1)
+    r = oracle.tron_batch(oracle.OBJ_DENSE, d["params"], d["l"], d["u"], d["x0"],
+                          d["delta0"])
+    assert np.all(r["status"] == oracle.CONVERGED)
+    n = 32
+    for p in range(64):
+        rec = d["params"][p]
+        Q = rec[:n * n].reshape(n, n)
+        x = r["x"][p]
+        g = Q @ x + rec[n * n:n * n + n] + 4 * rec[n * n + n:] * x ** 3
+        pg = g.copy()
+        pg[(x <= d["l"][p]) & (g > 0)] = 0
+        pg[(x >= d["u"][p]) & (g < 0)] = 0
+        assert np.abs(pg).max() <= 1e-6
+        assert np.all(x >= d["l"][p]) and np.all(x <= d["u"][p])
+
+
+def test_branch_workload_kkt():
+    d = synth.branch_batch(256, seed_index=0)
+    r = oracle.tron_batch(oracle.OBJ_BRANCH, d["params"], d["l"], d["u"], d["x0"],
+                          d["delta0"])
+    assert np.all(r["status"] == oracle.CONVERGED)
+    for p in range(0, 256, 7):
+        x = r["x"][p]
+        # gradient by central differences, independent of the oracle's derivative code
+        g = np.zeros(4)
+        for i in range(4):
+            e = np.zeros(4)
+            e[i] = 1e-7
+            fp, _, _ = oracle.eval_obj(oracle.OBJ_BRANCH, d["params"][p], x + e)
+            fm, _, _ = oracle.eval_obj(oracle.OBJ_BRANCH, d["params"][p], x - e)
+            g[i] = (fp - fm) / 2e-7
+        pg = g.copy()
+        pg[(x <= d["l"][p]) & (g > 0)] = 0
+        pg[(x >= d["u"][p]) & (g < 0)] = 0
+        # central differences with h = 1e-7 are accurate to about 1e-6 relative to |g|
+        assert np.abs(pg).max() <= 1e-6 + 1e-6 * max(1.0, np.abs(g).max())
+
+
+def test_status_codes_for_bad_input():
+    n = 3
+    rec, l, u, x0 = synth.dense_records(np.random.default_rng(11), 1, n)
+    lb = l[0].copy()
+    lb[1] = u[0][1] + 1.0
+    r = _solve(oracle.OBJ_DENSE, rec[0], lb, u[0], x0[0])
+    assert r["status"] == oracle.BAD_BOUNDS and r["iters"] == 0
+    rec2 = rec[0].copy()
+    rec2[n * n] = np.nan
+    r = _solve(oracle.OBJ_DENSE, rec2, l[0], u[0], x0[0])
+    assert r["status"] == oracle.NONFINITE
+    r = _solve(oracle.OBJ_DENSE, rec[0], l[0], u[0], x0[0], max_outer=1, gtol=1e-300)
+    assert r["status"] == oracle.MAX_ITER and r["iters"] == 1
+
+
+def test_converged_start_takes_no_iteration():
+    n = 4
+    Q = np.eye(n)
+    rec = np.concatenate([Q.ravel(), np.zeros(n), np.zeros(n)])
+    r = _solve(oracle.OBJ_DENSE, rec, -np.ones(n), np.ones(n), np.zeros(n))
+    assert r["status"] == oracle.CONVERGED and r["iters"] == 0
+
+
+# ---------------------------------------------------------------------------- ADMM
+
+def _small_net(nbus=12, seed=3):
+    return synth.network(nbus, nchord=max(1, nbus // 4), ngen=max(1, nbus // 3),
+                         rng=np.random.default_rng(seed))
+
+
+def test_admm_generator_update_is_scalar_qp_minimiser():
+    net = _small_net()
+    A = oracle.Admm(net)
+    A.run(3)
+    pre = {k: v.copy() for k, v in A.arrays.items()}
+    A.run(1)
+    rho = 400.0
+    for g in range(len(net["gen_bus"])):
+        pt, qt = pre["gen_tilde"][g]
+        lp, lq = pre["gen_lam"][g]
+        c2, c1 = net["gen_c2"][g], net["gen_c1"][g]
+        # brute force on a fine grid of the box, then compare
+        pg = np.linspace(net["gen_pmin"][g], net["gen_pmax"][g], 200001)
+        fp = c2 * pg * pg + c1 * pg + lp * (pg - pt) + 0.5 * rho * (pg - pt) ** 2
+        qg = np.linspace(net["gen_qmin"][g], net["gen_qmax"][g], 200001)
+        fq = lq * (qg - qt) + 0.5 * rho * (qg - qt) ** 2
+        hp = pg[1] - pg[0]
+        hq = qg[1] - qg[0]
+        assert abs(A.arrays["gen_pq"][g, 0] - pg[np.argmin(fp)]) <= hp
+        assert abs(A.arrays["gen_pq"][g, 1] - qg[np.argmin(fq)]) <= hq
+
+
+def _ends(net):
+    nb = net["nbus"]
+    ends = [[] for _ in range(nb)]
+    for k, (i, j) in enumerate(zip(net["br_from"], net["br_to"])):
+        ends[i].append((k, 0))
+        ends[j].append((k, 1))
+    gens = [[] for _ in range(nb)]
+    for g, b in enumerate(net["gen_bus"]):
+        gens[b].append(g)
+    return ends, gens
+
+
+def test_admm_bus_update_kkt_and_multipliers():
+    net = _small_net(15, seed=4)
+    A = oracle.Admm(net)
+    A.run(2)
+    pre = {k: v.copy() for k, v in A.arrays.items()}
+    hp, hd = A.run(1)
+    st = A.arrays
+    rho = 400.0
+    ends, gens = _ends(net)
+    for b in range(net["nbus"]):
+        # balance: sum_g pt_g - sum_e pt_e = p_d (no shunts)
+        sp = sum(st["gen_tilde"][g, 0] for g in gens[b]) - sum(
+            st["br_tilde"][k, 2 * s] for k, s in ends[b])
+        sq = sum(st["gen_tilde"][g, 1] for g in gens[b]) - sum(
+            st["br_tilde"][k, 2 * s + 1] for k, s in ends[b])
+        assert abs(sp - net["bus_pd"][b]) < 1e-12 * max(1, abs(sp))
+        assert abs(sq - net["bus_qd"][b]) < 1e-12 * max(1, abs(sq))
+        # stationarity: rho (xt - a) equal to -mu on generator copies and +mu on flows
+        mus = []
+        for g in gens[b]:
+            a = st["gen_pq"][g, 0] + pre["gen_lam"][g, 0] / rho
+            mus.append(-rho * (st["gen_tilde"][g, 0] - a))
+        for k, s in ends[b]:
+            a = st["br_val"][k, 2 * s] + pre["br_lam"][k, 2 * s] / rho
+            mus.append(rho * (st["br_tilde"][k, 2 * s] - a))
+        assert max(mus) - min(mus) < 1e-9 * max(1, max(abs(m) for m in mus))
+        # voltage / angle copies: the mean of x + lambda/rho over incident ends
+        if ends[b]:
+            aw = np.mean([st["br_val"][k, 4 + s] + pre["br_lam"][k, 4 + s] / rho
+                          for k, s in ends[b]])
+            at = np.mean([st["br_val"][k, 6 + s] + pre["br_lam"][k, 6 + s] / rho
+                          for k, s in ends[b]])
+            assert abs(st["bus_w"][b] - aw) < 1e-12
+            assert abs(st["bus_th"][b] - at) < 1e-12
+    # multiplier update and residuals recomputed from the state
+    xs, xt, xp = [], [], []
+    for g in range(len(net["gen_bus"])):
+        for a in range(2):
+            xs.append(st["gen_pq"][g, a])
+            xt.append(st["gen_tilde"][g, a])
+            xp.append(pre["gen_tilde"][g, a])
+            np.testing.assert_allclose(
+                st["gen_lam"][g, a],
+                pre["gen_lam"][g, a] + rho * (st["gen_pq"][g, a] - st["gen_tilde"][g, a]),
+                rtol=1e-12, atol=1e-9)
+    for k, (i, j) in enumerate(zip(net["br_from"], net["br_to"])):
+        tild = [st["br_tilde"][k, 0], st["br_tilde"][k, 1], st["br_tilde"][k, 2],
+                st["br_tilde"][k, 3], st["bus_w"][i], st["bus_w"][j], st["bus_th"][i],
+                st["bus_th"][j]]
+        prev = [pre["br_tilde"][k, 0], pre["br_tilde"][k, 1], pre["br_tilde"][k, 2],
+                pre["br_tilde"][k, 3], pre["bus_w"][i], pre["bus_w"][j], pre["bus_th"][i],
+                pre["bus_th"][j]]
+        for a in range(8):
+            xs.append(st["br_val"][k, a])
+            xt.append(tild[a])
+            xp.append(prev[a])
+            np.testing.assert_allclose(
+                st["br_lam"][k, a], pre["br_lam"][k, a] + rho * (st["br_val"][k, a] - tild[a]),
+                rtol=1e-12, atol=1e-9)
+    xs, xt, xp = map(np.asarray, (xs, xt, xp))
+    assert abs(hp[0] - np.linalg.norm(xs - xt)) <= 1e-12 * max(1, hp[0])
+    assert abs(hd[0] - rho * np.linalg.norm(xt - xp)) <= 1e-12 * max(1, hd[0])
+
+
+def test_admm_branch_values_are_tron_solutions():
+    net = _small_net(10, seed=5)
+    A = oracle.Admm(net)
+    A.run(2)
+    recs = [A.branch_record(k) for k in range(len(net["br_from"]))]
+    x_before = A.arrays["br_x"].copy()
+    d_before = A.arrays["br_delta"].copy()
+    # re-solve the records the next iteration will see, independently, and compare
+    A.run(1)
+    for k, rec in enumerate(recs[:5]):
+        r = oracle.tron_solve(oracle.OBJ_BRANCH, rec, [0.9, 0.9, -2 * np.pi, -2 * np.pi],
+                              [1.1, 1.1, 2 * np.pi, 2 * np.pi], x_before[k], d_before[k])
+        np.testing.assert_array_equal(r["x"], A.arrays["br_x"][k])
+
+
+def test_admm_residuals_decay_on_convex_case():
+    """Zero line charging, lightly loaded, small network: the residuals fall by orders
+    of magnitude over the iterations."""
+    net = _small_net(6, seed=6)
+    hp, hd = oracle.Admm(net).run(300)
+    assert hp[-1] < 1e-2 * hp[:5].max()
+    assert hd[-1] < 1e-2 * hd[:5].max()
+    assert np.all(np.isfinite(hp)) and np.all(np.isfinite(hd))
+
+
+def test_admm_two_bus_by_hand():
+    """Radial 2-bus case: after the bus update the flows balance the loads exactly:
+    bus 0 holds the generator, bus 1 only a load, so pt_ji = -p_d1 and qt_ji = -q_d1."""
+    net = synth.network(2, nchord=0, ngen=1, rng=np.random.default_rng(7))
+    net["gen_bus"] = np.array([0], dtype=np.int32)
+    net["br_from"] = np.array([0], dtype=np.int32)
+    net["br_to"] = np.array([1], dtype=np.int32)
+    A = oracle.Admm(net)
+    A.run(5)
+    st = A.arrays
+    assert abs(st["br_tilde"][0, 2] + net["bus_pd"][1]) < 1e-12
+    assert abs(st["br_tilde"][0, 3] + net["bus_qd"][1]) < 1e-12
+    assert abs(st["gen_tilde"][0, 0] - st["br_tilde"][0, 0] - net["bus_pd"][0]) < 1e-12
