@@ -1,0 +1,329 @@
+"""Benchmark: batched TRON subproblems/s at a 1e-6 projected-gradient tolerance.
+
+Workload (the configuration the headline metric is quoted on): 10,000 dense problems,
+n = 32, f = 1/2 x'Qx + c'x + 0.1 sum x^4, Q = U diag(lam) U' with U Haar and lam
+log-uniform in [1, 1e3], c ~ N(0, 4^2), l ~ U[-2, -0.5], u ~ U[0.5, 2], x0 = 0, FP64.
+One step = one batched solve of the whole batch from x0 (one kernel launch).
+
+Launch:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+         (N > 1 under torch.distributed.run: each rank solves its own batch; weak scaling)
+
+Timed region: K steps bracketed by a barrier and device synchronisation; device time
+from CUDA events on the launch stream; max over ranks.  Inputs larger than L2: each
+step reads its own copy of the batch (rotating buffers, total > 2 x L2).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TRON subproblems/s & ADMM iters/s at 1e-6 proj-grad; serving p50/p99 vs plain"
+UNIT = "subproblems/s"
+B_DEFAULT = 10000
+N_VARS = 32
+L2_BYTES = 129 * 2 ** 20
+FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--batch", type=int, default=B_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    """The oracle (plain C, FP64) on this host's cores, same workload, sampled steps."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2106_14995_gb300 import synth
+    cores = os.cpu_count() or 1
+    sample = min(args.batch, 2000)
+    d = synth.dense_batch(args.batch, N_VARS, seed_index=1)
+    sub = {k: (v[:sample] if isinstance(v, np.ndarray) and v.ndim and v.shape[0] == args.batch
+               else v) for k, v in d.items()}
+
+    def step():
+        return oracle.tron_batch(2, sub["params"], sub["l"], sub["u"], sub["x0"],
+                                 sub["delta0"], nthreads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = step()
+    dt = time.perf_counter() - t0
+    assert (r["status"] == 0).all()
+    value = sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"dense quartic TRON, n=32, {args.batch} problems "
+                               f"(first {sample} per step)", "global_batch": args.batch},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} of the {args.batch} problems per step, "
+                                   f"{args.steps} steps, {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- cpu baseline
+def cpu_baseline(d, budget_s=12.0):
+    """Oracle on the host cores over the whole batch, repeated for ~budget_s; also
+    returns the oracle-counted algorithmic flops per problem on these inputs."""
+    import oracle
+    cores = os.cpu_count() or 1
+    B = d["x0"].shape[0]
+    t0 = time.perf_counter()
+    reps, flops = 0, 0.0
+    while True:
+        r = oracle.tron_batch(2, d["params"], d["l"], d["u"], d["x0"], d["delta0"],
+                              nthreads=cores)
+        reps += 1
+        flops = r["counters"]["flops"]
+        if time.perf_counter() - t0 >= budget_s or reps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return ({"value": B * reps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"the full {B}-problem batch solved {reps} time(s) on {cores} threads"},
+            flops / B, r)
+
+
+# -------------------------------------------------------------------- main arm
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2106_14995_gb300 import _build, native, synth
+    from paper_2106_14995_gb300.tron import TronBatch, options
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    _build.build()
+    native.load()
+
+    # weak scaling: every rank solves its own batch of the same distribution
+    d = synth.dense_batch(args.batch, N_VARS, seed_index=1)
+    B = args.batch
+    stream = torch.cuda.Stream(device=dev)
+
+    def t(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    params, lo, hi = t(d["params"]), t(d["l"]), t(d["u"])
+    x0, d0 = t(d["x0"]), t(d["delta0"])
+    bytes_in = (params.numel() + lo.numel() + hi.numel() + x0.numel() + d0.numel()) * 8
+    nbuf = max(2, int(np.ceil(2 * L2_BYTES / bytes_in)) + 1)
+    bufs = [dict(p=params.clone(), l=lo.clone(), u=hi.clone()) for _ in range(nbuf)]
+    xs = [x0.clone() for _ in range(args.warmup + args.steps)]
+    ds = [d0.clone() for _ in range(args.warmup + args.steps)]
+    out = dict(f=torch.empty(B, dtype=torch.float64, device=dev),
+               pg=torch.empty(B, dtype=torch.float64, device=dev),
+               iters=torch.empty(B, dtype=torch.int32, device=dev),
+               status=torch.empty(B, dtype=torch.int32, device=dev))
+    tb = TronBatch(2, B, n=N_VARS, opts=options(), stream=stream)
+
+    def step(i):
+        b = bufs[i % nbuf]
+        tb.solve(b["p"], b["l"], b["u"], xs[i], ds[i], stream=stream, **out)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            step(args.warmup + k)
+            ev[k][1].record(stream)
+            launches += tb.last_launches
+        t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    st = out["status"].cpu().numpy()
+    pgv = out["pg"].cpu().numpy()
+    ok = bool((st == 0).all() and (pgv <= 1e-6).all())
+    if world > 1:
+        tm = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        total_ms = float(tm.item())
+    value = world * B * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers (pinned), every step:
+    # H2D of the batch, the solve, D2H of x, f, pg, iters, status
+    host = {k: torch.as_tensor(np.ascontiguousarray(d[k]), dtype=torch.float64).pin_memory()
+            for k in ("params", "l", "u", "x0", "delta0")}
+    hres = dict(x=torch.empty(B, N_VARS, dtype=torch.float64).pin_memory(),
+                f=torch.empty(B, dtype=torch.float64).pin_memory(),
+                pg=torch.empty(B, dtype=torch.float64).pin_memory(),
+                iters=torch.empty(B, dtype=torch.int32).pin_memory(),
+                status=torch.empty(B, dtype=torch.int32).pin_memory())
+    dbuf = dict(params=torch.empty_like(params), l=torch.empty_like(lo),
+                u=torch.empty_like(hi), x0=torch.empty_like(x0), delta0=torch.empty_like(d0))
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in hres.values())
+
+    def e2e_step():
+        for k in dbuf:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        tb.solve(dbuf["params"], dbuf["l"], dbuf["u"], dbuf["x0"], dbuf["delta0"],
+                 stream=stream, **out)
+        hres["x"].copy_(dbuf["x0"], non_blocking=True)
+        for k in ("f", "pg", "iters", "status"):
+            hres[k].copy_(out[k], non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tm = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tm.item())
+    e2e_value = world * B * args.steps / (e2e_ms * 1e-3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded; stands in for the paper's branch batches)",
+        "config": {"workload": f"batched TRON, dense quartic, n={N_VARS}, {B} problems per GPU",
+                   "global_batch": world * B, "n": N_VARS, "gtol": 1e-6,
+                   "parallelism": f"replicas x{world} (independent problems per GPU)",
+                   "l2": f"inputs larger than L2: {nbuf} rotating copies of the batch"},
+        "all_converged": ok,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, flops_per_problem, _ = cpu_baseline(d)
+        achieved = flops_per_problem * B / (float(np.median(launch_ms)) * 1e-3) / 1e9
+        line["roofline"] = {
+            "bound": "alu", "kernel": "k_tron_plain<DenseObj<32,32>,32,32>",
+            "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+            "flops_per_launch": flops_per_problem * B,
+            "launch_ms_median": float(np.median(launch_ms)),
+            "note": "FP64 CUDA-core pipe; peak from 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tb.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * tron.h -- C ABI of the GB300 batched trust-region Newton solver (libexatron_gb300.so).
+ *
+ * Solves many small bound-constrained problems  min f(x)  s.t.  l <= x <= u  (eq. prob,
+ * Sec. 1) with the trust-region Newton method of Algorithm 1 (Sec. 3): Cauchy point,
+ * free-set identification, a complete Cholesky preconditioner with diagonal shift
+ * (Sec. 4.3), Steihaug PCG on the free variables, back transform and projected search,
+ * stopping when the projected-gradient max-norm is below gtol (Sec. 5.1).  Every step
+ * runs on the GPU (Sec. 3: no host/device traffic during a solve); one launch solves a
+ * whole batch, one problem per thread group (Sec. 4.1, Sec. 4.2).
+ *
+ * Conventions
+ *  - Pointers named d_* are DEVICE pointers owned by the caller.  The library owns only
+ *    its own workspace, allocated in *_create and released in *_destroy; no call made
+ *    after *_create allocates device memory.
+ *  - All doubles are IEEE binary64.  Arrays are C-contiguous.
+ *  - Calls enqueue work on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ *    return without synchronising unless stated otherwise.
+ *  - Errors are returned as tron_err_t; tron_last_error() gives a thread-local message.
+ *    Nothing throws across this ABI.  A problem that fails numerically is NOT a call
+ *    error: its code goes to d_status (tron_status_t).
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef EXATRON_GB300_TRON_H
+#define EXATRON_GB300_TRON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tron_err {
+  TRON_OK = 0,
+  TRON_EINVAL = 1,        /* bad argument (null pointer, size, kind, option)          */
+  TRON_ENOMEM = 2,        /* workspace allocation failed in *_create                 */
+  TRON_ECUDA = 3,         /* a CUDA runtime call failed (message in tron_last_error)  */
+  TRON_EUNSUPPORTED = 4   /* valid request this build does not implement (e.g. size)  */
+} tron_err_t;
+
+/* Objective families and the packed per-problem parameter record of each.
+ *
+ * TRON_OBJ_ACOPF_BRANCH (n = 4, x = (v_i, v_j, theta_i, theta_j)): the branch
+ *   subproblem of the component ADMM, eq. exp-branch (Sec. 6.1) with the flows of
+ *   eqs. pij-qji, w_i = v_i^2, w_j = v_j^2, wR = v_i v_j cos(theta_i - theta_j),
+ *   wI = v_i v_j sin(theta_i - theta_j), plus the line-limit penalty
+ *   (rho_l / 2) max(0, p^2 + q^2 - smax^2)^2 for both directions.
+ *   Record of 36 doubles:
+ *     [0:8]   gc_ij bc_ij g_ij b_ij gc_ji bc_ji g_ji b_ji
+ *     [8:16]  multipliers of the pairs (p_ij q_ij p_ji q_ji w_i w_j theta_i theta_j)
+ *     [16:24] targets (bus-side copies) of the same pairs
+ *     [24:32] penalties rho of the same pairs
+ *     [32]    smax^2        [33] rho_l        [34:36] unused
+ * TRON_OBJ_DENSE_QUARTIC (any n <= 32): f = 1/2 x'Qx + c'x + sum_i d_i x_i^4.
+ *   Record of n*n + 2n doubles: Q (row-major, symmetric), c, d.
+ * TRON_OBJ_HS45 (n <= 8): the hs45 variant of Sec. 4.2, f = 120 - prod_i x_i.
+ *   No record (d_params may be NULL); bounds are the caller's.
+ */
+typedef enum tron_obj {
+  TRON_OBJ_ACOPF_BRANCH = 1,
+  TRON_OBJ_DENSE_QUARTIC = 2,
+  TRON_OBJ_HS45 = 3
+} tron_obj_t;
+
+/* Per-problem outcome written to d_status. */
+typedef enum tron_status {
+  TRON_CONVERGED = 0,     /* ||grad_[l,u] f(x)||_inf <= gtol                           */
+  TRON_MAX_ITER = 1,      /* max_outer iterations without convergence                  */
+  TRON_TR_TOO_SMALL = 2,  /* radius fell below delta_min_rel * (1 + ||x||)             */
+  TRON_CHOL_FAIL = 3,     /* no shift of the sequence made H_FF + alpha I factorizable */
+  TRON_NONFINITE = 4,     /* f, gradient or Hessian not finite at an accepted point    */
+  TRON_BAD_BOUNDS = 5     /* some l_i > u_i (or NaN); x is left as given               */
+} tron_status_t;
+
+/* How a batch is scheduled on the GPU. */
+typedef enum tron_schedule {
+  TRON_SCHED_PLAIN = 0,       /* one launch, one thread group per problem (Sec. 4.1)   */
+  TRON_SCHED_PERSISTENT = 1   /* one launch of resident groups that pull problems from
+                                 a device work counter until the batch is exhausted    */
+} tron_schedule_t;
+
+/* Solver constants.  The paper fixes none of the search and radius constants; the
+ * defaults are the readings recorded in the design notes. */
+typedef struct tron_options {
+  double gtol;            /* 1e-6   projected-gradient max-norm tolerance (Sec. 5.1)     */
+  int32_t max_outer;      /* 500    outer iterations                                     */
+  int32_t max_trials;     /* 30     trials in each Cauchy and projected search           */
+  double mu0;             /* 0.01   sufficient-decrease constant                         */
+  double mu1;             /* 1.0    Cauchy step bound ||s|| <= mu1 * delta               */
+  double interpf;         /* 0.1    Cauchy interpolation factor                          */
+  double extrapf;         /* 10.0   Cauchy extrapolation factor                          */
+  double proj_shrink;     /* 0.5    projected-search step factor                         */
+  double eta0;            /* 1e-4   accept when rho > eta0                               */
+  double eta1;            /* 0.25   shrink when rho < eta1                               */
+  double eta2;            /* 0.75   expand when rho > eta2 and the step reached 0.99 delta */
+  double sigma1;          /* 0.25   shrink factor, delta = sigma1 * min(||s||, delta)    */
+  double sigma3;          /* 4.0    expansion factor                                     */
+  double delta_max;       /* 1e10   radius cap                                           */
+  double delta_min_rel;   /* 1e-12  TR_TOO_SMALL threshold, times (1 + ||x||)            */
+  double cg_rtol;         /* 0.1    CG stops at ||residual|| <= cg_rtol * ||bhat||       */
+  double shift_frac;      /* 1e-3   Cholesky shift base, times max |A_ii|                */
+  int32_t max_shift;      /* 30     shift retries before TRON_CHOL_FAIL                  */
+  int32_t group;          /* 0      threads per problem: 0 = library's table, or
+                                    1, 2, 4, 8, 16, 32 (must divide the size class)     */
+  double ared_guard;      /* 1e-13  rounding guard of the reduction ratio,
+                                    rho = (ared + e) / (pred + e), e = ared_guard*max(1,|f|) */
+  int32_t schedule;       /* TRON_SCHED_PLAIN                                            */
+  int32_t warps_per_block;/* 0      CTA size in warps (0 = library's choice)             */
+  int32_t reserved[8];    /* must be zero                                                */
+} tron_options_t;
+
+typedef struct tron_batch tron_batch_t;
+
+/* Fill *opt with the defaults above.  Returns TRON_EINVAL if opt is NULL. */
+tron_err_t tron_options_default(tron_options_t* opt);
+
+/* Create a batch handle for nprob problems of one objective family.
+ *   n_host:     host array [nprob] of per-problem sizes, or NULL when all problems have
+ *               n_uniform variables.  With n_host, records and vectors of consecutive
+ *               problems are concatenated (problem p starts after problems 0..p-1).
+ *   opt:        NULL selects the defaults; copied into the handle.
+ *   stream:     stream for the workspace uploads made here (the call synchronises it).
+ * Allocates the handle's device workspace (size tables and work counters); fails with
+ * TRON_EUNSUPPORTED for sizes outside the family's range and TRON_ENOMEM when the
+ * allocation fails. */
+tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
+                             const int32_t* n_host, int32_t n_uniform,
+                             const tron_options_t* opt, void* stream);
+
+/* Replace the options of a handle (e.g. the schedule or the group size). */
+tron_err_t tron_batch_set_options(tron_batch_t* b, const tron_options_t* opt);
+
+/* Solve the batch.  Device arrays (caller-owned):
+ *   d_params  packed records of the objective family (see tron_obj_t)
+ *   d_lower, d_upper   bounds, [sum n]
+ *   d_x       in: x0 (projected onto [l,u] first), out: final iterate, [sum n]
+ *   d_delta   in: initial radius (<= 0 selects ||P[x0 - g0] - x0||, or 1), out: final
+ *             radius, [nprob]
+ *   d_f, d_pgnorm   out: objective and projected-gradient max-norm at x, [nprob]
+ *   d_iters   out: outer iterations taken, [nprob]
+ *   d_status  out: tron_status_t, [nprob]
+ * Enqueues one launch (or one per size class for mixed sizes with the plain schedule)
+ * on `stream`. */
+tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const double* d_lower,
+                            const double* d_upper, double* d_x, double* d_delta,
+                            double* d_f, double* d_pgnorm, int32_t* d_iters,
+                            int32_t* d_status, void* stream);
+
+/* Number of GPU kernel launches the last tron_batch_solve on this handle enqueued. */
+int32_t tron_batch_last_launches(const tron_batch_t* b);
+
+/* Release the handle and its workspace (NULL is ignored).  Synchronises nothing; the
+ * caller must not destroy a handle whose solve is still running on the GPU. */
+void tron_batch_destroy(tron_batch_t* b);
+
+/* Message of the last error raised on this host thread ("" if none). */
+const char* tron_last_error(void);
+
+/* Library version string. */
+const char* tron_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXATRON_GB300_TRON_H */

@@ -1,0 +1,77 @@
+// tron_common.cuh -- thread-group primitives shared by the TRON device code.
+//
+// A problem is solved by a group of G lanes of one warp (G = 1, 2, 4, 8, 16, 32).
+// Lane t of the group owns the variables i = r*G + t, r = 0..N/G-1 ("slots"), so every
+// vector of a problem lives in registers spread over the group (data-level parallelism,
+// Sec. 5.2).  Reductions use register shuffles inside the group with a butterfly, which
+// leaves the result in every lane and needs no broadcast step (Sec. 5.1, Figure 4).
+//
+// FP64 on this GPU: a warp-wide FP64 instruction costs the same issue slot whether one
+// lane or all 32 are active, so the mapping keeps lanes busy: G = 1 (one problem per
+// lane) for the 4-variable branch problems, G = 32 (one variable per lane) for n = 32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace xt {
+
+template <int G>
+struct Grp {
+  static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "group size");
+  int lane;       // lane in the warp
+  int t;          // rank in the group
+  unsigned mask;  // lanes of this group
+
+  __device__ __forceinline__ Grp() {
+    lane = threadIdx.x & 31;
+    t = lane & (G - 1);
+    mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  }
+  __device__ __forceinline__ void sync() const {
+    if (G > 1) __syncwarp(mask);
+  }
+  __device__ __forceinline__ double sum(double v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+  }
+  __device__ __forceinline__ double max(double v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+  }
+  __device__ __forceinline__ double min(double v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+  }
+  // ballot restricted to the group, bit k = rank k
+  __device__ __forceinline__ unsigned ballot(bool p) const {
+    if (G == 1) return p ? 1u : 0u;
+    unsigned b = __ballot_sync(mask, p) & mask;
+    return b >> (lane & ~(G - 1));
+  }
+  __device__ __forceinline__ bool any(bool p) const { return ballot(p) != 0u; }
+  __device__ __forceinline__ double bcast(double v, int src) const {
+    if (G == 1) return v;
+    return __shfl_sync(mask, v, src, G);
+  }
+  __device__ __forceinline__ int bcast(int v, int src) const {
+    if (G == 1) return v;
+    return __shfl_sync(mask, v, src, G);
+  }
+};
+
+// View of one problem's slice of shared memory.  With G = 1 the 32 problems of a warp
+// are interleaved element by element (element k of lane q at k*32 + q), so a warp-wide
+// access is always conflict free; with G >= 2 each problem owns a contiguous slice.
+template <int G, typename T = double>
+struct SV {
+  T* p;
+  __device__ __forceinline__ T& operator[](int k) const { return p[(G == 1) ? k * 32 : k]; }
+  __device__ __forceinline__ SV at(int off) const { return SV{p + ((G == 1) ? off * 32 : off)}; }
+};
+
+}  // namespace xt

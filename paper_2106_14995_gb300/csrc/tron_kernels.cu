@@ -1,0 +1,493 @@
+// tron_kernels.cu -- batched TRON kernels and the tron_batch_* C ABI.
+//
+// Plain schedule: one launch per size class, grid = problems / problems-per-CTA, each
+// thread group solves one problem start to finish (single-kernel design, Sec. 4.1).
+// Persistent schedule: one launch of resident CTAs; each warp pulls the next problems
+// of its size class from a device work counter until the class is exhausted, so warps
+// that drew quick problems take more of them instead of idling.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "capi_common.h"
+#include "tron_solver.cuh"
+
+namespace xt {
+
+// ------------------------------------------------------------------ error plumbing
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+// ------------------------------------------------------------------ kernel arguments
+struct KArgs {
+  const double* params;
+  const double* lo;
+  const double* hi;
+  double* x;
+  double* delta;
+  double* f;
+  double* pg;
+  int32_t* iters;
+  int32_t* status;
+  const int32_t* nvec;   // per-problem sizes (NULL: uniform)
+  const int64_t* poff;   // record offsets (NULL: p * pstride)
+  const int64_t* voff;   // vector offsets (NULL: p * n_uniform)
+  const int32_t* plist;  // problems of this launch (NULL: 0..count-1)
+  int64_t count;
+  int64_t pstride;
+  int32_t n_uniform;
+  int32_t pad;
+  unsigned long long* counter;  // persistent schedule work counter
+  tron_options_t opt;
+};
+
+template <class Obj, int N, int G>
+__device__ __forceinline__ void solve_problem(const KArgs& a, int64_t idx, double* wsm) {
+  using S = Solver<Obj, N, G>;
+  constexpr int R = S::R;
+  S sv(a.opt, wsm);
+  const int64_t q = a.plist ? (int64_t)a.plist[idx] : idx;
+  const int n = a.nvec ? a.nvec[q] : a.n_uniform;
+  const int64_t po = a.poff ? a.poff[q] : q * a.pstride;
+  const int64_t vo = a.voff ? a.voff[q] : q * (int64_t)a.n_uniform;
+  sv.n = n;
+  double x[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = r * G + sv.gp.t;
+    if (i < n) {
+      sv.l[r] = a.lo[vo + i];
+      sv.u[r] = a.hi[vo + i];
+      x[r] = a.x[vo + i];
+    } else {
+      sv.l[r] = 0.0;
+      sv.u[r] = 0.0;
+      x[r] = 0.0;
+    }
+  }
+  const bool pf = sv.obj.load(sv.gp, a.params ? a.params + po : nullptr, n);
+  double delta = a.delta[q];
+  double f, pg;
+  int k;
+  const int st = sv.run(x, delta, f, pg, k, pf);
+  if (st != TRON_BAD_BOUNDS) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = r * G + sv.gp.t;
+      if (i < n) a.x[vo + i] = x[r];
+    }
+  }
+  if (sv.gp.t == 0) {
+    a.delta[q] = delta;
+    a.f[q] = f;
+    a.pg[q] = pg;
+    a.iters[q] = k;
+    a.status[q] = st;
+  }
+}
+
+template <class Obj, int N, int G>
+__global__ void __launch_bounds__(256) k_tron_plain(const KArgs a) {
+  using S = Solver<Obj, N, G>;
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5;
+  double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  const int64_t idx = gw * S::PROBS_PER_WARP + (threadIdx.x & 31) / G;
+  if (idx >= a.count) return;
+  solve_problem<Obj, N, G>(a, idx, wsm);
+}
+
+template <class Obj, int N, int G>
+__global__ void __launch_bounds__(256) k_tron_persistent(const KArgs a) {
+  using S = Solver<Obj, N, G>;
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)S::PROBS_PER_WARP);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)base >= a.count) break;
+    const int64_t idx = (int64_t)base + lane / G;
+    if (idx < a.count) solve_problem<Obj, N, G>(a, idx, wsm);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ dispatch table
+struct KernelEntry {
+  int kind, N, G;
+  const void* plain;
+  const void* persistent;
+  int warp_doubles;
+  int probs_per_warp;
+  int occupancy[9];  // CTAs per SM by warps per block (cached, 0 = unknown)
+};
+
+template <class Obj, int N, int G>
+static KernelEntry make_entry(int kind) {
+  using S = Solver<Obj, N, G>;
+  KernelEntry e;
+  e.kind = kind;
+  e.N = N;
+  e.G = G;
+  e.plain = (const void*)k_tron_plain<Obj, N, G>;
+  e.persistent = (const void*)k_tron_persistent<Obj, N, G>;
+  e.warp_doubles = S::WARP_DOUBLES;
+  e.probs_per_warp = S::PROBS_PER_WARP;
+  for (int i = 0; i < 9; ++i) e.occupancy[i] = 0;
+  return e;
+}
+
+static std::vector<KernelEntry>& table() {
+  static std::vector<KernelEntry> t = {
+      make_entry<BranchObj, 4, 1>(TRON_OBJ_ACOPF_BRANCH),
+      make_entry<DenseObj<4, 1>, 4, 1>(TRON_OBJ_DENSE_QUARTIC),
+      make_entry<DenseObj<4, 4>, 4, 4>(TRON_OBJ_DENSE_QUARTIC),
+      make_entry<DenseObj<8, 1>, 8, 1>(TRON_OBJ_DENSE_QUARTIC),
+      make_entry<DenseObj<8, 8>, 8, 8>(TRON_OBJ_DENSE_QUARTIC),
+      make_entry<DenseObj<16, 8>, 16, 8>(TRON_OBJ_DENSE_QUARTIC),
+      make_entry<DenseObj<16, 16>, 16, 16>(TRON_OBJ_DENSE_QUARTIC),
+      make_entry<DenseObj<32, 16>, 32, 16>(TRON_OBJ_DENSE_QUARTIC),
+      make_entry<DenseObj<32, 32>, 32, 32>(TRON_OBJ_DENSE_QUARTIC),
+      make_entry<Hs45Obj<8>, 8, 1>(TRON_OBJ_HS45),
+  };
+  return t;
+}
+static std::mutex g_table_mu;
+
+// size classes per family and the default group size of each
+static int size_class(int kind, int n) {
+  if (kind == TRON_OBJ_ACOPF_BRANCH) return n == 4 ? 4 : -1;
+  if (kind == TRON_OBJ_HS45) return (n >= 1 && n <= 8) ? 8 : -1;
+  if (kind == TRON_OBJ_DENSE_QUARTIC) {
+    if (n < 1) return -1;
+    for (int c : {4, 8, 16, 32})
+      if (n <= c) return c;
+  }
+  return -1;
+}
+static int default_group(int kind, int N) {
+  if (kind == TRON_OBJ_DENSE_QUARTIC) return N <= 8 ? 1 : N;
+  return 1;
+}
+static KernelEntry* find_entry(int kind, int N, int G) {
+  for (auto& e : table())
+    if (e.kind == kind && e.N == N && e.G == G) return &e;
+  return nullptr;
+}
+
+}  // namespace xt
+
+using namespace xt;
+
+// ------------------------------------------------------------------------ handle
+struct tron_batch {
+  tron_obj_t kind;
+  int64_t nprob;
+  tron_options_t opt;
+  int32_t n_uniform;  // > 0 when every problem has this size
+  int32_t* d_n;
+  int64_t* d_poff;
+  int64_t* d_voff;
+  struct Bucket {
+    int N;
+    int64_t count;
+    int32_t* d_list;  // NULL when the bucket is the whole (uniform) batch
+  };
+  std::vector<Bucket> buckets;
+  unsigned long long* d_counter;  // one work counter per bucket
+  int last_launches;
+  int sms;
+};
+
+static int64_t record_size(int kind, int n) {
+  if (kind == TRON_OBJ_ACOPF_BRANCH) return 36;
+  if (kind == TRON_OBJ_DENSE_QUARTIC) return (int64_t)n * n + 2 * n;
+  return 0;
+}
+
+static tron_err_t check_options(const tron_options_t* o) {
+  XT_REQUIRE(o->max_outer >= 0 && o->max_trials >= 0 && o->max_shift >= 0, TRON_EINVAL,
+             "negative iteration cap in options");
+  XT_REQUIRE(o->group == 0 || o->group == 1 || o->group == 2 || o->group == 4 ||
+                 o->group == 8 || o->group == 16 || o->group == 32,
+             TRON_EINVAL, "options.group must be 0, 1, 2, 4, 8, 16 or 32");
+  XT_REQUIRE(o->schedule == TRON_SCHED_PLAIN || o->schedule == TRON_SCHED_PERSISTENT,
+             TRON_EINVAL, "options.schedule must be TRON_SCHED_PLAIN or TRON_SCHED_PERSISTENT");
+  XT_REQUIRE(o->warps_per_block >= 0 && o->warps_per_block <= 8, TRON_EINVAL,
+             "options.warps_per_block must be in [0, 8]");
+  return TRON_OK;
+}
+
+extern "C" {
+
+const char* tron_last_error(void) { return g_err.c_str(); }
+const char* tron_version(void) { return "exatron-gb300 0.1 (sm_103a, FP64)"; }
+
+tron_err_t tron_options_default(tron_options_t* o) {
+  XT_REQUIRE(o != nullptr, TRON_EINVAL, "tron_options_default: null pointer");
+  memset(o, 0, sizeof(*o));
+  o->gtol = 1e-6;
+  o->max_outer = 500;
+  o->max_trials = 30;
+  o->mu0 = 0.01;
+  o->mu1 = 1.0;
+  o->interpf = 0.1;
+  o->extrapf = 10.0;
+  o->proj_shrink = 0.5;
+  o->eta0 = 1e-4;
+  o->eta1 = 0.25;
+  o->eta2 = 0.75;
+  o->sigma1 = 0.25;
+  o->sigma3 = 4.0;
+  o->delta_max = 1e10;
+  o->delta_min_rel = 1e-12;
+  o->cg_rtol = 0.1;
+  o->shift_frac = 1e-3;
+  o->max_shift = 30;
+  o->group = 0;
+  o->ared_guard = 1e-13;
+  o->schedule = TRON_SCHED_PLAIN;
+  o->warps_per_block = 0;
+  return TRON_OK;
+}
+
+tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
+                             const int32_t* n_host, int32_t n_uniform,
+                             const tron_options_t* opt, void* stream) {
+  clear_error();
+  XT_REQUIRE(out != nullptr, TRON_EINVAL, "tron_batch_create: out is NULL");
+  *out = nullptr;
+  XT_REQUIRE(kind == TRON_OBJ_ACOPF_BRANCH || kind == TRON_OBJ_DENSE_QUARTIC ||
+                 kind == TRON_OBJ_HS45,
+             TRON_EINVAL, "tron_batch_create: unknown objective kind %d", (int)kind);
+  XT_REQUIRE(nprob >= 0 && nprob < (int64_t)1 << 31, TRON_EINVAL,
+             "tron_batch_create: nprob %lld out of range", (long long)nprob);
+  tron_options_t o;
+  if (opt) o = *opt;
+  else tron_options_default(&o);
+  tron_err_t e = check_options(&o);
+  if (e != TRON_OK) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  tron_batch* b = new tron_batch();
+  b->kind = kind;
+  b->nprob = nprob;
+  b->opt = o;
+  b->n_uniform = 0;
+  b->d_n = nullptr;
+  b->d_poff = nullptr;
+  b->d_voff = nullptr;
+  b->d_counter = nullptr;
+  b->last_launches = 0;
+  b->sms = device_sm_count();
+  auto fail = [&](tron_err_t code) {
+    tron_batch_destroy(b);
+    return code;
+  };
+  if (b->sms <= 0) {
+    set_error("tron_batch_create: no CUDA device");
+    return fail(TRON_ECUDA);
+  }
+  if (n_host == nullptr) {
+    if (size_class(kind, n_uniform) < 0) {
+      set_error("tron_batch_create: size n=%d not supported for kind %d", n_uniform, (int)kind);
+      return fail(TRON_EUNSUPPORTED);
+    }
+    b->n_uniform = n_uniform;
+    b->buckets.push_back({size_class(kind, n_uniform), nprob, nullptr});
+  } else {
+    std::vector<int64_t> poff(nprob), voff(nprob);
+    std::vector<std::vector<int32_t>> lists(5);
+    const int classes[5] = {4, 8, 16, 32, 0};
+    int64_t pa = 0, va = 0;
+    for (int64_t p = 0; p < nprob; ++p) {
+      const int n = n_host[p];
+      const int c = size_class(kind, n);
+      if (c < 0) {
+        set_error("tron_batch_create: problem %lld has unsupported size %d", (long long)p, n);
+        return fail(TRON_EUNSUPPORTED);
+      }
+      poff[p] = pa;
+      voff[p] = va;
+      pa += record_size(kind, n);
+      va += n;
+      int slot = 0;
+      while (classes[slot] != c) ++slot;
+      lists[slot].push_back((int32_t)p);
+    }
+    if (cudaMalloc(&b->d_n, sizeof(int32_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_poff, sizeof(int64_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_voff, sizeof(int64_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess) {
+      set_error("tron_batch_create: cudaMalloc of size tables failed");
+      return fail(TRON_ENOMEM);
+    }
+    if (nprob > 0) {
+      if (cudaMemcpyAsync(b->d_n, n_host, sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st) ||
+          cudaMemcpyAsync(b->d_poff, poff.data(), sizeof(int64_t) * nprob,
+                          cudaMemcpyHostToDevice, st) ||
+          cudaMemcpyAsync(b->d_voff, voff.data(), sizeof(int64_t) * nprob,
+                          cudaMemcpyHostToDevice, st)) {
+        set_error("tron_batch_create: upload of size tables failed");
+        return fail(TRON_ECUDA);
+      }
+    }
+    // largest class first: the longest solves start earliest
+    for (int slot = 3; slot >= 0; --slot) {
+      if (lists[slot].empty()) continue;
+      tron_batch::Bucket bk{classes[slot], (int64_t)lists[slot].size(), nullptr};
+      if (cudaMalloc(&bk.d_list, sizeof(int32_t) * lists[slot].size()) != cudaSuccess) {
+        set_error("tron_batch_create: cudaMalloc of a problem list failed");
+        return fail(TRON_ENOMEM);
+      }
+      b->buckets.push_back(bk);
+      if (cudaMemcpyAsync(bk.d_list, lists[slot].data(), sizeof(int32_t) * lists[slot].size(),
+                          cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        set_error("tron_batch_create: upload of a problem list failed");
+        return fail(TRON_ECUDA);
+      }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("tron_batch_create: stream synchronisation failed");
+      return fail(TRON_ECUDA);
+    }
+  }
+  if (cudaMalloc(&b->d_counter, sizeof(unsigned long long) * 8) != cudaSuccess) {
+    set_error("tron_batch_create: cudaMalloc of work counters failed");
+    return fail(TRON_ENOMEM);
+  }
+  // resolve the kernels now so that a bad group option fails here
+  for (auto& bk : b->buckets) {
+    const int G = o.group ? o.group : default_group(kind, bk.N);
+    if (!find_entry(kind, bk.N, G)) {
+      set_error("tron_batch_create: no kernel for kind %d, size class %d, group %d", (int)kind,
+                bk.N, G);
+      return fail(TRON_EUNSUPPORTED);
+    }
+  }
+  *out = b;
+  return TRON_OK;
+}
+
+tron_err_t tron_batch_set_options(tron_batch_t* b, const tron_options_t* opt) {
+  clear_error();
+  XT_REQUIRE(b && opt, TRON_EINVAL, "tron_batch_set_options: null argument");
+  tron_err_t e = check_options(opt);
+  if (e != TRON_OK) return e;
+  for (auto& bk : b->buckets) {
+    const int G = opt->group ? opt->group : default_group(b->kind, bk.N);
+    XT_REQUIRE(find_entry(b->kind, bk.N, G), TRON_EUNSUPPORTED,
+               "no kernel for kind %d, size class %d, group %d", (int)b->kind, bk.N, G);
+  }
+  b->opt = *opt;
+  return TRON_OK;
+}
+
+tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const double* d_lower,
+                            const double* d_upper, double* d_x, double* d_delta, double* d_f,
+                            double* d_pgnorm, int32_t* d_iters, int32_t* d_status,
+                            void* stream) {
+  clear_error();
+  XT_REQUIRE(b != nullptr, TRON_EINVAL, "tron_batch_solve: null handle");
+  b->last_launches = 0;
+  if (b->nprob == 0) return TRON_OK;
+  XT_REQUIRE(d_lower && d_upper && d_x && d_delta && d_f && d_pgnorm && d_iters && d_status,
+             TRON_EINVAL, "tron_batch_solve: null device array");
+  XT_REQUIRE(d_params || b->kind == TRON_OBJ_HS45, TRON_EINVAL,
+             "tron_batch_solve: d_params is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int wpb = b->opt.warps_per_block ? b->opt.warps_per_block : 4;
+  for (size_t bi = 0; bi < b->buckets.size(); ++bi) {
+    const auto& bk = b->buckets[bi];
+    if (bk.count == 0) continue;
+    const int G = b->opt.group ? b->opt.group : default_group(b->kind, bk.N);
+    KernelEntry* ke = find_entry(b->kind, bk.N, G);
+    XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d group %d", bk.N, G);
+    KArgs a;
+    memset(&a, 0, sizeof(a));
+    a.params = d_params;
+    a.lo = d_lower;
+    a.hi = d_upper;
+    a.x = d_x;
+    a.delta = d_delta;
+    a.f = d_f;
+    a.pg = d_pgnorm;
+    a.iters = d_iters;
+    a.status = d_status;
+    a.nvec = b->d_n;
+    a.poff = b->d_poff;
+    a.voff = b->d_voff;
+    a.plist = bk.d_list;
+    a.count = bk.count;
+    a.n_uniform = b->n_uniform;
+    a.pstride = record_size(b->kind, b->n_uniform);
+    a.counter = b->d_counter + bi;
+    a.opt = b->opt;
+    const size_t smem = (size_t)wpb * ke->warp_doubles * sizeof(double);
+    const void* fn = (b->opt.schedule == TRON_SCHED_PERSISTENT) ? ke->persistent : ke->plain;
+    {
+      std::lock_guard<std::mutex> lk(g_table_mu);
+      XT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    int64_t grid;
+    if (b->opt.schedule == TRON_SCHED_PERSISTENT) {
+      int occ = 0;
+      {
+        std::lock_guard<std::mutex> lk(g_table_mu);
+        occ = ke->occupancy[wpb];
+        if (occ == 0) {
+          XT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, wpb * 32, smem));
+          ke->occupancy[wpb] = occ;
+        }
+      }
+      XT_REQUIRE(occ > 0, TRON_EUNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
+      const int64_t per_cta = (int64_t)wpb * ke->probs_per_warp;
+      grid = std::min<int64_t>((int64_t)occ * b->sms, (bk.count + per_cta - 1) / per_cta);
+      XT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st));
+    } else {
+      const int64_t per_cta = (int64_t)wpb * ke->probs_per_warp;
+      grid = (bk.count + per_cta - 1) / per_cta;
+    }
+    void* args[] = {&a};
+    XT_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(wpb * 32), args, smem, st));
+    b->last_launches++;
+  }
+  return TRON_OK;
+}
+
+int32_t tron_batch_last_launches(const tron_batch_t* b) { return b ? b->last_launches : 0; }
+
+void tron_batch_destroy(tron_batch_t* b) {
+  if (!b) return;
+  cudaFree(b->d_n);
+  cudaFree(b->d_poff);
+  cudaFree(b->d_voff);
+  cudaFree(b->d_counter);
+  for (auto& bk : b->buckets) cudaFree(bk.d_list);
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,347 @@
+// tron_objectives.cuh -- device evaluators of f, grad f and the Hessian (Alg. 1 line 3).
+//
+// Interface used by the solver (tron_solver.cuh):
+//   SMEM                doubles of per-problem shared memory the evaluator needs
+//   kHasHd              the Hessian is hq(i,j) + [i==j] hd(i)
+//   load(gp, rec, n)    stage the packed record; returns false if it holds a non-finite
+//   eval_f(gp, y)       f(y); caches what the gradient needs
+//   grad_hess(gp, x, g) gradient at the point of the last eval_f, Hessian made current
+//   hq(i,j), hd(i)      Hessian entries at the current point
+//   hess_finite(gp)     all Hessian entries finite
+#pragma once
+
+#include "tron_common.cuh"
+
+namespace xt {
+
+// ------------------------------------------------------------------ dense quartic
+// f = 1/2 x'Qx + c'x + sum_i d_i x_i^4, record [Q (n x n) | c | d].
+// Q is staged once in shared memory and read by every Hessian product; the Hessian is
+// Q + diag(12 d_i x_i^2), kept as Q plus a diagonal vector.
+template <int N, int G>
+struct DenseObj {
+  static constexpr int R = N / G;
+  static constexpr int LDQ = (G == 1) ? N : N + 1;  // odd stride: conflict-free columns
+  static constexpr int SMEM = N * LDQ + 2 * N;      // Q, hd, staging
+  static constexpr bool kHasHd = true;
+
+  SV<G> Q, hdg, st;
+  double c[R], d[R], qy[R];
+  int n;
+
+  __device__ __forceinline__ void bind(SV<G> base) {
+    Q = base;
+    hdg = base.at(N * LDQ);
+    st = base.at(N * LDQ + N);
+  }
+
+  __device__ __forceinline__ bool load(const Grp<G>& gp, const double* __restrict__ rec, int n_) {
+    n = n_;
+    bool fin = true;
+    const int nn = n * n;
+    // zero the padding rows/columns, then copy Q (coalesced over the group)
+    for (int e = gp.t; e < N * LDQ; e += G) Q[e] = 0.0;
+    gp.sync();
+    for (int e = gp.t; e < nn; e += G) {
+      double v = __ldg(rec + e);
+      fin = fin && isfinite(v);
+      int i = e / n, j = e - i * n;
+      Q[i * LDQ + j] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int i = r * G + gp.t;
+      c[r] = (i < n) ? __ldg(rec + nn + i) : 0.0;
+      d[r] = (i < n) ? __ldg(rec + nn + n + i) : 0.0;
+      fin = fin && isfinite(c[r]) && isfinite(d[r]);
+      hdg[i] = 0.0;
+    }
+    gp.sync();
+    return !gp.any(!fin);
+  }
+
+  // y_i = sum_j Q_ij v_j for the slots of this lane (v staged in st for G >= 2)
+  __device__ __forceinline__ void qmul(const Grp<G>& gp, const double (&v)[R], double (&y)[R]) {
+    if constexpr (G == 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(Q[i * LDQ + j], v[j], s);
+        y[i] = s;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) st[r * G + gp.t] = v[r];
+      gp.sync();
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = r * G + gp.t;
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s = fma(Q[i * LDQ + j], st[j], s);
+        y[r] = s;
+      }
+      gp.sync();
+    }
+  }
+
+  __device__ __forceinline__ double eval_f(const Grp<G>& gp, const double (&y)[R]) {
+    qmul(gp, y, qy);
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      double y2 = y[r] * y[r];
+      s += y[r] * (0.5 * qy[r] + c[r]) + d[r] * y2 * y2;
+    }
+    return gp.sum(s);
+  }
+
+  __device__ __forceinline__ void grad_hess(const Grp<G>& gp, const double (&x)[R], double (&g)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      double x2 = x[r] * x[r];
+      g[r] = qy[r] + c[r] + 4.0 * d[r] * x2 * x[r];
+      hdg[r * G + gp.t] = 12.0 * d[r] * x[r] * x[r];
+    }
+    gp.sync();
+  }
+
+  __device__ __forceinline__ double hq(int i, int j) const { return Q[i * LDQ + j]; }
+  __device__ __forceinline__ double hd(int i) const { return hdg[i]; }
+
+  __device__ __forceinline__ bool hess_finite(const Grp<G>& gp) const {
+    bool fin = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) fin = fin && isfinite(hdg[r * G + gp.t]);
+    return !gp.any(!fin);
+  }
+};
+
+// -------------------------------------------------------------- ACOPF branch (n = 4)
+// eq. exp-branch of Sec. 6.1 with the flows of eqs. pij-qji and the line-limit penalty.
+// One problem per lane (G = 1): every lane evaluates its own branch, so the FP64 pipe
+// (including the sin/cos of theta_i - theta_j) runs with all 32 lanes busy.
+struct BranchObj {
+  static constexpr int N = 4;
+  static constexpr int R = 4;
+  static constexpr int SMEM = 36 + 16;  // record, Hessian
+  static constexpr bool kHasHd = false;
+
+  SV<1> rec, H;
+  double cs, sn, F[4];
+  int n;
+
+  __device__ __forceinline__ void bind(SV<1> base) {
+    rec = base;
+    H = base.at(36);
+  }
+
+  __device__ __forceinline__ bool load(const Grp<1>&, const double* __restrict__ src, int n_) {
+    n = n_;
+    bool fin = true;
+#pragma unroll
+    for (int k = 0; k < 34; ++k) {
+      double v = __ldg(src + k);
+      fin = fin && isfinite(v);
+      rec[k] = v;
+    }
+    return fin;
+  }
+
+  __device__ __forceinline__ double eval_f(const Grp<1>&, const double (&y)[4]) {
+    sincos(y[2] - y[3], &sn, &cs);
+    const double vi = y[0], vj = y[1];
+    const double wi = vi * vi, wj = vj * vj;
+    const double vv = vi * vj;
+    const double wR = vv * cs, wI = vv * sn;
+    F[0] = rec[0] * wi - rec[2] * wR + rec[3] * wI;
+    F[1] = rec[1] * wi - rec[3] * wR - rec[2] * wI;
+    F[2] = rec[4] * wj - rec[6] * wR - rec[7] * wI;
+    F[3] = rec[5] * wj - rec[7] * wR + rec[6] * wI;
+    const double P[8] = {F[0], F[1], F[2], F[3], wi, wj, y[2], y[3]};
+    double val = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double r = P[k] - rec[16 + k];
+      val += rec[8 + k] * r + 0.5 * rec[24 + k] * r * r;
+    }
+    const double smax2 = rec[32], rhol = rec[33];
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      double m = F[2 * dir] * F[2 * dir] + F[2 * dir + 1] * F[2 * dir + 1] - smax2;
+      if (m > 0.0) val += 0.5 * rhol * m * m;
+    }
+    return val;
+  }
+
+  // gradient and Hessian at the point of the last eval_f.  Each pair quantity is
+  // F_k = a_k w_i + b_k w_j + cR_k wR + cI_k wI (+ theta for k = 6, 7); the first-order
+  // weights t_k = lambda_k + rho_k (F_k - target_k) are folded into four scalars that
+  // multiply the second derivatives of w_i, w_j, wR, wI, and the Gauss-Newton part is
+  // the sum of rho_k grad F_k grad F_k'.
+  __device__ __forceinline__ void grad_hess(const Grp<1>&, const double (&x)[4], double (&g)[4]) {
+    const double vi = x[0], vj = x[1];
+    const double vv = vi * vj;
+    const double wR = vv * cs, wI = vv * sn;
+    const double wi = vi * vi, wj = vj * vj;
+    // derivatives of wR, wI (order v_i, v_j, th_i, th_j)
+    const double dR[4] = {vj * cs, vi * cs, -wI, wI};
+    const double dI[4] = {vj * sn, vi * sn, wR, -wR};
+    // coefficients (a, b, cR, cI) of the four flows
+    const double co[4][4] = {{rec[0], 0.0, -rec[2], rec[3]},
+                             {rec[1], 0.0, -rec[3], -rec[2]},
+                             {0.0, rec[4], -rec[6], -rec[7]},
+                             {0.0, rec[5], -rec[7], rec[6]}};
+    double dF[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      dF[k][0] = co[k][0] * (2.0 * vi) + co[k][2] * dR[0] + co[k][3] * dI[0];
+      dF[k][1] = co[k][1] * (2.0 * vj) + co[k][2] * dR[1] + co[k][3] * dI[1];
+      dF[k][2] = co[k][2] * dR[2] + co[k][3] * dI[2];
+      dF[k][3] = co[k][2] * dR[3] + co[k][3] * dI[3];
+    }
+    double t[8], W[4];
+    {
+      const double P[8] = {F[0], F[1], F[2], F[3], wi, wj, x[2], x[3]};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t[k] = rec[8 + k] + rec[24 + k] * (P[k] - rec[16 + k]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) W[k] = rec[24 + k];
+    }
+    double Hm[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Hm[a][b] = 0.0;
+    const double smax2 = rec[32], rhol = rec[33];
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      const int kp = 2 * dir, kq = 2 * dir + 1;
+      const double p = F[kp], q = F[kq];
+      const double m = p * p + q * q - smax2;
+      if (m > 0.0) {
+        // (rho_l/2) m^2: first-order weight rho_l m grad m, grad m = 2p dp + 2q dq;
+        // second order rho_l (grad m grad m' + m (2 dp dp' + 2p H_p + 2 dq dq' + 2q H_q))
+        t[kp] += rhol * m * 2.0 * p;
+        t[kq] += rhol * m * 2.0 * q;
+        W[kp] += 2.0 * rhol * m;
+        W[kq] += 2.0 * rhol * m;
+        double gm[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) gm[a] = 2.0 * p * dF[kp][a] + 2.0 * q * dF[kq][a];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = a; b < 4; ++b) Hm[a][b] += rhol * gm[a] * gm[b];
+      }
+    }
+    // scalars multiplying grad/Hessian of w_i, w_j, wR, wI
+    double Aw = t[4], Bw = t[5], CR = 0.0, CI = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Aw += t[k] * co[k][0];
+      Bw += t[k] * co[k][1];
+      CR += t[k] * co[k][2];
+      CI += t[k] * co[k][3];
+    }
+    g[0] = Aw * (2.0 * vi) + CR * dR[0] + CI * dI[0];
+    g[1] = Bw * (2.0 * vj) + CR * dR[1] + CI * dI[1];
+    g[2] = CR * dR[2] + CI * dI[2] + t[6];
+    g[3] = CR * dR[3] + CI * dI[3] + t[7];
+    // Gauss-Newton part
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a; b < 4; ++b) Hm[a][b] += W[k] * dF[k][a] * dF[k][b];
+    Hm[0][0] += rec[28] * (2.0 * vi) * (2.0 * vi);
+    Hm[1][1] += rec[29] * (2.0 * vj) * (2.0 * vj);
+    Hm[2][2] += rec[30];
+    Hm[3][3] += rec[31];
+    // second derivatives of w_i, w_j, wR, wI
+    Hm[0][0] += 2.0 * Aw;
+    Hm[1][1] += 2.0 * Bw;
+    Hm[0][1] += CR * cs + CI * sn;
+    Hm[0][2] += -CR * vj * sn + CI * vj * cs;
+    Hm[0][3] += CR * vj * sn - CI * vj * cs;
+    Hm[1][2] += -CR * vi * sn + CI * vi * cs;
+    Hm[1][3] += CR * vi * sn - CI * vi * cs;
+    Hm[2][2] += -CR * wR - CI * wI;
+    Hm[2][3] += CR * wR + CI * wI;
+    Hm[3][3] += -CR * wR - CI * wI;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        H[a * 4 + b] = Hm[a][b];
+        H[b * 4 + a] = Hm[a][b];
+      }
+  }
+
+  __device__ __forceinline__ double hq(int i, int j) const { return H[i * 4 + j]; }
+  __device__ __forceinline__ double hd(int) const { return 0.0; }
+  __device__ __forceinline__ bool hess_finite(const Grp<1>&) const {
+    bool fin = true;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) fin = fin && isfinite(H[e]);
+    return fin;
+  }
+};
+
+// ------------------------------------------------------------------ hs45 variant
+// f = 120 - prod_i x_i (Sec. 4.2 footnote), one problem per lane, n <= N.
+template <int N>
+struct Hs45Obj {
+  static constexpr int R = N;
+  static constexpr int SMEM = N * N;
+  static constexpr bool kHasHd = false;
+
+  SV<1> H;
+  double xc[N];
+  int n;
+
+  __device__ __forceinline__ void bind(SV<1> base) { H = base; }
+  __device__ __forceinline__ bool load(const Grp<1>&, const double*, int n_) {
+    n = n_;
+    return true;
+  }
+  __device__ __forceinline__ double eval_f(const Grp<1>&, const double (&y)[N]) {
+    double p = 1.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      xc[i] = y[i];
+      if (i < n) p *= y[i];
+    }
+    return 120.0 - p;
+  }
+  __device__ __forceinline__ void grad_hess(const Grp<1>&, const double (&)[N], double (&g)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double q = 1.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+        if (j != i && j < n) q *= xc[j];
+      g[i] = (i < n) ? -q : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        double q = 1.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k != i && k != j && k < n) q *= xc[k];
+        H[i * N + j] = (i == j || i >= n || j >= n) ? 0.0 : -q;
+      }
+  }
+  __device__ __forceinline__ double hq(int i, int j) const { return H[i * N + j]; }
+  __device__ __forceinline__ double hd(int) const { return 0.0; }
+  __device__ __forceinline__ bool hess_finite(const Grp<1>&) const {
+    bool fin = true;
+    for (int e = 0; e < n * N; ++e) fin = fin && isfinite(H[e]);
+    return fin;
+  }
+};
+
+}  // namespace xt

@@ -1,0 +1,562 @@
+// tron_solver.cuh -- Algorithm 1 (Sec. 3) on one thread group of G lanes.
+//
+// Per outer iteration, all on the device (Sec. 4.1: single kernel, no host traffic):
+//   projected-gradient max-norm test (Sec. 5.1) -> Cauchy point with the
+//   interpolation/extrapolation search (line 4) -> free set of the current point and
+//   gather of H_FF (line 5, Sec. 5.3) -> shifted complete Cholesky, left-looking, with
+//   L^T mirrored into the upper triangle (lines 6-7, Sec. 4.3, 4.4) -> Steihaug PCG in
+//   the preconditioned variables with the step kept inside ||w||_2 <= delta (lines 8-9)
+//   -> projected search (line 10) -> reduction ratio, acceptance and radius update.
+//
+// Storage: the vectors of a problem are register arrays spread over the group (slot r
+// of lane t holds variable r*G + t); the factor L (with L^T mirrored) and the objective
+// data sit in the problem's shared-memory slice; the free-set indices are an int list
+// in shared memory.  Triangular solves read rows of the lower part (backward, L^T z = p)
+// or rows of the mirrored upper part (forward, L y = b), so every shared-memory access
+// of a solve is contiguous across the group (Sec. 4.4).
+//
+// FP64 economy on this GPU: the pivot of each Cholesky column is taken with one rsqrt,
+// whose value scales the column and is kept as 1/L_jj for the triangular solves, which
+// then multiply instead of divide.
+#pragma once
+
+#include "../../include/tron.h"
+#include "tron_common.cuh"
+#include "tron_objectives.cuh"
+
+namespace xt {
+
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+template <class Obj, int N, int G>
+struct Solver {
+  static constexpr int R = N / G;
+  static_assert(N % G == 0, "size class must be a multiple of the group size");
+  static constexpr int LD = (G == 1) ? N : N + 1;
+  // per-problem shared-memory slice, offsets in doubles
+  static constexpr int OFF_L = 0;
+  static constexpr int OFF_VB = OFF_L + N * LD;
+  static constexpr int OFF_DINV = OFF_VB + N;
+  static constexpr int OFF_FI = OFF_DINV + N;  // N ints (in N double slots)
+  static constexpr int OFF_OBJ = OFF_FI + N;
+  static constexpr int S_RAW = OFF_OBJ + Obj::SMEM;
+  // problems of one warp start at banks that differ by G doubles (conflict-free when
+  // several problems share a warp)
+  static constexpr int S = (G == 1 || G >= 16) ? round_up(S_RAW, 2)
+                                               : S_RAW + ((G - S_RAW % 16) % 16 + 16) % 16;
+  static constexpr int PROBS_PER_WARP = 32 / G;
+  static constexpr int WARP_DOUBLES = (G == 1) ? S * 32 : S * PROBS_PER_WARP;
+
+  Grp<G> gp;
+  const tron_options_t& o;
+  Obj obj;
+  int n;
+  SV<G> Lm, vb, dinv;
+  SV<G, int> Fi;
+  double l[R], u[R];
+
+  __device__ __forceinline__ Solver(const tron_options_t& opt, double* warp_smem) : o(opt) {
+    double* base = (G == 1) ? warp_smem + gp.lane : warp_smem + (gp.lane / G) * S;
+    SV<G> sv{base};
+    Lm = sv.at(OFF_L);
+    vb = sv.at(OFF_VB);
+    dinv = sv.at(OFF_DINV);
+    Fi = SV<G, int>{(G == 1) ? reinterpret_cast<int*>(warp_smem + OFF_FI * 32) + gp.lane
+                             : reinterpret_cast<int*>(base + OFF_FI)};
+    obj.bind(sv.at(OFF_OBJ));
+  }
+
+  // ------------------------------------------------------------------ vector helpers
+  __device__ __forceinline__ double P(double v, int r) const {
+    return v < l[r] ? l[r] : (v > u[r] ? u[r] : v);
+  }
+  __device__ __forceinline__ double dotv(const double (&a)[R], const double (&b)[R]) const {
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) s = fma(a[r], b[r], s);
+    return gp.sum(s);
+  }
+  __device__ __forceinline__ double pgnorm(const double (&x)[R], const double (&g)[R]) const {
+    double m = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      double p = g[r];
+      if (x[r] <= l[r] && p > 0.0) p = 0.0;
+      if (x[r] >= u[r] && p < 0.0) p = 0.0;
+      m = fmax(m, fabs(p));
+    }
+    return gp.max(m);
+  }
+
+  // y = H v over the full vector (H at the current accepted point)
+  __device__ __forceinline__ void hv(const double (&v)[R], double (&y)[R]) {
+    if constexpr (G == 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(obj.hq(i, j), v[j], s);
+        if (Obj::kHasHd) s = fma(obj.hd(i), v[i], s);
+        y[i] = s;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) vb[r * G + gp.t] = v[r];
+      gp.sync();
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = r * G + gp.t;
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s = fma(obj.hq(i, j), vb[j], s);
+        if (Obj::kHasHd) s = fma(obj.hd(i), v[r], s);
+        y[r] = s;
+      }
+      gp.sync();
+    }
+  }
+
+  // q = H_FF z in compacted coordinates (slot r <-> free position r*G + t)
+  __device__ __forceinline__ void hv_free(int m, const double (&z)[R], double (&q)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) vb[r * G + gp.t] = z[r];
+    gp.sync();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = r * G + gp.t;
+      double s = 0.0;
+      if (c < m) {
+        const int i = Fi[c];
+        for (int d = 0; d < m; ++d) s = fma(obj.hq(i, Fi[d]), vb[d], s);
+        if (Obj::kHasHd) s = fma(obj.hd(i), z[r], s);
+      }
+      q[r] = s;
+    }
+    gp.sync();
+  }
+
+  // ------------------------------------------------------------ Cholesky (Sec. 4.3)
+  // left-looking: column j gathers the updates of columns 0..j-1 (read from the
+  // mirrored rows of L^T), then scales by 1/sqrt(pivot); L^T mirrored as it goes.
+  __device__ __forceinline__ bool chol_left(int m) {
+    for (int j = 0; j < m; ++j) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = r * G + gp.t;
+        if (c >= j && c < m) {
+          double v = Lm[c * LD + j];
+          for (int k = 0; k < j; ++k) v = fma(-Lm[k * LD + c], Lm[k * LD + j], v);
+          Lm[j * LD + c] = v;
+        }
+      }
+      gp.sync();
+      const double piv = Lm[j * LD + j];
+      if (!(piv > 0.0)) {
+        gp.sync();
+        return false;
+      }
+      const double rs = rsqrt(piv);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = r * G + gp.t;
+        if (c > j && c < m) {
+          const double lcj = Lm[j * LD + c] * rs;
+          Lm[j * LD + c] = lcj;
+          Lm[c * LD + j] = lcj;
+        }
+      }
+      if (gp.t == (j & (G - 1))) {
+        Lm[j * LD + j] = piv * rs;
+        dinv[j] = rs;
+      }
+      gp.sync();
+    }
+    return true;
+  }
+
+  // shifted factorization A + alpha I = L L^T, alpha from the sequence
+  // 0 (or beta - min A_ii), then max(2 alpha, beta), beta = shift_frac * max |A_ii|
+  __device__ __forceinline__ bool factor(int m) {
+    double dmax = 0.0, dmin = CUDART_INF;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = r * G + gp.t;
+      if (c < m) {
+        const int i = Fi[c];
+        double a = obj.hq(i, i);
+        if (Obj::kHasHd) a = a + obj.hd(i);
+        dmax = fmax(dmax, fabs(a));
+        dmin = fmin(dmin, a);
+      }
+    }
+    dmax = gp.max(dmax);
+    dmin = gp.min(dmin);
+    double beta = o.shift_frac * dmax;
+    if (beta == 0.0) beta = o.shift_frac;
+    double alpha = (dmin > 0.0) ? 0.0 : beta - dmin;
+    for (int tr = 0; tr <= o.max_shift; ++tr) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = r * G + gp.t;
+        if (c < m) {
+          const int i = Fi[c];
+          for (int d = 0; d < c; ++d) Lm[c * LD + d] = obj.hq(i, Fi[d]);
+          double a = obj.hq(i, i);
+          if (Obj::kHasHd) a = a + obj.hd(i);
+          Lm[c * LD + c] = a + alpha;
+        }
+      }
+      gp.sync();
+      if (chol_left(m)) return true;
+      alpha = fmax(2.0 * alpha, beta);
+    }
+    return false;
+  }
+
+  // b <- L^-1 b (column-oriented; column j of L is row j of the mirrored upper part)
+  __device__ __forceinline__ void solve_L(int m, double (&b)[R]) {
+#pragma unroll
+    for (int rj = 0; rj < R; ++rj) {
+      for (int tj = 0; tj < G; ++tj) {
+        const int j = rj * G + tj;
+        if (j >= m) break;
+        const double yj = gp.bcast(b[rj], tj) * dinv[j];
+        if (gp.t == tj) b[rj] = yj;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int c = r * G + gp.t;
+          if (c > j && c < m) b[r] = fma(-Lm[j * LD + c], yj, b[r]);
+        }
+      }
+    }
+  }
+
+  // z <- L^-T z (column-oriented over L^T; column j of L^T is row j of L)
+  __device__ __forceinline__ void solve_Lt(int m, double (&z)[R]) {
+#pragma unroll
+    for (int rj = R - 1; rj >= 0; --rj) {
+      for (int tj = G - 1; tj >= 0; --tj) {
+        const int j = rj * G + tj;
+        if (j >= m) continue;
+        const double zj = gp.bcast(z[rj], tj) * dinv[j];
+        if (gp.t == tj) z[rj] = zj;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int c = r * G + gp.t;
+          if (c < j) z[r] = fma(-Lm[j * LD + c], zj, z[r]);
+        }
+      }
+    }
+  }
+
+  // trqsol (Figure 2): sigma >= 0 with ||x + sigma p||_2 = delta
+  __device__ __forceinline__ double trqsol(const double (&x)[R], const double (&p)[R],
+                                           double delta) const {
+    const double ptx = dotv(p, x), ptp = dotv(p, p), xtx = dotv(x, x);
+    const double dsq = delta * delta;
+    double rad = ptx * ptx + ptp * (dsq - xtx);
+    if (rad < 0.0) rad = 0.0;
+    rad = sqrt(rad);
+    return (ptx >= 0.0) ? (dsq - xtx) / (ptx + rad) : (rad - ptx) / ptp;
+  }
+
+  // Steihaug PCG on Ahat = L^-1 A L^-T, bhat given; w = L^-T s accumulated directly.
+  // Returns 0 converged, 1 iteration cap, 2 boundary, 3 negative curvature.
+  __device__ __forceinline__ int steihaug(int m, double delta, const double (&bh)[R],
+                                          double (&w)[R]) {
+    double res[R], p[R], z[R], q[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      w[r] = 0.0;
+      res[r] = -bh[r];
+      p[r] = res[r];
+    }
+    double rr = dotv(res, res);
+    const double tol = o.cg_rtol * sqrt(rr);
+    int info = 1;
+    for (int it = 0; it < m; ++it) {
+      if (sqrt(rr) <= tol) {
+        info = 0;
+        break;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) z[r] = p[r];
+      solve_Lt(m, z);
+      hv_free(m, z, q);
+      solve_L(m, q);
+      const double kappa = dotv(p, q);
+      if (kappa <= 0.0) {
+        const double sg = trqsol(w, z, delta);
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[r] = fma(sg, z[r], w[r]);
+        info = 3;
+        break;
+      }
+      const double alpha = rr / kappa;
+      double wn[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) wn[r] = fma(alpha, z[r], w[r]);
+      if (sqrt(dotv(wn, wn)) >= delta) {
+        const double sg = trqsol(w, z, delta);
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[r] = fma(sg, z[r], w[r]);
+        info = 2;
+        break;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        w[r] = wn[r];
+        res[r] = fma(-alpha, q[r], res[r]);
+      }
+      const double rrn = dotv(res, res);
+      const double beta = rrn / rr;
+      rr = rrn;
+#pragma unroll
+      for (int r = 0; r < R; ++r) p[r] = fma(beta, p[r], res[r]);
+    }
+    return info;
+  }
+
+  // Cauchy trial s(alpha) = P[x - alpha g] - x: q(s) <= mu0 g's and ||s|| <= mu1 delta
+  __device__ __forceinline__ bool cauchy_try(double alpha, const double (&x)[R],
+                                             const double (&g)[R], double delta,
+                                             double (&s)[R], double (&Hs)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[r] = P(fma(alpha, -g[r], x[r]), r) - x[r];
+    hv(s, Hs);
+    const double gts = dotv(g, s);
+    const double q = gts + 0.5 * dotv(s, Hs);
+    const double snorm = sqrt(dotv(s, s));
+    return (q <= o.mu0 * gts) && (snorm <= o.mu1 * delta);
+  }
+
+  // largest breakpoint along w = -g (breakpt of Figure 2), 0 if nothing can move
+  __device__ __forceinline__ double brptmax(const double (&x)[R], const double (&g)[R]) const {
+    double bmax = -CUDART_INF;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double w = -g[r];
+      if (x[r] < u[r] && w > 0.0) bmax = fmax(bmax, (u[r] - x[r]) / w);
+      else if (x[r] > l[r] && w < 0.0) bmax = fmax(bmax, (l[r] - x[r]) / w);
+    }
+    bmax = gp.max(bmax);
+    return (bmax == -CUDART_INF) ? 0.0 : bmax;
+  }
+
+  __device__ __forceinline__ bool all_finite(const double (&v)[R]) const {
+    bool fin = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) fin = fin && isfinite(v[r]);
+    return !gp.any(!fin);
+  }
+
+  // ------------------------------------------------------------------- Algorithm 1
+  __device__ int run(double (&x)[R], double& delta, double& f, double& pg, int& k,
+                     bool params_finite) {
+    k = 0;
+    {
+      bool bad = false;
+#pragma unroll
+      for (int r = 0; r < R; ++r) bad = bad || !(l[r] <= u[r]);
+      if (gp.any(bad)) {
+        f = CUDART_NAN;
+        pg = CUDART_NAN;
+        return TRON_BAD_BOUNDS;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = P(x[r], r);
+    double g[R];
+    f = obj.eval_f(gp, x);
+    obj.grad_hess(gp, x, g);
+    if (!params_finite || !isfinite(f) || !all_finite(g) || !obj.hess_finite(gp)) {
+      pg = isfinite(f) ? pgnorm(x, g) : CUDART_NAN;
+      return TRON_NONFINITE;
+    }
+    if (!(delta > 0.0)) {
+      double s[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[r] = P(x[r] - g[r], r) - x[r];
+      delta = sqrt(dotv(s, s));
+      if (delta == 0.0) delta = 1.0;
+    }
+    double alpha_c = 1.0;
+    int status = TRON_MAX_ITER;
+
+    for (;;) {
+      pg = pgnorm(x, g);
+      if (pg <= o.gtol) {
+        status = TRON_CONVERGED;
+        break;
+      }
+      if (k >= o.max_outer) {
+        status = TRON_MAX_ITER;
+        break;
+      }
+      ++k;
+
+      // ---- Cauchy point (line 4)
+      double s[R], Hs[R];
+      double alpha = alpha_c;
+      if (cauchy_try(alpha, x, g, delta, s, Hs)) {
+        const double bmax = brptmax(x, g);
+        double sb[R], Hsb[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          sb[r] = s[r];
+          Hsb[r] = Hs[r];
+        }
+        for (int t = 0; t < o.max_trials; ++t) {
+          if (!(alpha < bmax)) break;
+          const double a2 = alpha * o.extrapf;
+          if (!cauchy_try(a2, x, g, delta, s, Hs)) break;
+          alpha = a2;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            sb[r] = s[r];
+            Hsb[r] = Hs[r];
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          s[r] = sb[r];
+          Hs[r] = Hsb[r];
+        }
+      } else {
+        for (int t = 0; t < o.max_trials; ++t) {
+          alpha = alpha * o.interpf;
+          if (cauchy_try(alpha, x, g, delta, s, Hs)) break;
+        }
+      }
+      alpha_c = alpha;
+      double y[R], rv[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        // x_c = P[x - alpha g]; y - x equals the s of the accepted trial bit for bit,
+        // so the model gradient at x_c is g + Hs without another product
+        y[r] = P(fma(-alpha, g[r], x[r]), r);
+        rv[r] = g[r] + Hs[r];
+      }
+
+      // ---- subspace passes (lines 5-10)
+      double rF0 = 0.0;
+      for (int pass = 0; pass < n; ++pass) {
+        int cidx[R];
+        int m = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const bool fr = (l[r] < y[r]) && (y[r] < u[r]);
+          const unsigned b = gp.ballot(fr);
+          cidx[r] = fr ? m + __popc(b & ((1u << gp.t) - 1u)) : -1;
+          m += __popc(b);
+        }
+        if (m == 0) break;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (cidx[r] >= 0) Fi[cidx[r]] = r * G + gp.t;
+          vb[r * G + gp.t] = rv[r];
+        }
+        gp.sync();
+        double rF[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int c = r * G + gp.t;
+          rF[r] = (c < m) ? vb[Fi[c]] : 0.0;
+        }
+        gp.sync();
+        if (pass == 0) rF0 = sqrt(dotv(rF, rF));
+        if (!factor(m)) {
+          status = TRON_CHOL_FAIL;
+          break;
+        }
+        double bh[R], wF[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) bh[r] = rF[r];
+        solve_L(m, bh);
+        const int info = steihaug(m, delta, bh, wF);
+        // scatter w_F to the full direction w
+#pragma unroll
+        for (int r = 0; r < R; ++r) vb[r * G + gp.t] = 0.0;
+        gp.sync();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int c = r * G + gp.t;
+          if (c < m) vb[Fi[c]] = wF[r];
+        }
+        gp.sync();
+        double w[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[r] = vb[r * G + gp.t];
+        gp.sync();
+        // projected search from y along w (line 10)
+        double beta = 1.0;
+        bool found = false;
+        double yt[R], d[R], Hd[R];
+        for (int t = 0; t < o.max_trials; ++t) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            yt[r] = P(fma(beta, w[r], y[r]), r);
+            d[r] = yt[r] - y[r];
+          }
+          hv(d, Hd);
+          const double rtd = dotv(rv, d);
+          const double dHd = dotv(d, Hd);
+          if (rtd + 0.5 * dHd <= o.mu0 * rtd) {
+            found = true;
+            break;
+          }
+          beta = beta * o.proj_shrink;
+        }
+        if (!found) break;
+        bool na = false;
+        double ss = 0.0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (cidx[r] >= 0 && !((l[r] < yt[r]) && (yt[r] < u[r]))) na = true;
+          y[r] = yt[r];
+          rv[r] = rv[r] + Hd[r];
+          if (cidx[r] >= 0) ss = fma(rv[r], rv[r], ss);
+        }
+        const bool newly_active = gp.any(na);
+        const double rFn = sqrt(gp.sum(ss));
+        if (info == 2 || info == 3 || newly_active || rFn <= o.cg_rtol * rF0) break;
+      }
+      if (status == TRON_CHOL_FAIL) break;
+
+      // ---- reduction ratio, acceptance, radius
+      double s2[R], Hs2[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) s2[r] = y[r] - x[r];
+      hv(s2, Hs2);
+      const double qs = dotv(g, s2) + 0.5 * dotv(s2, Hs2);
+      const double fy = obj.eval_f(gp, y);
+      const double pred = -qs;
+      const double ared = f - fy;
+      const double fl = o.ared_guard * fmax(fabs(f), 1.0);
+      const double rho = (pred > 0.0 && isfinite(fy)) ? (ared + fl) / (pred + fl) : -CUDART_INF;
+      const double snorm = sqrt(dotv(s2, s2));
+      if (rho > o.eta0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = y[r];
+        f = fy;
+        obj.grad_hess(gp, x, g);
+        if (!all_finite(g) || !obj.hess_finite(gp)) {
+          status = TRON_NONFINITE;
+          break;
+        }
+      }
+      if (rho < o.eta1) {
+        delta = o.sigma1 * fmin(snorm, delta);
+      } else if (rho > o.eta2 && snorm >= 0.99 * delta) {
+        delta = fmin(o.sigma3 * delta, o.delta_max);
+      }
+      if (delta < o.delta_min_rel * (1.0 + sqrt(dotv(x, x)))) {
+        status = TRON_TR_TOO_SMALL;
+        break;
+      }
+    }
+    pg = pgnorm(x, g);
+    return status;
+  }
+};
+
+}  // namespace xt

@@ -1,0 +1,109 @@
+"""ctypes binding of the C ABI (include/tron.h, include/admm.h).
+
+Argument marshalling only: every step of a solve runs in the CUDA kernels of
+libexatron_gb300.so.  The functions keep the C names; device buffers are torch CUDA
+tensors (their data pointers are passed) and streams are torch CUDA streams.  There is
+no fallback: a missing library or a failing call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+TRON_OBJ_ACOPF_BRANCH, TRON_OBJ_DENSE_QUARTIC, TRON_OBJ_HS45 = 1, 2, 3
+TRON_CONVERGED, TRON_MAX_ITER, TRON_TR_TOO_SMALL, TRON_CHOL_FAIL, TRON_NONFINITE, \
+    TRON_BAD_BOUNDS = range(6)
+TRON_SCHED_PLAIN, TRON_SCHED_PERSISTENT = 0, 1
+ERR_NAMES = {0: "TRON_OK", 1: "TRON_EINVAL", 2: "TRON_ENOMEM", 3: "TRON_ECUDA",
+             4: "TRON_EUNSUPPORTED"}
+
+
+class TronOptions(C.Structure):
+    _fields_ = [
+        ("gtol", C.c_double), ("max_outer", C.c_int32), ("max_trials", C.c_int32),
+        ("mu0", C.c_double), ("mu1", C.c_double), ("interpf", C.c_double),
+        ("extrapf", C.c_double), ("proj_shrink", C.c_double), ("eta0", C.c_double),
+        ("eta1", C.c_double), ("eta2", C.c_double), ("sigma1", C.c_double),
+        ("sigma3", C.c_double), ("delta_max", C.c_double), ("delta_min_rel", C.c_double),
+        ("cg_rtol", C.c_double), ("shift_frac", C.c_double), ("max_shift", C.c_int32),
+        ("group", C.c_int32), ("ared_guard", C.c_double), ("schedule", C.c_int32),
+        ("warps_per_block", C.c_int32), ("reserved", C.c_int32 * 8),
+    ]
+
+
+class TronError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building in-tree if needed) libexatron_gb300.so; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise TronError("libexatron_gb300.so is missing; run __graft_entry__.build()")
+        L = C.CDLL(_build.LIB)
+        P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "tron_options_default": (I32, [C.POINTER(TronOptions)]),
+            "tron_batch_create": (I32, [C.POINTER(P), I32, I64, P, I32,
+                                        C.POINTER(TronOptions), P]),
+            "tron_batch_set_options": (I32, [P, C.POINTER(TronOptions)]),
+            "tron_batch_solve": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
+            "tron_batch_last_launches": (I32, [P]),
+            "tron_batch_destroy": (None, [P]),
+            "tron_last_error": (C.c_char_p, []),
+            "tron_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def check(code: int, what: str) -> None:
+    if code != 0:
+        msg = load().tron_last_error().decode(errors="replace")
+        raise TronError(f"{what}: {ERR_NAMES.get(code, code)}: {msg}")
+
+
+def ptr(t) -> int:
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise TronError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise TronError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def tron_options_default() -> TronOptions:
+    o = TronOptions()
+    check(load().tron_options_default(C.byref(o)), "tron_options_default")
+    return o
+
+
+def tron_version() -> str:
+    return load().tron_version().decode()

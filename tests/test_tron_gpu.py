@@ -1,0 +1,181 @@
+"""GPU parity of batched TRON against the CPU oracle, through the C ABI.
+
+Tolerances (from the stated accuracy targets): projected-gradient max-norm <= 1e-6 for
+every converged problem; on convex problems ||x_gpu - x_oracle||_inf <= 1e-6 and
+relative objective difference <= 1e-8; on nonconvex problems (branch, hs45) x within
+1e-6 where both runs took the same path, otherwise both must be KKT points.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2106_14995_gb300 import native, synth
+from paper_2106_14995_gb300.tron import TronBatch, options
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+def _t(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def gpu_solve(d, n=None, n_list=None, **opt):
+    B = d["delta0"].shape[0]
+    o = options(**opt)
+    tb = TronBatch(d["kind"], B, n=n if n_list is None else None, n_list=n_list, opts=o)
+    params = _t(d["params"]) if np.size(d["params"]) else None
+    x = _t(d["x0"])
+    delta = _t(d["delta0"])
+    out = tb.solve(params, _t(d["l"]), _t(d["u"]), x, delta)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["launches"] = tb.last_launches
+    tb.close()
+    return res
+
+
+def oracle_solve(d, n_list=None, **opt):
+    return oracle.tron_batch(d["kind"], d["params"] if np.size(d["params"]) else None, d["l"],
+                             d["u"], d["x0"], d["delta0"], n=n_list,
+                             opts=oracle.default_opts(**opt), nthreads=8)
+
+
+def assert_convex_parity(g, r, l, u):
+    assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
+    assert np.all(r["status"] == oracle.CONVERGED)
+    assert np.all(g["pg"] <= 1e-6)
+    np.testing.assert_allclose(g["x"], r["x"], rtol=0, atol=1e-6)
+    rel = np.abs(g["f"] - r["f"]) / np.maximum(1.0, np.abs(r["f"]))
+    assert rel.max() <= 1e-8, rel.max()
+    assert np.all(g["x"] >= l) and np.all(g["x"] <= u)
+
+
+def test_dense_n32_parity_ragged():
+    # 301 problems of the n = 32 workload: several CTAs and a ragged tail
+    d = synth.dense_batch(301, 32, seed_index=1)
+    g = gpu_solve(d, n=32)
+    r = oracle_solve(d)
+    assert g["launches"] == 1
+    assert_convex_parity(g, r, d["l"], d["u"])
+    # same path: iteration counts agree on (almost) every problem
+    assert np.mean(g["iters"] == r["iters"]) >= 0.95
+
+
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 7, 8, 12, 16, 20, 31, 32])
+def test_dense_sizes(n):
+    d = synth.dense_batch(97, n, seed_index=20 + n)
+    g = gpu_solve(d, n=n)
+    r = oracle_solve(d)
+    assert_convex_parity(g, r, d["l"], d["u"])
+
+
+@pytest.mark.parametrize("n,group", [(4, 1), (4, 4), (8, 1), (8, 8), (16, 8), (16, 16),
+                                     (32, 16), (32, 32)])
+def test_dense_group_mappings(n, group):
+    d = synth.dense_batch(133, n, seed_index=40 + n)
+    g = gpu_solve(d, n=n, group=group)
+    r = oracle_solve(d)
+    assert_convex_parity(g, r, d["l"], d["u"])
+
+
+def _branch_kkt(rec, x, l, u):
+    f, gr, _ = oracle.eval_obj(oracle.OBJ_BRANCH, rec, x)
+    return oracle.pgnorm(x, gr, l, u)
+
+
+def test_branch_parity_256():
+    d = synth.branch_batch(256, seed_index=0)
+    g = gpu_solve(d, n=4)
+    r = oracle_solve(d)
+    assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
+    assert np.all(r["status"] == oracle.CONVERGED)
+    # the GPU result is a KKT point by the oracle's own gradient
+    for p in range(256):
+        assert _branch_kkt(d["params"][p], g["x"][p], d["l"][p], d["u"][p]) <= 1e-6 * 1.01
+    same = np.all(np.abs(g["x"] - r["x"]) <= 1e-6, axis=1)
+    assert same.mean() >= 0.98, f"{(~same).sum()} of 256 branch solutions differ"
+    rel = np.abs(g["f"] - r["f"])[same] / np.maximum(1.0, np.abs(r["f"][same]))
+    assert rel.max() <= 1e-8
+
+
+def test_hs45_gpu_matches_printed_solution():
+    for n in range(2, 9):
+        d = synth.hs45_batch(33, n)
+        g = gpu_solve(d, n=n)
+        assert np.all(g["status"] == native.TRON_CONVERGED)
+        np.testing.assert_allclose(g["x"], np.tile(np.arange(1, n + 1), (33, 1)), atol=1e-9)
+
+
+def test_uneven_sizes_one_batch():
+    d = synth.uneven_batch(400, seed_index=3, sizes=(4, 6, 8, 16, 32),
+                           probs=(0.4, 0.2, 0.15, 0.15, 0.1))
+    nv = d["nvec"]
+    g = gpu_solve(d, n_list=nv)
+    r = oracle_solve(d, n_list=nv)
+    classes = {min(c for c in (4, 8, 16, 32) if n <= c) for n in nv.tolist()}
+    assert g["launches"] == len(classes)   # one launch per size class
+    assert np.all(g["status"] == 0) and np.all(r["status"] == 0)
+    np.testing.assert_allclose(g["x"], r["x"], rtol=0, atol=1e-6)
+
+
+def test_persistent_equals_plain_bitwise():
+    d = synth.dense_batch(500, 32, seed_index=7)
+    a = gpu_solve(d, n=32)
+    b = gpu_solve(d, n=32, schedule=native.TRON_SCHED_PERSISTENT)
+    for k in ("x", "f", "pg", "iters", "status", "delta"):
+        np.testing.assert_array_equal(a[k], b[k])
+    d = synth.branch_batch(300, seed_index=8)
+    a = gpu_solve(d, n=4)
+    b = gpu_solve(d, n=4, schedule=native.TRON_SCHED_PERSISTENT)
+    for k in ("x", "f", "pg", "iters", "status", "delta"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_edge_cases_status_codes():
+    n = 6
+    d = synth.dense_batch(8, n, seed_index=9)
+    d["l"][1, 2] = d["u"][1, 2] + 1.0                     # l > u
+    d["params"][2, n * n] = np.nan                        # non-finite record
+    d["x0"][3] = 50.0                                     # x0 outside the box
+    d["delta0"][4] = -1.0                                 # automatic initial radius
+    g = gpu_solve(d, n=n)
+    r = oracle_solve(d)
+    np.testing.assert_array_equal(g["status"], r["status"])
+    assert g["status"][1] == native.TRON_BAD_BOUNDS and g["iters"][1] == 0
+    np.testing.assert_array_equal(g["x"][1], d["x0"][1])   # left as given
+    assert g["status"][2] == native.TRON_NONFINITE
+    for p in (0, 3, 4, 5, 6, 7):
+        assert g["status"][p] == 0
+        np.testing.assert_allclose(g["x"][p], r["x"][p], atol=1e-6)
+    # iteration cap
+    g = gpu_solve(d, n=n, max_outer=1, gtol=1e-300)
+    assert np.all(g["status"][[0, 3, 4]] == native.TRON_MAX_ITER)
+    assert np.all(g["iters"][[0, 3, 4]] == 1)
+
+
+def test_empty_batch_is_noop():
+    tb = TronBatch(native.TRON_OBJ_DENSE_QUARTIC, 0, n=8)
+    e = torch.empty(0, dtype=torch.float64, device=DEV)
+    out = tb.solve(e, e, e, e, e)
+    assert tb.last_launches == 0
+    tb.close()
+
+
+def test_full_size_dense_workload_sampled():
+    """10,000 problems, n = 32, in the benchmark's launch configuration; 200 sampled
+    problems re-solved by the oracle one by one; all problems satisfy the invariants."""
+    d = synth.dense_batch(10000, 32, seed_index=1)
+    g = gpu_solve(d, n=32)
+    assert np.all(g["status"] == 0)
+    assert np.all(g["pg"] <= 1e-6)
+    assert np.all(g["x"] >= d["l"]) and np.all(g["x"] <= d["u"])
+    idx = np.random.default_rng(0).choice(10000, 200, replace=False)
+    sub = {k: (v[idx] if isinstance(v, np.ndarray) and v.ndim and v.shape[0] == 10000 else v)
+           for k, v in d.items()}
+    r = oracle_solve(sub)
+    np.testing.assert_allclose(g["x"][idx], r["x"], rtol=0, atol=1e-6)
+    rel = np.abs(g["f"][idx] - r["f"]) / np.maximum(1.0, np.abs(r["f"]))
+    assert rel.max() <= 1e-8
