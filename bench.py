@@ -33,6 +33,23 @@ B_DEFAULT = 10000
 N_VARS = 32
 L2_BYTES = 129 * 2 ** 20
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+# DRAM bytes per launch of the timed kernel from one ncu capture (profiles/
+# tron_dense32_n10000.md: 19.12 MB for 2,000 problems, scaled by 5 to the 10,000-problem
+# launch), valid only for the kernel sources it was taken on.
+TRAFFIC_BYTES_PER_PROBLEM = 19.12e6 / 2000
+TRAFFIC_SOURCES_SHA1 = "bd4d3cac65420469ed74d7f5087a22ed073b3570"
+TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
+
+
+def traffic_per_launch(nprob: int):
+    import hashlib
+    h = hashlib.sha1()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2106_14995_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != TRAFFIC_SOURCES_SHA1:
+        return None  # kernel changed since the counters were taken
+    return TRAFFIC_BYTES_PER_PROBLEM * nprob
 
 
 def parse():
@@ -313,7 +330,7 @@ def main():
         line["roofline"] = {
             "bound": "alu", "kernel": "k_tron_plain<DenseObj<32,32>,32,32>",
             "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic_per_launch(B),
             "flops_per_launch": flops_per_problem * B,
             "launch_ms_median": float(np.median(launch_ms)),
             "note": "FP64 CUDA-core pipe; peak from 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
