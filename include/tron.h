@@ -146,6 +146,31 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
                             double* d_f, double* d_pgnorm, int32_t* d_iters,
                             int32_t* d_status, void* stream);
 
+/* Solve a batch of mixed sizes without allocating device memory.  (The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc — code running while
+ * a CUDA graph is captured, hosts whose device memory all belongs to their own pool
+ * allocator, loops that must not pay an allocation's implicit synchronisation.)
+ *
+ * Same problem layout and device arrays as tron_batch_solve with per-problem sizes
+ * n_host (host array [nprob]); opt may be NULL; the persistent schedule is always used.
+ * The library keeps the size/offset tables, per-class problem lists and work counters
+ * in one fixed device array of about 24 * TRON_NOALLOC_MAX_PROBLEMS bytes (6 MiB)
+ * that every GPU loading the library reserves until the process exits; no call
+ * allocates device memory (the tables are staged in host memory and copied in).
+ *  - nprob > TRON_NOALLOC_MAX_PROBLEMS is rejected with TRON_EINVAL.
+ *  - The first call on a device looks up the array's device address once for that
+ *    device; make that first call before any stream capture begins.
+ *  - Every call uses the same array: the counters are cleared and the tables rewritten
+ *    by each call on `stream`, so calls on one stream are ordered, but calls that
+ *    overlap on the GPU (other streams, other host threads) race and give wrong
+ *    results. */
+#define TRON_NOALLOC_MAX_PROBLEMS 262144
+tron_err_t tron_solve_mixed_noalloc(tron_obj_t kind, int64_t nprob, const int32_t* n_host,
+                                    const tron_options_t* opt, const double* d_params,
+                                    const double* d_lower, const double* d_upper, double* d_x,
+                                    double* d_delta, double* d_f, double* d_pgnorm,
+                                    int32_t* d_iters, int32_t* d_status, void* stream);
+
 /* Number of GPU kernel launches the last tron_batch_solve on this handle enqueued. */
 int32_t tron_batch_last_launches(const tron_batch_t* b);
 

@@ -491,3 +491,177 @@ void tron_batch_destroy(tron_batch_t* b) {
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------------------------------
+// Entry point that allocates nothing on the device.
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being
+// captured, hosts whose device memory is all handed to their own pool allocator, and
+// real-time loops that must not hit the implicit synchronisation of an allocation.
+// tron_solve_mixed_noalloc serves them: it solves a batch of mixed sizes with the
+// persistent kernel, keeping the per-problem size/offset tables, the per-class problem
+// lists and the work counters in the fixed array below instead of in memory it would
+// otherwise allocate.  The array is reserved on every GPU that loads this library and
+// stays there until the process exits.
+// --------------------------------------------------------------------------------------
+namespace xt {
+
+constexpr int64_t kNoAllocMaxProblems = TRON_NOALLOC_MAX_PROBLEMS;
+constexpr size_t kNaCounters = 0;                                   // 8 x uint64
+constexpr size_t kNaN = 256;                                        // int32 [max]
+constexpr size_t kNaPoff = kNaN + 4 * kNoAllocMaxProblems;          // int64 [max]
+constexpr size_t kNaVoff = kNaPoff + 8 * kNoAllocMaxProblems;       // int64 [max]
+constexpr size_t kNaList = kNaVoff + 8 * kNoAllocMaxProblems;       // int32 [max]
+constexpr size_t kNaBytes = kNaList + 4 * kNoAllocMaxProblems;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+static std::mutex g_na_mu;
+static void* g_na_addr[256];  // device address of the array, per device ordinal
+
+// Device address of the array for the current device, looked up once per device.
+static tron_err_t noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  XT_CUDA(cudaGetDevice(&dev));
+  XT_REQUIRE(dev >= 0 && dev < 256, TRON_EUNSUPPORTED, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (g_na_addr[dev] == nullptr) {
+    void* p = nullptr;
+    XT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_na_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_na_addr[dev]);
+  return TRON_OK;
+}
+
+}  // namespace xt
+
+extern "C" tron_err_t tron_solve_mixed_noalloc(
+    tron_obj_t kind, int64_t nprob, const int32_t* n_host, const tron_options_t* opt,
+    const double* d_params, const double* d_lower, const double* d_upper, double* d_x,
+    double* d_delta, double* d_f, double* d_pgnorm, int32_t* d_iters, int32_t* d_status,
+    void* stream) {
+  clear_error();
+  XT_REQUIRE(kind == TRON_OBJ_ACOPF_BRANCH || kind == TRON_OBJ_DENSE_QUARTIC ||
+                 kind == TRON_OBJ_HS45,
+             TRON_EINVAL, "tron_solve_mixed_noalloc: unknown objective kind %d", (int)kind);
+  XT_REQUIRE(nprob >= 0 && nprob <= kNoAllocMaxProblems, TRON_EINVAL,
+             "tron_solve_mixed_noalloc: nprob = %lld exceeds the fixed scratch capacity of "
+             "%lld problems (TRON_NOALLOC_MAX_PROBLEMS); use tron_batch_create/solve",
+             (long long)nprob, (long long)kNoAllocMaxProblems);
+  if (nprob == 0) return TRON_OK;
+  XT_REQUIRE(n_host != nullptr, TRON_EINVAL, "tron_solve_mixed_noalloc: n_host is NULL");
+  XT_REQUIRE(d_lower && d_upper && d_x && d_delta && d_f && d_pgnorm && d_iters && d_status,
+             TRON_EINVAL, "tron_solve_mixed_noalloc: null device array");
+  XT_REQUIRE(d_params || kind == TRON_OBJ_HS45, TRON_EINVAL,
+             "tron_solve_mixed_noalloc: d_params is NULL");
+  tron_options_t o;
+  if (opt) o = *opt;
+  else tron_options_default(&o);
+  tron_err_t e = check_options(&o);
+  if (e != TRON_OK) return e;
+  o.schedule = TRON_SCHED_PERSISTENT;
+  const int sms = device_sm_count();
+  XT_REQUIRE(sms > 0, TRON_ECUDA, "tron_solve_mixed_noalloc: no CUDA device");
+  unsigned char* base = nullptr;
+  e = noalloc_scratch(&base);
+  if (e != TRON_OK) return e;
+
+  // host-side tables (host memory only), then one upload of each into the array
+  const int classes[4] = {4, 8, 16, 32};
+  std::vector<int64_t> poff(nprob), voff(nprob);
+  std::vector<int32_t> lists;
+  lists.reserve(nprob);
+  int64_t start[4] = {0, 0, 0, 0}, count[4] = {0, 0, 0, 0};
+  {
+    int64_t pa = 0, va = 0;
+    for (int64_t p = 0; p < nprob; ++p) {
+      const int c = size_class(kind, n_host[p]);
+      XT_REQUIRE(c > 0, TRON_EUNSUPPORTED,
+                 "tron_solve_mixed_noalloc: problem %lld has unsupported size %d",
+                 (long long)p, n_host[p]);
+      poff[p] = pa;
+      voff[p] = va;
+      pa += record_size(kind, n_host[p]);
+      va += n_host[p];
+      for (int s = 0; s < 4; ++s)
+        if (classes[s] == c) count[s]++;
+    }
+    int64_t at = 0;
+    for (int s = 3; s >= 0; --s) {  // largest class first, as in tron_batch_solve
+      start[s] = at;
+      at += count[s];
+    }
+    lists.resize(nprob);
+    int64_t fill[4] = {0, 0, 0, 0};
+    for (int64_t p = 0; p < nprob; ++p) {
+      const int c = size_class(kind, n_host[p]);
+      for (int s = 0; s < 4; ++s)
+        if (classes[s] == c) lists[start[s] + fill[s]++] = (int32_t)p;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* na_n = reinterpret_cast<int32_t*>(base + kNaN);
+  int64_t* na_poff = reinterpret_cast<int64_t*>(base + kNaPoff);
+  int64_t* na_voff = reinterpret_cast<int64_t*>(base + kNaVoff);
+  int32_t* na_list = reinterpret_cast<int32_t*>(base + kNaList);
+  unsigned long long* na_ctr = reinterpret_cast<unsigned long long*>(base + kNaCounters);
+  // the counters must start at zero on every call; the tables are overwritten in full
+  XT_CUDA(cudaMemsetAsync(na_ctr, 0, 8 * sizeof(unsigned long long), st));
+  XT_CUDA(cudaMemcpyAsync(na_n, n_host, sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
+  XT_CUDA(cudaMemcpyAsync(na_poff, poff.data(), sizeof(int64_t) * nprob,
+                          cudaMemcpyHostToDevice, st));
+  XT_CUDA(cudaMemcpyAsync(na_voff, voff.data(), sizeof(int64_t) * nprob,
+                          cudaMemcpyHostToDevice, st));
+  XT_CUDA(cudaMemcpyAsync(na_list, lists.data(), sizeof(int32_t) * nprob,
+                          cudaMemcpyHostToDevice, st));
+
+  const int wpb = o.warps_per_block ? o.warps_per_block : 4;
+  for (int s = 3; s >= 0; --s) {
+    if (count[s] == 0) continue;
+    const int N = classes[s];
+    const int G = o.group ? o.group : default_group(kind, N);
+    KernelEntry* ke = find_entry(kind, N, G);
+    XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for kind %d, size class %d, group %d",
+               (int)kind, N, G);
+    KArgs a;
+    memset(&a, 0, sizeof(a));
+    a.params = d_params;
+    a.lo = d_lower;
+    a.hi = d_upper;
+    a.x = d_x;
+    a.delta = d_delta;
+    a.f = d_f;
+    a.pg = d_pgnorm;
+    a.iters = d_iters;
+    a.status = d_status;
+    a.nvec = na_n;
+    a.poff = na_poff;
+    a.voff = na_voff;
+    a.plist = na_list + start[s];
+    a.count = count[s];
+    a.n_uniform = 0;
+    a.pstride = 0;
+    a.counter = na_ctr + s;
+    a.opt = o;
+    const size_t smem = (size_t)wpb * ke->warp_doubles * sizeof(double);
+    int occ = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_table_mu);
+      XT_CUDA(cudaFuncSetAttribute(ke->persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+      occ = ke->occupancy[wpb];
+      if (occ == 0) {
+        XT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ke->persistent, wpb * 32,
+                                                              smem));
+        ke->occupancy[wpb] = occ;
+      }
+    }
+    XT_REQUIRE(occ > 0, TRON_EUNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
+    const int64_t per_cta = (int64_t)wpb * ke->probs_per_warp;
+    const int64_t grid = std::min<int64_t>((int64_t)occ * sms, (count[s] + per_cta - 1) / per_cta);
+    void* args[] = {&a};
+    XT_CUDA(cudaLaunchKernel(ke->persistent, dim3((unsigned)grid), dim3(wpb * 32), args, smem, st));
+  }
+  return TRON_OK;
+}

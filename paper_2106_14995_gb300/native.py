@@ -64,6 +64,8 @@ def load(build_if_missing: bool = True):
             "tron_batch_set_options": (I32, [P, C.POINTER(TronOptions)]),
             "tron_batch_solve": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
             "tron_batch_last_launches": (I32, [P]),
+            "tron_solve_mixed_noalloc": (I32, [I32, I64, P, C.POINTER(TronOptions), P, P, P, P,
+                                               P, P, P, P, P, P]),
             "tron_batch_destroy": (None, [P]),
             "tron_last_error": (C.c_char_p, []),
             "tron_version": (C.c_char_p, []),
