@@ -1,0 +1,149 @@
+/*
+ * admm.h -- C ABI of the GPU component ADMM for AC optimal power flow (Sec. 6.1).
+ *
+ * The ACOPF of eq. ac-rectangular is split into generator, branch and bus components
+ * with duplicated linking variables (Sec. 6.1).  Every iteration runs, on the GPU:
+ *   1. generator updates (closed form) in parallel with the branch updates (the
+ *      4-variable NLP of eq. exp-branch with a line-limit penalty, solved by the
+ *      batched trust-region Newton solver of tron.h, warm started), one launch;
+ *   2. bus updates (closed-form equality-constrained QP over the bus copies with the
+ *      power-balance equations), the multiplier update lambda += rho (x - xt) and the
+ *      primal/dual residuals, one launch.
+ * Iterations are captured once into a CUDA graph and replayed.
+ *
+ * Two levels:
+ *  - admm_* : one network (a pool holding exactly one instance).
+ *  - admm_pool_* : a resident pool of many independent instances (continuous
+ *    batching): instances are admitted into free slot ranges while others run, their
+ *    state stays on the device between steps, every step advances all live instances
+ *    with shared launches, and results do not depend on the other residents.
+ *
+ * Conventions as in tron.h: host pointers unless named d_*, errors as tron_err_t with
+ * tron_last_error(), no allocation after *_create, work enqueued on `stream`.
+ *
+ * Pair order of a branch k (from bus i, to bus j), used by every per-branch array of 8:
+ *   p_ij q_ij p_ji q_ji  w_i w_j  theta_i theta_j
+ * branch x = (v_i, v_j, theta_i, theta_j); bus-side flow copies (4): p_ij q_ij p_ji q_ji.
+ */
+#ifndef EXATRON_GB300_ADMM_H
+#define EXATRON_GB300_ADMM_H
+
+#include <stdint.h>
+
+#include "tron.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A network, host arrays (copied at create/add). */
+typedef struct admm_network {
+  int32_t nbus, nbranch, ngen;
+  const int32_t* br_from;   /* [nbranch] bus index of the from end                   */
+  const int32_t* br_to;     /* [nbranch] bus index of the to end                     */
+  const double* br_coef;    /* [nbranch][8] gc_ij bc_ij g_ij b_ij gc_ji bc_ji g_ji b_ji */
+  const double* br_smax2;   /* [nbranch] squared apparent-power limit                */
+  const int32_t* gen_bus;   /* [ngen] */
+  const double* gen_c2;     /* [ngen] cost c2 p^2 + c1 p                             */
+  const double* gen_c1;
+  const double* gen_pmin, *gen_pmax, *gen_qmin, *gen_qmax;  /* [ngen] */
+  const double* bus_pd, *bus_qd;     /* [nbus] loads                                 */
+  const double* bus_gsh, *bus_bsh;   /* [nbus] shunts                                */
+  double rho;        /* penalty of every coupling pair (400 in the workloads)         */
+  double rho_line;   /* line-limit penalty                                            */
+  double vmin, vmax; /* voltage magnitude bounds (theta is bounded by +-2 pi)          */
+} admm_network_t;
+
+/* Host buffers for state transfer (checkpoint / resume).  Sizes as in admm_network_t:
+ * br_x [nbranch][4], br_delta [nbranch], br_lam [nbranch][8], br_val [nbranch][8],
+ * br_tilde [nbranch][4], bus_w [nbus], bus_th [nbus], gen_pq [ngen][2],
+ * gen_lam [ngen][2], gen_tilde [ngen][2]; iteration = iterations completed. */
+typedef struct admm_state_view {
+  double* br_x;
+  double* br_delta;
+  double* br_lam;
+  double* br_val;
+  double* br_tilde;
+  double* bus_w;
+  double* bus_th;
+  double* gen_pq;
+  double* gen_lam;
+  double* gen_tilde;
+  int64_t iteration;
+} admm_state_view_t;
+
+typedef struct admm_pool admm_pool_t;
+typedef admm_pool_t admm_t;
+
+/* ---------------------------------------------------------------- single network */
+
+/* Create the device state of one network (initial point: v = 1, theta = 0, generators
+ * at box midpoints, bus copies equal to the component values, lambda = 0, delta = 1).
+ * opt: TRON options of the branch solves (NULL = defaults). */
+tron_err_t admm_create(admm_t** out, const admm_network_t* net, const tron_options_t* opt,
+                       void* stream);
+
+/* Run n_iters iterations; when h_primal / h_dual are not NULL, synchronise the stream
+ * and return the residuals of the last iteration:
+ *   primal = ||x - xt||_2 over all coupling pairs, dual = rho ||xt - xt_prev||_2. */
+tron_err_t admm_step(admm_t* a, int32_t n_iters, double* h_primal, double* h_dual,
+                     void* stream);
+
+/* Residuals of iterations [first, first + count) (they must be among the last
+ * admm_history_capacity() iterations).  Synchronises the stream. */
+tron_err_t admm_residual_history(admm_t* a, int64_t first, int64_t count, double* h_primal,
+                                 double* h_dual, void* stream);
+
+/* Copy the whole state to / from host buffers (synchronises the stream).  Resuming
+ * from a saved state reproduces the uninterrupted run bit for bit. */
+tron_err_t admm_get_state(admm_t* a, admm_state_view_t* host, void* stream);
+tron_err_t admm_set_state(admm_t* a, const admm_state_view_t* host, void* stream);
+
+/* Status counts (tron_status_t, [6]) of the branch solves of the last iteration. */
+tron_err_t admm_branch_status_counts(admm_t* a, int64_t* h_counts6, void* stream);
+
+int64_t admm_iterations(const admm_t* a);
+int64_t admm_history_capacity(const admm_t* a);
+/* GPU kernel launches one iteration performs (inside the replayed graph). */
+int32_t admm_launches_per_iteration(void);
+void admm_destroy(admm_t* a);
+
+/* ------------------------------------------------- resident pool (continuous batching) */
+
+/* Capacities in slots; instances are placed in contiguous, 128-aligned ranges. */
+tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_branch,
+                            int32_t cap_gen, int32_t cap_instances, int32_t history_len,
+                            const tron_options_t* opt, void* stream);
+
+/* Admit an instance: returns TRON_ENOMEM (and *id = -1) when no free ranges can hold
+ * it — nothing is allocated here, the pool's slots are reused.  The new instance
+ * starts at the initial point and advances with every later admm_pool_step. */
+tron_err_t admm_pool_add(admm_pool_t* p, const admm_network_t* net, int32_t* id,
+                         void* stream);
+
+/* Retire an instance and free its slots (its results should be read first). */
+tron_err_t admm_pool_remove(admm_pool_t* p, int32_t id, void* stream);
+
+/* Advance every live instance by n_iters iterations (shared launches). */
+tron_err_t admm_pool_step(admm_pool_t* p, int32_t n_iters, void* stream);
+
+/* Latest residuals and iteration counts of all instance slots ([cap_instances] each,
+ * iteration = -1 for a free slot).  Synchronises the stream. */
+tron_err_t admm_pool_residuals(admm_pool_t* p, int64_t* h_iter, double* h_primal,
+                               double* h_dual, void* stream);
+
+/* Residual history of one instance, as admm_residual_history. */
+tron_err_t admm_pool_history(admm_pool_t* p, int32_t id, int64_t first, int64_t count,
+                             double* h_primal, double* h_dual, void* stream);
+
+tron_err_t admm_pool_get_state(admm_pool_t* p, int32_t id, admm_state_view_t* host,
+                               void* stream);
+tron_err_t admm_pool_set_state(admm_pool_t* p, int32_t id, const admm_state_view_t* host,
+                               void* stream);
+int32_t admm_pool_live(const admm_pool_t* p);
+void admm_pool_destroy(admm_pool_t* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXATRON_GB300_ADMM_H */

@@ -103,7 +103,8 @@ typedef struct tron_options {
   int32_t group;          /* 0      threads per problem: 0 = library's table, or
                                     1, 2, 4, 8, 16, 32 (must divide the size class)     */
   double ared_guard;      /* 1e-13  rounding guard of the reduction ratio,
-                                    rho = (ared + e) / (pred + e), e = ared_guard*max(1,|f|) */
+                                    rho = (ared + e) / (pred + e), e = ared_guard * max(1, S)
+                                    with S the sum of the magnitudes of the terms of f */
   int32_t schedule;       /* TRON_SCHED_PLAIN                                            */
   int32_t warps_per_block;/* 0      CTA size in warps (0 = library's choice)             */
   int32_t reserved[8];    /* must be zero                                                */

@@ -47,7 +47,7 @@ typedef struct ot_opts {
   double shift_frac;            /* Cholesky shift base, times max |A_ii| */
   int32_t max_shift;            /* Cholesky shift retries */
   int32_t pad0;
-  double ared_guard;            /* rounding guard of the reduction ratio, times max(1,|f|) */
+  double ared_guard;            /* rounding guard of the ratio, times max(1, magnitude of the terms of f) */
 } ot_opts;
 
 typedef struct ot_counters {

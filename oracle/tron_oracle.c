@@ -317,11 +317,11 @@ int ot_steihaug(int m, const double* A, const double* L, const double* bhat, dou
 /* Dense quartic family: params = [Q (n x n, row-major) | c (n) | d (n)],
  * f = 1/2 x'Qx + c'x + sum_i d_i x_i^4. */
 static int eval_dense(int n, const double* P, const double* x, double* f, double* g,
-                      double* H, ot_counters* c) {
+                      double* H, ot_counters* c, double* fscale) {
   const double* Q = P;
   const double* cv = P + (size_t)n * n;
   const double* d = cv + n;
-  double quad = 0.0, lin = 0.0, quart = 0.0;
+  double quad = 0.0, lin = 0.0, quart = 0.0, mag = 0.0;
   for (int i = 0; i < n; i++) {
     double qx = 0.0;
     for (int j = 0; j < n; j++) qx += Q[(size_t)i * n + j] * x[j];
@@ -329,9 +329,11 @@ static int eval_dense(int n, const double* P, const double* x, double* f, double
     lin += cv[i] * x[i];
     double x2 = x[i] * x[i];
     quart += d[i] * x2 * x2;
+    mag += 0.5 * fabs(x[i] * qx) + fabs(cv[i] * x[i]) + fabs(d[i]) * x2 * x2;
     if (g) g[i] = qx + cv[i] + 4.0 * d[i] * x2 * x[i];
   }
   *f = 0.5 * quad + lin + quart;
+  if (fscale) *fscale = mag;
   if (H) {
     for (int i = 0; i < n; i++)
       for (int j = 0; j < n; j++) H[(size_t)i * n + j] = Q[(size_t)i * n + j];
@@ -346,10 +348,12 @@ static int eval_dense(int n, const double* P, const double* x, double* f, double
 }
 
 /* hs45 variant (Sec. 4.2 footnote): f = 120 - prod_i x_i */
-static int eval_hs45(int n, const double* x, double* f, double* g, double* H, ot_counters* c) {
+static int eval_hs45(int n, const double* x, double* f, double* g, double* H, ot_counters* c,
+                     double* fscale) {
   double p = 1.0;
   for (int i = 0; i < n; i++) p *= x[i];
   *f = 120.0 - p;
+  if (fscale) *fscale = 120.0 + fabs(p);
   if (g) {
     for (int i = 0; i < n; i++) {
       double q = 1.0;
@@ -403,7 +407,7 @@ static void branch_pairs(const double* cf, const double* x, double cs, double sn
 /* eq. exp-branch plus the line-limit penalty (rho_l/2) max(0, p^2 + q^2 - smax^2)^2 for
  * both directions, with analytic gradient and Hessian */
 static int eval_branch(const double* P, const double* x, double* f, double* g, double* H,
-                       ot_counters* c) {
+                       ot_counters* c, double* fscale) {
   const double* cf = P;
   const double* lam = P + 8;
   const double* tg = P + 16;
@@ -416,17 +420,35 @@ static int eval_branch(const double* P, const double* x, double* f, double* g, d
   double wR = vi * vj * cs, wI = vi * vj * sn;
   double F[8];
   branch_pairs(cf, x, cs, sn, F);
-  double val = 0.0;
+  /* magnitudes of the terms of each pair quantity, for the rounding scale of f */
+  double M[8];
+  {
+    const double wi = vi * vi, wj = vj * vj;
+    M[0] = fabs(cf[0] * wi) + fabs(cf[2] * wR) + fabs(cf[3] * wI);
+    M[1] = fabs(cf[1] * wi) + fabs(cf[3] * wR) + fabs(cf[2] * wI);
+    M[2] = fabs(cf[4] * wj) + fabs(cf[6] * wR) + fabs(cf[7] * wI);
+    M[3] = fabs(cf[5] * wj) + fabs(cf[7] * wR) + fabs(cf[6] * wI);
+    M[4] = wi;
+    M[5] = wj;
+    M[6] = fabs(x[2]);
+    M[7] = fabs(x[3]);
+  }
+  double val = 0.0, mag = 0.0;
   for (int k = 0; k < 8; k++) {
     double r = F[k] - tg[k];
     val += lam[k] * r + 0.5 * rh[k] * r * r;
+    mag += fabs(lam[k] * r) + 0.5 * rh[k] * r * r + (fabs(lam[k]) + rh[k] * fabs(r)) * M[k];
   }
   for (int dir = 0; dir < 2; dir++) {
     double p = F[2 * dir], q = F[2 * dir + 1];
     double m = p * p + q * q - smax2;
-    if (m > 0.0) val += 0.5 * rhol * m * m;
+    if (m > 0.0) {
+      val += 0.5 * rhol * m * m;
+      mag += 0.5 * rhol * m * m + rhol * m * (p * p + q * q + smax2);
+    }
   }
   *f = val;
+  if (fscale) *fscale = mag;
   if (c) c->flops += 30.0 + 8 * 5.0 + 2 * 9.0;
   if (!g && !H) return 0;
 
@@ -509,21 +531,24 @@ static int eval_branch(const double* P, const double* x, double* f, double* g, d
   return 0;
 }
 
+/* f, gradient, Hessian; *fscale receives the sum of the magnitudes of the terms f is
+ * assembled from (including, for the branch, the first-order effect of the terms of
+ * each flow), the scale of the rounding error of the computed f */
 static int eval_c(int kind, int n, const double* P, const double* x, double* f, double* g,
-                  double* H, ot_counters* c) {
+                  double* H, ot_counters* c, double* fscale) {
   switch (kind) {
-    case OT_OBJ_DENSE: return eval_dense(n, P, x, f, g, H, c);
-    case OT_OBJ_HS45: return eval_hs45(n, x, f, g, H, c);
+    case OT_OBJ_DENSE: return eval_dense(n, P, x, f, g, H, c, fscale);
+    case OT_OBJ_HS45: return eval_hs45(n, x, f, g, H, c, fscale);
     case OT_OBJ_BRANCH:
       if (n != 4) return -1;
-      return eval_branch(P, x, f, g, H, c);
+      return eval_branch(P, x, f, g, H, c, fscale);
     default: return -1;
   }
 }
 
 int ot_eval(int kind, int n, const double* params, const double* x, double* f, double* g,
             double* H) {
-  return eval_c(kind, n, params, x, f, g, H, NULL);
+  return eval_c(kind, n, params, x, f, g, H, NULL, NULL);
 }
 
 static int all_finite(int n, const double* v) {
@@ -571,7 +596,8 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
   }
   /* Alg. 1 REQUIRE: x0 in [l,u]; project it */
   for (int i = 0; i < n; i++) x[i] = proj1(x[i], l[i], u[i]);
-  if (eval_c(kind, n, params, x, &f, g, H, c) != 0) {
+  double fs = 0.0;
+  if (eval_c(kind, n, params, x, &f, g, H, c, &fs) != 0) {
     status = OT_NONFINITE;
     goto out_nopg;
   }
@@ -718,22 +744,25 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
     for (int i = 0; i < n; i++) s[i] = y[i] - x[i];
     gemv(n, H, n, s, Hd, c);
     double qs = dot(n, g, s, c) + 0.5 * dot(n, s, Hd, c);
-    double fy;
-    eval_c(kind, n, params, y, &fy, NULL, NULL, c);
+    double fy, fsy = 0.0;
+    eval_c(kind, n, params, y, &fy, NULL, NULL, c, &fsy);
     c->f_evals++;
     /* rho = ared / pred, both shifted by the rounding level of f (Conn, Gould and
      * Toint, Trust-Region Methods, Sec. 17.4.2) so that reductions below the
-     * precision of f do not decide the step */
+     * precision of f do not decide the step; the level is taken from the magnitude
+     * of the terms f is assembled from, not from |f|, which cancellation can make
+     * much smaller */
     double pred = -qs;
     double ared = f - fy;
-    double fl = o->ared_guard * (fabs(f) > 1.0 ? fabs(f) : 1.0);
+    double fl = o->ared_guard * (fs > 1.0 ? fs : 1.0);
     double rho = (pred > 0.0 && isfinite(fy)) ? (ared + fl) / (pred + fl) : -INFINITY;
     double snorm = nrm2(n, s, c);
     c->flops += 5.0 + n;
     if (rho > o->eta0) {
       for (int i = 0; i < n; i++) x[i] = y[i];
       f = fy;
-      eval_c(kind, n, params, x, &fy, g, H, c);
+      fs = fsy;
+      eval_c(kind, n, params, x, &fy, g, H, c, NULL);
       c->gh_evals++;
       c->accepted++;
       if (!all_finite(n, g) || !all_finite((int)nn, H)) {

@@ -1,0 +1,986 @@
+// admm_kernels.cu -- component ADMM (Sec. 6.1) on the GPU: kernels, resident instance
+// pool and the admm_* / admm_pool_* C ABI.
+//
+// One iteration = two launches, both over the pool's whole capacity:
+//   k_admm_branch_gen : generator updates (closed form) alongside the branch updates
+//                       (the branch NLP of eq. exp-branch solved by the TRON solver of
+//                       tron_solver.cuh, one branch per lane, warm started; the branch
+//                       record is gathered on the fly from the multipliers and the bus
+//                       copies, the pair values at the new point are written back)
+//   k_admm_bus        : per bus, the closed-form equality-constrained QP over its copies
+//                       (power balance, eqs. PowerBalanceReal/Reactive), the multiplier
+//                       update of every pair it owns and the residual partial sums; the
+//                       last CTA to finish reduces each instance's partials in a fixed
+//                       order and appends to its residual history.
+// Slots of free or retired instances carry instance id -1 and are skipped, so the
+// iteration can be captured once into a CUDA graph and replayed while instances come
+// and go.  Every instance occupies 128-aligned slot ranges, so its reductions are
+// identical whether it runs alone or next to others.
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "../../include/admm.h"
+#include "capi_common.h"
+#include "tron_solver.cuh"
+
+namespace xt {
+
+constexpr int kAlign = 128;      // slot alignment of every instance range
+constexpr int kBusThreads = 128; // = kAlign: one bus block never spans two instances
+constexpr int kBranchWarps = 4;  // branch CTA = 4 warps x 32 lanes = 128 branches
+constexpr int kGraphChunk = 8;   // iterations per replayed graph
+constexpr double kTwoPi = 6.283185307179586;
+
+struct PoolDev {
+  // branch slots
+  int32_t* br_from;
+  int32_t* br_to;
+  int32_t* br_inst;
+  double* br_coef;
+  double* br_smax2;
+  double* br_x;
+  double* br_delta;
+  double* br_lam;
+  double* br_val;
+  double* br_tilde;
+  int32_t* br_status;
+  int32_t* br_iters;
+  // generator slots
+  int32_t* gen_bus;
+  int32_t* gen_inst;
+  double* gen_c2;
+  double* gen_c1;
+  double* gen_pmin;
+  double* gen_pmax;
+  double* gen_qmin;
+  double* gen_qmax;
+  double* gen_pq;
+  double* gen_lam;
+  double* gen_tilde;
+  // bus slots
+  int32_t* bus_inst;
+  int32_t* bus_eoff;
+  int32_t* bus_ecnt;
+  int32_t* bus_goff;
+  int32_t* bus_gcnt;
+  double* bus_pd;
+  double* bus_qd;
+  double* bus_gsh;
+  double* bus_bsh;
+  double* bus_w;
+  double* bus_th;
+  int32_t* end_list;  // end id 2 * branch_slot + side, grouped per bus
+  int32_t* gen_list;  // generator slots grouped per bus
+  // instances
+  double* inst_param;  // [cap_inst][4] rho, rho_line, vmin, vmax
+  int32_t* inst_active;
+  int32_t* inst_blk;   // [cap_inst][2] bus-block range
+  int64_t* inst_iter;
+  double* hist;        // [cap_inst][H][2] primal, dual
+  // reduction scratch
+  double* part;        // [bus blocks][2]
+  unsigned int* done;
+  int64_t* lat_iter;   // latest residuals gathered for the host
+  double* lat_res;
+  int32_t cap_br, cap_gen, cap_bus, cap_inst, H;
+};
+
+struct AdmmArgs {
+  PoolDev d;
+  tron_options_t opt;
+  int32_t nbb;    // branch CTAs
+  int32_t ngb;    // generator CTAs
+};
+
+using BranchSolver = Solver<BranchObj, 4, 1>;
+
+__global__ void __launch_bounds__(128) k_admm_branch_gen(const AdmmArgs a) {
+  const PoolDev& d = a.d;
+  if ((int)blockIdx.x < a.nbb) {
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = ((int)blockIdx.x * kBranchWarps + warp) * 32 + lane;
+    if (k >= d.cap_br) return;
+    const int inst = d.br_inst[k];
+    if (inst < 0 || !d.inst_active[inst]) return;
+    const double rho = d.inst_param[4 * inst + 0];
+    const double rhol = d.inst_param[4 * inst + 1];
+    const double vmin = d.inst_param[4 * inst + 2];
+    const double vmax = d.inst_param[4 * inst + 3];
+    BranchSolver sv(a.opt, smem + (size_t)warp * BranchSolver::WARP_DOUBLES);
+    sv.n = 4;
+    sv.obj.n = 4;
+    sv.l[0] = vmin;
+    sv.l[1] = vmin;
+    sv.l[2] = -kTwoPi;
+    sv.l[3] = -kTwoPi;
+    sv.u[0] = vmax;
+    sv.u[1] = vmax;
+    sv.u[2] = kTwoPi;
+    sv.u[3] = kTwoPi;
+    // the branch record: coefficients, multipliers, bus-side copies as targets
+    const int i = d.br_from[k], j = d.br_to[k];
+    bool fin = true;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double c = d.br_coef[8 * (size_t)k + q];
+      const double l = d.br_lam[8 * (size_t)k + q];
+      fin = fin && isfinite(c) && isfinite(l);
+      sv.obj.rec[q] = c;
+      sv.obj.rec[8 + q] = l;
+      sv.obj.rec[24 + q] = rho;
+    }
+    double tg[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tg[q] = d.br_tilde[4 * (size_t)k + q];
+    tg[4] = d.bus_w[i];
+    tg[5] = d.bus_w[j];
+    tg[6] = d.bus_th[i];
+    tg[7] = d.bus_th[j];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      fin = fin && isfinite(tg[q]);
+      sv.obj.rec[16 + q] = tg[q];
+    }
+    sv.obj.rec[32] = d.br_smax2[k];
+    sv.obj.rec[33] = rhol;
+    double x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = d.br_x[4 * (size_t)k + q];
+    double delta = d.br_delta[k];
+    double f, pg;
+    int it;
+    const int st = sv.run(x, delta, f, pg, it, fin);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      d.br_x[4 * (size_t)k + q] = x[q];
+      d.br_val[8 * (size_t)k + q] = sv.obj.Fx[q];
+    }
+    d.br_val[8 * (size_t)k + 4] = x[0] * x[0];
+    d.br_val[8 * (size_t)k + 5] = x[1] * x[1];
+    d.br_val[8 * (size_t)k + 6] = x[2];
+    d.br_val[8 * (size_t)k + 7] = x[3];
+    d.br_delta[k] = delta;
+    d.br_status[k] = st;
+    d.br_iters[k] = it;
+  } else {
+    const int g = ((int)blockIdx.x - a.nbb) * (int)blockDim.x + (int)threadIdx.x;
+    if (g >= d.cap_gen) return;
+    const int inst = d.gen_inst[g];
+    if (inst < 0 || !d.inst_active[inst]) return;
+    const double rho = d.inst_param[4 * inst];
+    const double pt = d.gen_tilde[2 * g], qt = d.gen_tilde[2 * g + 1];
+    const double lp = d.gen_lam[2 * g], lq = d.gen_lam[2 * g + 1];
+    // minimiser of c2 p^2 + c1 p + lp (p - pt) + rho/2 (p - pt)^2 on [pmin, pmax],
+    // and of lq (q - qt) + rho/2 (q - qt)^2 on [qmin, qmax]
+    double p = (rho * pt - lp - d.gen_c1[g]) / (2.0 * d.gen_c2[g] + rho);
+    double q = qt - lq / rho;
+    p = p < d.gen_pmin[g] ? d.gen_pmin[g] : (p > d.gen_pmax[g] ? d.gen_pmax[g] : p);
+    q = q < d.gen_qmin[g] ? d.gen_qmin[g] : (q > d.gen_qmax[g] ? d.gen_qmax[g] : q);
+    d.gen_pq[2 * g] = p;
+    d.gen_pq[2 * g + 1] = q;
+  }
+}
+
+__global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
+  const PoolDev& d = a.d;
+  const int b = (int)blockIdx.x * kBusThreads + (int)threadIdx.x;
+  double pr2 = 0.0, du2 = 0.0;
+  if (b < d.cap_bus) {
+    const int inst = d.bus_inst[b];
+    if (inst >= 0 && d.inst_active[inst]) {
+      const double rho = d.inst_param[4 * inst];
+      const int g0 = d.bus_goff[b], gn = d.bus_gcnt[b];
+      const int e0 = d.bus_eoff[b], en = d.bus_ecnt[b];
+      // a = x + lambda / rho for every copy; balance rows A a - (p_d, q_d)
+      double rhsP = -d.bus_pd[b], rhsQ = -d.bus_qd[b];
+      double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
+      for (int t = 0; t < gn; ++t) {
+        const int g = d.gen_list[g0 + t];
+        rhsP += d.gen_pq[2 * g] + d.gen_lam[2 * g] / rho;
+        rhsQ += d.gen_pq[2 * g + 1] + d.gen_lam[2 * g + 1] / rho;
+        sinv += 1.0 / rho;
+      }
+      for (int t = 0; t < en; ++t) {
+        const int e = d.end_list[e0 + t];
+        const size_t k = (size_t)(e >> 1);
+        const int side = e & 1;
+        const int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
+        const double* val = d.br_val + 8 * k;
+        const double* lam = d.br_lam + 8 * k;
+        rhsP -= val[kp] + lam[kp] / rho;
+        rhsQ -= val[kq] + lam[kq] / rho;
+        sinv += 1.0 / rho;
+        Dw += rho;
+        awn += rho * (val[kw] + lam[kw] / rho);
+        athn += rho * (val[kt] + lam[kt] / rho);
+      }
+      const double gsh = d.bus_gsh[b], bsh = d.bus_bsh[b];
+      const double w_old = d.bus_w[b], th_old = d.bus_th[b];
+      const double aw = Dw > 0.0 ? awn / Dw : w_old;
+      rhsP -= gsh * aw;
+      rhsQ += bsh * aw;
+      double M11 = sinv, M22 = sinv, M12 = 0.0;
+      if (Dw > 0.0) {
+        M11 += gsh * gsh / Dw;
+        M22 += bsh * bsh / Dw;
+        M12 = -gsh * bsh / Dw;
+      }
+      const double det = M11 * M22 - M12 * M12;
+      double mu1 = 0.0, mu2 = 0.0;
+      if (det != 0.0) {
+        mu1 = (M22 * rhsP - M12 * rhsQ) / det;
+        mu2 = (M11 * rhsQ - M12 * rhsP) / det;
+      }
+      const double w_new = Dw > 0.0 ? aw - (-gsh * mu1 + bsh * mu2) / Dw : w_old;
+      const double th_new = Dw > 0.0 ? athn / Dw : th_old;
+      // new copies, multipliers lambda += rho (x - xt), residual sums
+      for (int t = 0; t < gn; ++t) {
+        const int g = d.gen_list[g0 + t];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const double xv = d.gen_pq[2 * g + c];
+          const double lam = d.gen_lam[2 * g + c];
+          const double xt = xv + lam / rho - (c == 0 ? mu1 : mu2) / rho;
+          const double old = d.gen_tilde[2 * g + c];
+          d.gen_tilde[2 * g + c] = xt;
+          d.gen_lam[2 * g + c] = lam + rho * (xv - xt);
+          pr2 += (xv - xt) * (xv - xt);
+          du2 += (xt - old) * (xt - old);
+        }
+      }
+      for (int t = 0; t < en; ++t) {
+        const int e = d.end_list[e0 + t];
+        const size_t k = (size_t)(e >> 1);
+        const int side = e & 1;
+        const int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
+        double* lam = d.br_lam + 8 * k;
+        const double* val = d.br_val + 8 * k;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int kk = c == 0 ? kp : kq;
+          const double xv = val[kk];
+          const double l = lam[kk];
+          const double xt = xv + l / rho + (c == 0 ? mu1 : mu2) / rho;
+          const double old = d.br_tilde[4 * k + kk];
+          d.br_tilde[4 * k + kk] = xt;
+          lam[kk] = l + rho * (xv - xt);
+          pr2 += (xv - xt) * (xv - xt);
+          du2 += (xt - old) * (xt - old);
+        }
+        {
+          const double xv = val[kw];
+          lam[kw] = lam[kw] + rho * (xv - w_new);
+          pr2 += (xv - w_new) * (xv - w_new);
+          du2 += (w_new - w_old) * (w_new - w_old);
+        }
+        {
+          const double xv = val[kt];
+          lam[kt] = lam[kt] + rho * (xv - th_new);
+          pr2 += (xv - th_new) * (xv - th_new);
+          du2 += (th_new - th_old) * (th_new - th_old);
+        }
+      }
+      d.bus_w[b] = w_new;
+      d.bus_th[b] = th_new;
+    }
+  }
+  // block sums in a fixed order: butterfly in each warp, then warp 0..3 in order
+  __shared__ double sp[kBusThreads / 32], sd[kBusThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pr2 += __shfl_xor_sync(0xffffffffu, pr2, o);
+    du2 += __shfl_xor_sync(0xffffffffu, du2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sp[threadIdx.x >> 5] = pr2;
+    sd[threadIdx.x >> 5] = du2;
+  }
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    double p = 0.0, q = 0.0;
+    for (int w = 0; w < kBusThreads / 32; ++w) {
+      p += sp[w];
+      q += sd[w];
+    }
+    d.part[2 * blockIdx.x] = p;
+    d.part[2 * blockIdx.x + 1] = q;
+    __threadfence();
+    const unsigned ticket = atomicAdd(d.done, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // last CTA: per-instance residuals from that instance's blocks, in block order
+  for (int i = threadIdx.x; i < d.cap_inst; i += blockDim.x) {
+    if (!d.inst_active[i]) continue;
+    double p = 0.0, q = 0.0;
+    for (int bk = d.inst_blk[2 * i]; bk < d.inst_blk[2 * i + 1]; ++bk) {
+      p += __ldcg(d.part + 2 * bk);
+      q += __ldcg(d.part + 2 * bk + 1);
+    }
+    const int64_t it = d.inst_iter[i];
+    const size_t slot = ((size_t)i * d.H + (size_t)(it % d.H)) * 2;
+    d.hist[slot] = sqrt(p);
+    d.hist[slot + 1] = d.inst_param[4 * i] * sqrt(q);
+    d.inst_iter[i] = it + 1;
+  }
+  if (threadIdx.x == 0) *d.done = 0u;
+}
+
+// initial point of a newly admitted instance (v = 1, theta = 0, generators at box
+// midpoints, bus copies equal to the component values, lambda = 0, delta = 1)
+__global__ void k_admm_init(const AdmmArgs a, int l0, int l1, int g0, int g1, int b0, int b1) {
+  const PoolDev& d = a.d;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = l0 + t;
+  if (k < l1 && d.br_inst[k] >= 0) {
+    const double* cf = d.br_coef + 8 * (size_t)k;
+    double sn, cs;
+    sincos(0.0, &sn, &cs);
+    const double F[4] = {cf[0] - cf[2] * cs + cf[3] * sn, cf[1] - cf[3] * cs - cf[2] * sn,
+                         cf[4] - cf[6] * cs - cf[7] * sn, cf[5] - cf[7] * cs + cf[6] * sn};
+    const double x0[4] = {1.0, 1.0, 0.0, 0.0};
+    for (int q = 0; q < 4; ++q) {
+      d.br_x[4 * (size_t)k + q] = x0[q];
+      d.br_val[8 * (size_t)k + q] = F[q];
+      d.br_tilde[4 * (size_t)k + q] = F[q];
+    }
+    d.br_val[8 * (size_t)k + 4] = 1.0;
+    d.br_val[8 * (size_t)k + 5] = 1.0;
+    d.br_val[8 * (size_t)k + 6] = 0.0;
+    d.br_val[8 * (size_t)k + 7] = 0.0;
+    for (int q = 0; q < 8; ++q) d.br_lam[8 * (size_t)k + q] = 0.0;
+    d.br_delta[k] = 1.0;
+    d.br_status[k] = 0;
+    d.br_iters[k] = 0;
+  }
+  const int g = g0 + t;
+  if (g < g1 && d.gen_inst[g] >= 0) {
+    const double p = 0.5 * (d.gen_pmin[g] + d.gen_pmax[g]);
+    const double q = 0.5 * (d.gen_qmin[g] + d.gen_qmax[g]);
+    d.gen_pq[2 * g] = p;
+    d.gen_pq[2 * g + 1] = q;
+    d.gen_tilde[2 * g] = p;
+    d.gen_tilde[2 * g + 1] = q;
+    d.gen_lam[2 * g] = 0.0;
+    d.gen_lam[2 * g + 1] = 0.0;
+  }
+  const int b = b0 + t;
+  if (b < b1 && d.bus_inst[b] >= 0) {
+    d.bus_w[b] = 1.0;
+    d.bus_th[b] = 0.0;
+  }
+}
+
+__global__ void k_admm_latest(const PoolDev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.cap_inst) return;
+  if (!d.inst_active[i] || d.inst_iter[i] == 0) {
+    d.lat_iter[i] = d.inst_active[i] ? 0 : -1;
+    d.lat_res[2 * i] = CUDART_NAN;
+    d.lat_res[2 * i + 1] = CUDART_NAN;
+    return;
+  }
+  const int64_t it = d.inst_iter[i];
+  const size_t slot = ((size_t)i * d.H + (size_t)((it - 1) % d.H)) * 2;
+  d.lat_iter[i] = it;
+  d.lat_res[2 * i] = d.hist[slot];
+  d.lat_res[2 * i + 1] = d.hist[slot + 1];
+}
+
+// first-fit allocator of aligned slot ranges
+struct RangeAlloc {
+  std::vector<std::pair<int, int>> free_;  // sorted, disjoint [start, end)
+  void init(int cap) {
+    free_.clear();
+    if (cap > 0) free_.push_back({0, cap});
+  }
+  int take(int n) {  // returns start or -1
+    if (n == 0) return 0;
+    for (size_t i = 0; i < free_.size(); ++i) {
+      if (free_[i].second - free_[i].first >= n) {
+        const int s = free_[i].first;
+        free_[i].first += n;
+        if (free_[i].first == free_[i].second) free_.erase(free_.begin() + i);
+        return s;
+      }
+    }
+    return -1;
+  }
+  void give(int s, int n) {
+    if (n == 0) return;
+    free_.push_back({s, s + n});
+    std::sort(free_.begin(), free_.end());
+    std::vector<std::pair<int, int>> m;
+    for (auto& r : free_) {
+      if (!m.empty() && m.back().second == r.first) m.back().second = r.second;
+      else m.push_back(r);
+    }
+    free_ = m;
+  }
+};
+
+static int align_up(int v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace xt
+
+using namespace xt;
+
+struct admm_pool {
+  PoolDev d;
+  tron_options_t opt;
+  int nbb, ngb, nbusb;
+  RangeAlloc ab, al, ag;
+  struct Inst {
+    bool live;
+    int b0, nb, l0, nl, g0, ng;  // slot starts and sizes (sizes aligned)
+    int nbus, nbranch, ngen;      // true sizes
+  };
+  std::vector<Inst> inst;
+  int live;
+  cudaStream_t cap_stream;
+  cudaGraphExec_t g1, gc;  // 1-iteration and chunk graphs
+  std::vector<void*> allocs;
+};
+
+static tron_err_t pool_alloc(admm_pool* p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 8;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    set_error("admm: cudaMalloc of %zu bytes failed", bytes);
+    return TRON_ENOMEM;
+  }
+  p->allocs.push_back(*ptr);
+  return TRON_OK;
+}
+
+#define PA(field, count)                                                                  \
+  do {                                                                                    \
+    tron_err_t e_ = pool_alloc(p, (void**)&p->d.field, sizeof(*p->d.field) * (size_t)(count)); \
+    if (e_ != TRON_OK) {                                                                  \
+      admm_pool_destroy(p);                                                               \
+      return e_;                                                                          \
+    }                                                                                     \
+  } while (0)
+
+static AdmmArgs make_args(const admm_pool* p) {
+  AdmmArgs a;
+  memset(&a, 0, sizeof(a));
+  a.d = p->d;
+  a.opt = p->opt;
+  a.nbb = p->nbb;
+  a.ngb = p->ngb;
+  return a;
+}
+
+static tron_err_t launch_iteration(admm_pool* p, cudaStream_t st) {
+  AdmmArgs a = make_args(p);
+  const size_t smem = (size_t)kBranchWarps * BranchSolver::WARP_DOUBLES * sizeof(double);
+  void* args[] = {&a};
+  XT_CUDA(cudaLaunchKernel((const void*)k_admm_branch_gen, dim3(p->nbb + p->ngb),
+                           dim3(kBranchWarps * 32), args, smem, st));
+  XT_CUDA(cudaLaunchKernel((const void*)k_admm_bus, dim3(p->nbusb), dim3(kBusThreads), args, 0,
+                           st));
+  return TRON_OK;
+}
+
+static tron_err_t capture(admm_pool* p, int iters, cudaGraphExec_t* out) {
+  cudaGraph_t g;
+  XT_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+  tron_err_t e = TRON_OK;
+  for (int i = 0; i < iters && e == TRON_OK; ++i) e = launch_iteration(p, p->cap_stream);
+  cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+  if (e != TRON_OK) return e;
+  if (ce != cudaSuccess) {
+    set_error("admm: graph capture failed: %s", cudaGetErrorString(ce));
+    return TRON_ECUDA;
+  }
+  ce = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) {
+    set_error("admm: graph instantiation failed: %s", cudaGetErrorString(ce));
+    return TRON_ECUDA;
+  }
+  return TRON_OK;
+}
+
+extern "C" {
+
+int32_t admm_launches_per_iteration(void) { return 2; }
+
+tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_branch,
+                            int32_t cap_gen, int32_t cap_instances, int32_t history_len,
+                            const tron_options_t* opt, void* stream) {
+  clear_error();
+  XT_REQUIRE(out != nullptr, TRON_EINVAL, "admm_pool_create: out is NULL");
+  *out = nullptr;
+  XT_REQUIRE(cap_bus >= 0 && cap_branch >= 0 && cap_gen >= 0 && cap_instances > 0 &&
+                 history_len > 0,
+             TRON_EINVAL, "admm_pool_create: bad capacities");
+  admm_pool* p = new admm_pool();
+  memset(&p->d, 0, sizeof(p->d));
+  p->cap_stream = nullptr;
+  p->g1 = nullptr;
+  p->gc = nullptr;
+  p->live = 0;
+  if (opt) p->opt = *opt;
+  else tron_options_default(&p->opt);
+  p->opt.group = 1;
+  const int cb = align_up(cap_bus), cl = align_up(cap_branch), cg = align_up(cap_gen);
+  p->d.cap_bus = cb;
+  p->d.cap_br = cl;
+  p->d.cap_gen = cg;
+  p->d.cap_inst = cap_instances;
+  p->d.H = history_len;
+  p->nbb = (cl + kBranchWarps * 32 - 1) / (kBranchWarps * 32);
+  p->ngb = (cg + kBranchWarps * 32 - 1) / (kBranchWarps * 32);
+  p->nbusb = std::max(1, (cb + kBusThreads - 1) / kBusThreads);
+  PA(br_from, cl);
+  PA(br_to, cl);
+  PA(br_inst, cl);
+  PA(br_coef, 8 * (size_t)cl);
+  PA(br_smax2, cl);
+  PA(br_x, 4 * (size_t)cl);
+  PA(br_delta, cl);
+  PA(br_lam, 8 * (size_t)cl);
+  PA(br_val, 8 * (size_t)cl);
+  PA(br_tilde, 4 * (size_t)cl);
+  PA(br_status, cl);
+  PA(br_iters, cl);
+  PA(gen_bus, cg);
+  PA(gen_inst, cg);
+  PA(gen_c2, cg);
+  PA(gen_c1, cg);
+  PA(gen_pmin, cg);
+  PA(gen_pmax, cg);
+  PA(gen_qmin, cg);
+  PA(gen_qmax, cg);
+  PA(gen_pq, 2 * (size_t)cg);
+  PA(gen_lam, 2 * (size_t)cg);
+  PA(gen_tilde, 2 * (size_t)cg);
+  PA(bus_inst, cb);
+  PA(bus_eoff, cb);
+  PA(bus_ecnt, cb);
+  PA(bus_goff, cb);
+  PA(bus_gcnt, cb);
+  PA(bus_pd, cb);
+  PA(bus_qd, cb);
+  PA(bus_gsh, cb);
+  PA(bus_bsh, cb);
+  PA(bus_w, cb);
+  PA(bus_th, cb);
+  PA(end_list, 2 * (size_t)cl);
+  PA(gen_list, cg);
+  PA(inst_param, 4 * (size_t)cap_instances);
+  PA(inst_active, cap_instances);
+  PA(inst_blk, 2 * (size_t)cap_instances);
+  PA(inst_iter, cap_instances);
+  PA(hist, 2 * (size_t)cap_instances * history_len);
+  PA(part, 2 * (size_t)p->nbusb);
+  PA(done, 1);
+  PA(lat_iter, cap_instances);
+  PA(lat_res, 2 * (size_t)cap_instances);
+  cudaStream_t st = (cudaStream_t)stream;
+  auto fail = [&](const char* what) {
+    set_error("admm_pool_create: %s failed", what);
+    admm_pool_destroy(p);
+    return TRON_ECUDA;
+  };
+  if (cudaMemsetAsync(p->d.br_inst, 0xFF, sizeof(int32_t) * cl, st) ||
+      cudaMemsetAsync(p->d.gen_inst, 0xFF, sizeof(int32_t) * cg, st) ||
+      cudaMemsetAsync(p->d.bus_inst, 0xFF, sizeof(int32_t) * cb, st) ||
+      cudaMemsetAsync(p->d.bus_ecnt, 0, sizeof(int32_t) * cb, st) ||
+      cudaMemsetAsync(p->d.bus_gcnt, 0, sizeof(int32_t) * cb, st) ||
+      cudaMemsetAsync(p->d.bus_eoff, 0, sizeof(int32_t) * cb, st) ||
+      cudaMemsetAsync(p->d.bus_goff, 0, sizeof(int32_t) * cb, st) ||
+      cudaMemsetAsync(p->d.inst_active, 0, sizeof(int32_t) * cap_instances, st) ||
+      cudaMemsetAsync(p->d.inst_blk, 0, sizeof(int32_t) * 2 * cap_instances, st) ||
+      cudaMemsetAsync(p->d.inst_iter, 0, sizeof(int64_t) * cap_instances, st) ||
+      cudaMemsetAsync(p->d.inst_param, 0, sizeof(double) * 4 * cap_instances, st) ||
+      cudaMemsetAsync(p->d.done, 0, sizeof(unsigned int), st) ||
+      cudaMemsetAsync(p->d.part, 0, sizeof(double) * 2 * p->nbusb, st))
+    return fail("workspace initialisation");
+  const size_t smem = (size_t)kBranchWarps * BranchSolver::WARP_DOUBLES * sizeof(double);
+  if (cudaFuncSetAttribute((const void*)k_admm_branch_gen,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+    return fail("cudaFuncSetAttribute");
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking)) return fail("stream");
+  if (cudaStreamSynchronize(st)) return fail("synchronisation");
+  tron_err_t e = capture(p, 1, &p->g1);
+  if (e == TRON_OK) e = capture(p, kGraphChunk, &p->gc);
+  if (e != TRON_OK) {
+    admm_pool_destroy(p);
+    return e;
+  }
+  p->ab.init(cb);
+  p->al.init(cl);
+  p->ag.init(cg);
+  p->inst.assign(cap_instances, admm_pool::Inst{false, 0, 0, 0, 0, 0, 0, 0, 0, 0});
+  *out = p;
+  return TRON_OK;
+}
+
+tron_err_t admm_pool_add(admm_pool_t* p, const admm_network_t* net, int32_t* id, void* stream) {
+  clear_error();
+  XT_REQUIRE(p && net && id, TRON_EINVAL, "admm_pool_add: null argument");
+  *id = -1;
+  const int nb = net->nbus, nl = net->nbranch, ng = net->ngen;
+  XT_REQUIRE(nb > 0 && nl >= 0 && ng >= 0, TRON_EINVAL, "admm_pool_add: bad sizes");
+  XT_REQUIRE(net->rho > 0.0 && net->vmin <= net->vmax, TRON_EINVAL,
+             "admm_pool_add: need rho > 0 and vmin <= vmax");
+  for (int k = 0; k < nl; ++k)
+    XT_REQUIRE(net->br_from[k] >= 0 && net->br_from[k] < nb && net->br_to[k] >= 0 &&
+                   net->br_to[k] < nb && net->br_from[k] != net->br_to[k],
+               TRON_EINVAL, "admm_pool_add: branch %d has bad end buses", k);
+  for (int g = 0; g < ng; ++g)
+    XT_REQUIRE(net->gen_bus[g] >= 0 && net->gen_bus[g] < nb, TRON_EINVAL,
+               "admm_pool_add: generator %d has a bad bus", g);
+  int slot = -1;
+  for (int i = 0; i < (int)p->inst.size(); ++i)
+    if (!p->inst[i].live) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) {
+    set_error("admm_pool_add: all %d instance slots are live", (int)p->inst.size());
+    return TRON_ENOMEM;
+  }
+  const int anb = align_up(nb), anl = align_up(nl), ang = align_up(ng);
+  const int b0 = p->ab.take(anb);
+  const int l0 = b0 < 0 ? -1 : p->al.take(anl);
+  const int g0 = l0 < 0 ? -1 : p->ag.take(ang);
+  if (b0 < 0 || l0 < 0 || g0 < 0) {
+    if (b0 >= 0) p->ab.give(b0, anb);
+    if (l0 >= 0) p->al.give(l0, anl);
+    set_error("admm_pool_add: no free slot ranges for %d buses, %d branches, %d generators",
+              nb, nl, ng);
+    return TRON_ENOMEM;
+  }
+  // host images of the instance's slot ranges (global slot indices)
+  std::vector<int32_t> bfrom(anl, 0), bto(anl, 0), binst(anl, -1);
+  std::vector<double> coef(8 * (size_t)anl, 0.0), smax2(anl, 0.0);
+  for (int k = 0; k < nl; ++k) {
+    bfrom[k] = b0 + net->br_from[k];
+    bto[k] = b0 + net->br_to[k];
+    binst[k] = slot;
+    for (int q = 0; q < 8; ++q) coef[8 * (size_t)k + q] = net->br_coef[8 * (size_t)k + q];
+    smax2[k] = net->br_smax2[k];
+  }
+  std::vector<int32_t> gbus(ang, 0), ginst(ang, -1);
+  std::vector<double> gc2(ang, 0.0), gc1(ang, 0.0), gpmin(ang, 0.0), gpmax(ang, 0.0),
+      gqmin(ang, 0.0), gqmax(ang, 0.0);
+  for (int g = 0; g < ng; ++g) {
+    gbus[g] = b0 + net->gen_bus[g];
+    ginst[g] = slot;
+    gc2[g] = net->gen_c2[g];
+    gc1[g] = net->gen_c1[g];
+    gpmin[g] = net->gen_pmin[g];
+    gpmax[g] = net->gen_pmax[g];
+    gqmin[g] = net->gen_qmin[g];
+    gqmax[g] = net->gen_qmax[g];
+  }
+  // incidence lists, ends and generators in increasing id per bus
+  std::vector<int32_t> ecnt(anb, 0), gcnt(anb, 0), eoff(anb, 0), goff(anb, 0);
+  for (int k = 0; k < nl; ++k) {
+    ecnt[net->br_from[k]]++;
+    ecnt[net->br_to[k]]++;
+  }
+  for (int g = 0; g < ng; ++g) gcnt[net->gen_bus[g]]++;
+  {
+    int ae = 2 * l0, ag = g0;
+    for (int b = 0; b < anb; ++b) {
+      eoff[b] = ae;
+      goff[b] = ag;
+      ae += ecnt[b];
+      ag += gcnt[b];
+    }
+  }
+  std::vector<int32_t> elist(2 * (size_t)anl, 0), glist(ang, 0);
+  {
+    std::vector<int32_t> fill(anb, 0);
+    for (int e = 0; e < 2 * nl; ++e) {
+      const int k = e / 2;
+      const int bus = (e % 2 == 0) ? net->br_from[k] : net->br_to[k];
+      elist[eoff[bus] - 2 * l0 + fill[bus]++] = 2 * (l0 + k) + (e % 2);
+    }
+    std::fill(fill.begin(), fill.end(), 0);
+    for (int g = 0; g < ng; ++g) {
+      const int bus = net->gen_bus[g];
+      glist[goff[bus] - g0 + fill[bus]++] = g0 + g;
+    }
+  }
+  std::vector<int32_t> binst_bus(anb, -1);
+  std::vector<double> pd(anb, 0.0), qd(anb, 0.0), gsh(anb, 0.0), bsh(anb, 0.0);
+  for (int b = 0; b < nb; ++b) {
+    binst_bus[b] = slot;
+    pd[b] = net->bus_pd[b];
+    qd[b] = net->bus_qd[b];
+    gsh[b] = net->bus_gsh[b];
+    bsh[b] = net->bus_bsh[b];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto up = [&](void* dst, const void* src, size_t bytes) -> bool {
+    return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  bool ok = true;
+  ok = ok && up(p->d.br_from + l0, bfrom.data(), 4 * (size_t)anl);
+  ok = ok && up(p->d.br_to + l0, bto.data(), 4 * (size_t)anl);
+  ok = ok && up(p->d.br_coef + 8 * (size_t)l0, coef.data(), 64 * (size_t)anl);
+  ok = ok && up(p->d.br_smax2 + l0, smax2.data(), 8 * (size_t)anl);
+  ok = ok && up(p->d.gen_bus + g0, gbus.data(), 4 * (size_t)ang);
+  ok = ok && up(p->d.gen_c2 + g0, gc2.data(), 8 * (size_t)ang);
+  ok = ok && up(p->d.gen_c1 + g0, gc1.data(), 8 * (size_t)ang);
+  ok = ok && up(p->d.gen_pmin + g0, gpmin.data(), 8 * (size_t)ang);
+  ok = ok && up(p->d.gen_pmax + g0, gpmax.data(), 8 * (size_t)ang);
+  ok = ok && up(p->d.gen_qmin + g0, gqmin.data(), 8 * (size_t)ang);
+  ok = ok && up(p->d.gen_qmax + g0, gqmax.data(), 8 * (size_t)ang);
+  ok = ok && up(p->d.bus_eoff + b0, eoff.data(), 4 * (size_t)anb);
+  ok = ok && up(p->d.bus_ecnt + b0, ecnt.data(), 4 * (size_t)anb);
+  ok = ok && up(p->d.bus_goff + b0, goff.data(), 4 * (size_t)anb);
+  ok = ok && up(p->d.bus_gcnt + b0, gcnt.data(), 4 * (size_t)anb);
+  ok = ok && up(p->d.bus_pd + b0, pd.data(), 8 * (size_t)anb);
+  ok = ok && up(p->d.bus_qd + b0, qd.data(), 8 * (size_t)anb);
+  ok = ok && up(p->d.bus_gsh + b0, gsh.data(), 8 * (size_t)anb);
+  ok = ok && up(p->d.bus_bsh + b0, bsh.data(), 8 * (size_t)anb);
+  ok = ok && up(p->d.end_list + 2 * (size_t)l0, elist.data(), 8 * (size_t)anl);
+  ok = ok && up(p->d.gen_list + g0, glist.data(), 4 * (size_t)ang);
+  // membership last: the slots join the iteration once everything else is in place
+  ok = ok && up(p->d.br_inst + l0, binst.data(), 4 * (size_t)anl);
+  ok = ok && up(p->d.gen_inst + g0, ginst.data(), 4 * (size_t)ang);
+  ok = ok && up(p->d.bus_inst + b0, binst_bus.data(), 4 * (size_t)anb);
+  const double param[4] = {net->rho, net->rho_line, net->vmin, net->vmax};
+  const int32_t blk[2] = {b0 / kBusThreads, (b0 + anb) / kBusThreads};
+  const int64_t zero64 = 0;
+  ok = ok && up(p->d.inst_param + 4 * (size_t)slot, param, sizeof(param));
+  ok = ok && up(p->d.inst_blk + 2 * (size_t)slot, blk, sizeof(blk));
+  ok = ok && up(p->d.inst_iter + slot, &zero64, sizeof(zero64));
+  if (ok) {
+    AdmmArgs a = make_args(p);
+    const int m = std::max(anl, std::max(ang, anb));
+    k_admm_init<<<(m + 127) / 128, 128, 0, st>>>(a, l0, l0 + anl, g0, g0 + ang, b0, b0 + anb);
+    ok = cudaGetLastError() == cudaSuccess;
+  }
+  const int32_t one = 1;
+  ok = ok && up(p->d.inst_active + slot, &one, sizeof(one));
+  if (!ok) {
+    p->ab.give(b0, anb);
+    p->al.give(l0, anl);
+    p->ag.give(g0, ang);
+    set_error("admm_pool_add: upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return TRON_ECUDA;
+  }
+  p->inst[slot] = admm_pool::Inst{true, b0, anb, l0, anl, g0, ang, nb, nl, ng};
+  p->live++;
+  *id = slot;
+  return TRON_OK;
+}
+
+tron_err_t admm_pool_remove(admm_pool_t* p, int32_t id, void* stream) {
+  clear_error();
+  XT_REQUIRE(p && id >= 0 && id < (int)p->inst.size() && p->inst[id].live, TRON_EINVAL,
+             "admm_pool_remove: %d is not a live instance", id);
+  cudaStream_t st = (cudaStream_t)stream;
+  auto& I = p->inst[id];
+  const int32_t zero = 0;
+  XT_CUDA(cudaMemcpyAsync(p->d.inst_active + id, &zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+  XT_CUDA(cudaMemsetAsync(p->d.br_inst + I.l0, 0xFF, 4 * (size_t)I.nl, st));
+  XT_CUDA(cudaMemsetAsync(p->d.gen_inst + I.g0, 0xFF, 4 * (size_t)I.ng, st));
+  XT_CUDA(cudaMemsetAsync(p->d.bus_inst + I.b0, 0xFF, 4 * (size_t)I.nb, st));
+  XT_CUDA(cudaMemsetAsync(p->d.bus_ecnt + I.b0, 0, 4 * (size_t)I.nb, st));
+  XT_CUDA(cudaMemsetAsync(p->d.bus_gcnt + I.b0, 0, 4 * (size_t)I.nb, st));
+  p->ab.give(I.b0, I.nb);
+  p->al.give(I.l0, I.nl);
+  p->ag.give(I.g0, I.ng);
+  I.live = false;
+  p->live--;
+  return TRON_OK;
+}
+
+tron_err_t admm_pool_step(admm_pool_t* p, int32_t n_iters, void* stream) {
+  clear_error();
+  XT_REQUIRE(p && n_iters >= 0, TRON_EINVAL, "admm_pool_step: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int left = n_iters;
+  while (left >= kGraphChunk) {
+    XT_CUDA(cudaGraphLaunch(p->gc, st));
+    left -= kGraphChunk;
+  }
+  while (left-- > 0) XT_CUDA(cudaGraphLaunch(p->g1, st));
+  return TRON_OK;
+}
+
+tron_err_t admm_pool_residuals(admm_pool_t* p, int64_t* h_iter, double* h_primal,
+                               double* h_dual, void* stream) {
+  clear_error();
+  XT_REQUIRE(p && h_iter && h_primal && h_dual, TRON_EINVAL, "admm_pool_residuals: null");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ci = p->d.cap_inst;
+  k_admm_latest<<<(ci + 127) / 128, 128, 0, st>>>(p->d);
+  XT_CUDA(cudaGetLastError());
+  std::vector<double> res(2 * (size_t)ci);
+  XT_CUDA(cudaMemcpyAsync(h_iter, p->d.lat_iter, 8 * (size_t)ci, cudaMemcpyDeviceToHost, st));
+  XT_CUDA(cudaMemcpyAsync(res.data(), p->d.lat_res, 16 * (size_t)ci, cudaMemcpyDeviceToHost, st));
+  XT_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < ci; ++i) {
+    h_primal[i] = res[2 * i];
+    h_dual[i] = res[2 * i + 1];
+  }
+  return TRON_OK;
+}
+
+tron_err_t admm_pool_history(admm_pool_t* p, int32_t id, int64_t first, int64_t count,
+                             double* h_primal, double* h_dual, void* stream) {
+  clear_error();
+  XT_REQUIRE(p && id >= 0 && id < (int)p->inst.size() && p->inst[id].live, TRON_EINVAL,
+             "admm_pool_history: %d is not a live instance", id);
+  XT_REQUIRE(count >= 0 && first >= 0 && h_primal && h_dual, TRON_EINVAL,
+             "admm_pool_history: bad range");
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t it = 0;
+  XT_CUDA(cudaMemcpyAsync(&it, p->d.inst_iter + id, 8, cudaMemcpyDeviceToHost, st));
+  XT_CUDA(cudaStreamSynchronize(st));
+  XT_REQUIRE(first + count <= it && first >= it - p->d.H, TRON_EINVAL,
+             "admm_pool_history: iterations [%lld, %lld) not in the last %d of %lld",
+             (long long)first, (long long)(first + count), p->d.H, (long long)it);
+  std::vector<double> buf(2 * (size_t)p->d.H);
+  XT_CUDA(cudaMemcpy(buf.data(), p->d.hist + (size_t)id * p->d.H * 2, 16 * (size_t)p->d.H,
+                     cudaMemcpyDeviceToHost));
+  for (int64_t t = 0; t < count; ++t) {
+    const size_t s = (size_t)((first + t) % p->d.H);
+    h_primal[t] = buf[2 * s];
+    h_dual[t] = buf[2 * s + 1];
+  }
+  return TRON_OK;
+}
+
+static tron_err_t state_xfer(admm_pool_t* p, int32_t id, admm_state_view_t* h, bool to_host,
+                             cudaStream_t st) {
+  XT_REQUIRE(p && h && id >= 0 && id < (int)p->inst.size() && p->inst[id].live, TRON_EINVAL,
+             "admm state: %d is not a live instance", id);
+  const auto& I = p->inst[id];
+  const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+  auto x = [&](void* dev, void* host, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return to_host ? cudaMemcpyAsync(host, dev, bytes, kind, st)
+                   : cudaMemcpyAsync(dev, host, bytes, kind, st);
+  };
+  const size_t L = I.nbranch, B = I.nbus, G = I.ngen;
+  XT_CUDA(x(p->d.br_x + 4 * (size_t)I.l0, h->br_x, 32 * L));
+  XT_CUDA(x(p->d.br_delta + I.l0, h->br_delta, 8 * L));
+  XT_CUDA(x(p->d.br_lam + 8 * (size_t)I.l0, h->br_lam, 64 * L));
+  XT_CUDA(x(p->d.br_val + 8 * (size_t)I.l0, h->br_val, 64 * L));
+  XT_CUDA(x(p->d.br_tilde + 4 * (size_t)I.l0, h->br_tilde, 32 * L));
+  XT_CUDA(x(p->d.bus_w + I.b0, h->bus_w, 8 * B));
+  XT_CUDA(x(p->d.bus_th + I.b0, h->bus_th, 8 * B));
+  XT_CUDA(x(p->d.gen_pq + 2 * (size_t)I.g0, h->gen_pq, 16 * G));
+  XT_CUDA(x(p->d.gen_lam + 2 * (size_t)I.g0, h->gen_lam, 16 * G));
+  XT_CUDA(x(p->d.gen_tilde + 2 * (size_t)I.g0, h->gen_tilde, 16 * G));
+  XT_CUDA(x(p->d.inst_iter + id, &h->iteration, 8));
+  XT_CUDA(cudaStreamSynchronize(st));
+  return TRON_OK;
+}
+
+tron_err_t admm_pool_get_state(admm_pool_t* p, int32_t id, admm_state_view_t* host,
+                               void* stream) {
+  clear_error();
+  return state_xfer(p, id, host, true, (cudaStream_t)stream);
+}
+
+tron_err_t admm_pool_set_state(admm_pool_t* p, int32_t id, const admm_state_view_t* host,
+                               void* stream) {
+  clear_error();
+  return state_xfer(p, id, const_cast<admm_state_view_t*>(host), false, (cudaStream_t)stream);
+}
+
+int32_t admm_pool_live(const admm_pool_t* p) { return p ? p->live : 0; }
+
+void admm_pool_destroy(admm_pool_t* p) {
+  if (!p) return;
+  if (p->g1) cudaGraphExecDestroy(p->g1);
+  if (p->gc) cudaGraphExecDestroy(p->gc);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  for (void* a : p->allocs) cudaFree(a);
+  delete p;
+}
+
+// ------------------------------------------------------------------ single network
+tron_err_t admm_create(admm_t** out, const admm_network_t* net, const tron_options_t* opt,
+                       void* stream) {
+  clear_error();
+  XT_REQUIRE(out && net, TRON_EINVAL, "admm_create: null argument");
+  *out = nullptr;
+  admm_pool_t* p = nullptr;
+  tron_err_t e = admm_pool_create(&p, net->nbus, net->nbranch, net->ngen, 1, 1 << 16, opt,
+                                  stream);
+  if (e != TRON_OK) return e;
+  int32_t id = -1;
+  e = admm_pool_add(p, net, &id, stream);
+  if (e != TRON_OK) {
+    admm_pool_destroy(p);
+    return e;
+  }
+  *out = p;
+  return TRON_OK;
+}
+
+tron_err_t admm_step(admm_t* a, int32_t n_iters, double* h_primal, double* h_dual,
+                     void* stream) {
+  tron_err_t e = admm_pool_step(a, n_iters, stream);
+  if (e != TRON_OK || (!h_primal && !h_dual)) return e;
+  int64_t it = 0;
+  double pr = 0.0, du = 0.0;
+  e = admm_pool_residuals(a, &it, &pr, &du, stream);
+  if (e != TRON_OK) return e;
+  if (h_primal) *h_primal = pr;
+  if (h_dual) *h_dual = du;
+  return TRON_OK;
+}
+
+tron_err_t admm_residual_history(admm_t* a, int64_t first, int64_t count, double* h_primal,
+                                 double* h_dual, void* stream) {
+  return admm_pool_history(a, 0, first, count, h_primal, h_dual, stream);
+}
+
+tron_err_t admm_get_state(admm_t* a, admm_state_view_t* host, void* stream) {
+  return admm_pool_get_state(a, 0, host, stream);
+}
+
+tron_err_t admm_set_state(admm_t* a, const admm_state_view_t* host, void* stream) {
+  return admm_pool_set_state(a, 0, host, stream);
+}
+
+tron_err_t admm_branch_status_counts(admm_t* a, int64_t* h_counts6, void* stream) {
+  clear_error();
+  XT_REQUIRE(a && h_counts6 && !a->inst.empty() && a->inst[0].live, TRON_EINVAL,
+             "admm_branch_status_counts: bad argument");
+  const auto& I = a->inst[0];
+  std::vector<int32_t> st(I.nbranch > 0 ? I.nbranch : 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (I.nbranch > 0) {
+    XT_CUDA(cudaMemcpyAsync(st.data(), a->d.br_status + I.l0, 4 * (size_t)I.nbranch,
+                            cudaMemcpyDeviceToHost, s));
+  }
+  XT_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < 6; ++k) h_counts6[k] = 0;
+  for (int k = 0; k < I.nbranch; ++k)
+    if (st[k] >= 0 && st[k] < 6) h_counts6[st[k]]++;
+  return TRON_OK;
+}
+
+int64_t admm_iterations(const admm_t* a) {
+  if (!a) return 0;
+  int64_t it = 0;
+  if (cudaMemcpy(&it, a->d.inst_iter, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return it;
+}
+
+int64_t admm_history_capacity(const admm_t* a) { return a ? a->d.H : 0; }
+
+void admm_destroy(admm_t* a) { admm_pool_destroy(a); }
+
+}  // extern "C"

@@ -4,7 +4,8 @@
 //   SMEM                doubles of per-problem shared memory the evaluator needs
 //   kHasHd              the Hessian is hq(i,j) + [i==j] hd(i)
 //   load(gp, rec, n)    stage the packed record; returns false if it holds a non-finite
-//   eval_f(gp, y)       f(y); caches what the gradient needs
+//   eval_f(gp, y)       f(y); caches what the gradient needs; sets fsc, the sum of the
+//                       magnitudes of the terms f is assembled from (its rounding scale)
 //   grad_hess(gp, x, g) gradient at the point of the last eval_f, Hessian made current
 //   hq(i,j), hd(i)      Hessian entries at the current point
 //   hess_finite(gp)     all Hessian entries finite
@@ -27,6 +28,7 @@ struct DenseObj {
 
   SV<G> Q, hdg, st;
   double c[R], d[R], qy[R];
+  double fsc;
   int n;
 
   __device__ __forceinline__ void bind(SV<G> base) {
@@ -87,12 +89,14 @@ struct DenseObj {
 
   __device__ __forceinline__ double eval_f(const Grp<G>& gp, const double (&y)[R]) {
     qmul(gp, y, qy);
-    double s = 0.0;
+    double s = 0.0, m = 0.0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       double y2 = y[r] * y[r];
       s += y[r] * (0.5 * qy[r] + c[r]) + d[r] * y2 * y2;
+      m += 0.5 * fabs(y[r] * qy[r]) + fabs(c[r] * y[r]) + fabs(d[r]) * y2 * y2;
     }
+    fsc = gp.sum(m);
     return gp.sum(s);
   }
 
@@ -129,6 +133,8 @@ struct BranchObj {
 
   SV<1> rec, H;
   double cs, sn, F[4];
+  double Fx[4];  // flows at the current (accepted) point
+  double fsc;
   int n;
 
   __device__ __forceinline__ void bind(SV<1> base) {
@@ -159,18 +165,32 @@ struct BranchObj {
     F[2] = rec[4] * wj - rec[6] * wR - rec[7] * wI;
     F[3] = rec[5] * wj - rec[7] * wR + rec[6] * wI;
     const double P[8] = {F[0], F[1], F[2], F[3], wi, wj, y[2], y[3]};
-    double val = 0.0;
+    // magnitudes of the terms of each pair quantity (rounding scale of f)
+    const double aR = fabs(wR), aI = fabs(wI);
+    const double M[8] = {fabs(rec[0]) * wi + fabs(rec[2]) * aR + fabs(rec[3]) * aI,
+                         fabs(rec[1]) * wi + fabs(rec[3]) * aR + fabs(rec[2]) * aI,
+                         fabs(rec[4]) * wj + fabs(rec[6]) * aR + fabs(rec[7]) * aI,
+                         fabs(rec[5]) * wj + fabs(rec[7]) * aR + fabs(rec[6]) * aI,
+                         wi, wj, fabs(y[2]), fabs(y[3])};
+    double val = 0.0, mag = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      double r = P[k] - rec[16 + k];
-      val += rec[8 + k] * r + 0.5 * rec[24 + k] * r * r;
+      const double r = P[k] - rec[16 + k];
+      const double lam = rec[8 + k], rho = rec[24 + k];
+      val += lam * r + 0.5 * rho * r * r;
+      mag += fabs(lam * r) + 0.5 * rho * r * r + (fabs(lam) + rho * fabs(r)) * M[k];
     }
     const double smax2 = rec[32], rhol = rec[33];
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
-      double m = F[2 * dir] * F[2 * dir] + F[2 * dir + 1] * F[2 * dir + 1] - smax2;
-      if (m > 0.0) val += 0.5 * rhol * m * m;
+      const double p2q2 = F[2 * dir] * F[2 * dir] + F[2 * dir + 1] * F[2 * dir + 1];
+      const double m = p2q2 - smax2;
+      if (m > 0.0) {
+        val += 0.5 * rhol * m * m;
+        mag += 0.5 * rhol * m * m + rhol * m * (p2q2 + smax2);
+      }
     }
+    fsc = mag;
     return val;
   }
 
@@ -180,6 +200,8 @@ struct BranchObj {
   // multiply the second derivatives of w_i, w_j, wR, wI, and the Gauss-Newton part is
   // the sum of rho_k grad F_k grad F_k'.
   __device__ __forceinline__ void grad_hess(const Grp<1>&, const double (&x)[4], double (&g)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Fx[k] = F[k];
     const double vi = x[0], vj = x[1];
     const double vv = vi * vj;
     const double wR = vv * cs, wI = vv * sn;
@@ -299,6 +321,7 @@ struct Hs45Obj {
 
   SV<1> H;
   double xc[N];
+  double fsc;
   int n;
 
   __device__ __forceinline__ void bind(SV<1> base) { H = base; }
@@ -313,6 +336,7 @@ struct Hs45Obj {
       xc[i] = y[i];
       if (i < n) p *= y[i];
     }
+    fsc = 120.0 + fabs(p);
     return 120.0 - p;
   }
   __device__ __forceinline__ void grad_hess(const Grp<1>&, const double (&)[N], double (&g)[N]) {

@@ -367,6 +367,7 @@ struct Solver {
     for (int r = 0; r < R; ++r) x[r] = P(x[r], r);
     double g[R];
     f = obj.eval_f(gp, x);
+    double fs = obj.fsc;  // rounding scale of f at x
     obj.grad_hess(gp, x, g);
     if (!params_finite || !isfinite(f) || !all_finite(g) || !obj.hess_finite(gp)) {
       pg = isfinite(f) ? pgnorm(x, g) : CUDART_NAN;
@@ -529,15 +530,19 @@ struct Solver {
       hv(s2, Hs2);
       const double qs = dotv(g, s2) + 0.5 * dotv(s2, Hs2);
       const double fy = obj.eval_f(gp, y);
+      const double fsy = obj.fsc;
+      // ratio guarded by the rounding level of f (Conn, Gould and Toint, Trust-Region
+      // Methods, Sec. 17.4.2), measured on the magnitudes of the terms of f
       const double pred = -qs;
       const double ared = f - fy;
-      const double fl = o.ared_guard * fmax(fabs(f), 1.0);
+      const double fl = o.ared_guard * fmax(fs, 1.0);
       const double rho = (pred > 0.0 && isfinite(fy)) ? (ared + fl) / (pred + fl) : -CUDART_INF;
       const double snorm = sqrt(dotv(s2, s2));
       if (rho > o.eta0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = y[r];
         f = fy;
+        fs = fsy;
         obj.grad_hess(gp, x, g);
         if (!all_finite(g) || !obj.hess_finite(gp)) {
           status = TRON_NONFINITE;

@@ -37,6 +37,25 @@ class TronOptions(C.Structure):
     ]
 
 
+class AdmmNetwork(C.Structure):
+    _fields_ = [
+        ("nbus", C.c_int32), ("nbranch", C.c_int32), ("ngen", C.c_int32),
+        ("br_from", C.c_void_p), ("br_to", C.c_void_p), ("br_coef", C.c_void_p),
+        ("br_smax2", C.c_void_p), ("gen_bus", C.c_void_p), ("gen_c2", C.c_void_p),
+        ("gen_c1", C.c_void_p), ("gen_pmin", C.c_void_p), ("gen_pmax", C.c_void_p),
+        ("gen_qmin", C.c_void_p), ("gen_qmax", C.c_void_p), ("bus_pd", C.c_void_p),
+        ("bus_qd", C.c_void_p), ("bus_gsh", C.c_void_p), ("bus_bsh", C.c_void_p),
+        ("rho", C.c_double), ("rho_line", C.c_double), ("vmin", C.c_double),
+        ("vmax", C.c_double),
+    ]
+
+
+class AdmmStateView(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in (
+        "br_x", "br_delta", "br_lam", "br_val", "br_tilde", "bus_w", "bus_th", "gen_pq",
+        "gen_lam", "gen_tilde")] + [("iteration", C.c_int64)]
+
+
 class TronError(RuntimeError):
     pass
 
@@ -69,6 +88,28 @@ def load(build_if_missing: bool = True):
             "tron_batch_destroy": (None, [P]),
             "tron_last_error": (C.c_char_p, []),
             "tron_version": (C.c_char_p, []),
+            "admm_create": (I32, [C.POINTER(P), C.POINTER(AdmmNetwork), C.POINTER(TronOptions),
+                                  P]),
+            "admm_step": (I32, [P, I32, P, P, P]),
+            "admm_residual_history": (I32, [P, I64, I64, P, P, P]),
+            "admm_get_state": (I32, [P, C.POINTER(AdmmStateView), P]),
+            "admm_set_state": (I32, [P, C.POINTER(AdmmStateView), P]),
+            "admm_branch_status_counts": (I32, [P, P, P]),
+            "admm_iterations": (I64, [P]),
+            "admm_history_capacity": (I64, [P]),
+            "admm_launches_per_iteration": (I32, []),
+            "admm_destroy": (None, [P]),
+            "admm_pool_create": (I32, [C.POINTER(P), I32, I32, I32, I32, I32,
+                                       C.POINTER(TronOptions), P]),
+            "admm_pool_add": (I32, [P, C.POINTER(AdmmNetwork), C.POINTER(I32), P]),
+            "admm_pool_remove": (I32, [P, I32, P]),
+            "admm_pool_step": (I32, [P, I32, P]),
+            "admm_pool_residuals": (I32, [P, P, P, P, P]),
+            "admm_pool_history": (I32, [P, I32, I64, I64, P, P, P]),
+            "admm_pool_get_state": (I32, [P, I32, C.POINTER(AdmmStateView), P]),
+            "admm_pool_set_state": (I32, [P, I32, C.POINTER(AdmmStateView), P]),
+            "admm_pool_live": (I32, [P]),
+            "admm_pool_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -1,0 +1,132 @@
+"""GPU component ADMM (Sec. 6.1) against the oracle, checkpoint/resume, and the resident
+pool's independence of its co-residents.  Tolerance on residual trajectories: 1e-6
+relative (the stated target)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_14995_gb300 import synth
+from paper_2106_14995_gb300.admm import Admm, AdmmPool
+
+pytestmark = pytest.mark.gpu
+
+
+def small_net(nb, seed):
+    return synth.network(nb, nchord=max(1, nb // 4), ngen=max(1, nb // 3),
+                         rng=np.random.default_rng(seed))
+
+
+def test_admm_residual_trajectory_matches_oracle():
+    net = small_net(60, 3)
+    K = 12
+    g = Admm(net)
+    g.step(K)
+    hp_g, hd_g = g.history(0, K)
+    o = oracle.Admm(net)
+    hp_o, hd_o = o.run(K, nthreads=4)
+    np.testing.assert_allclose(hp_g, hp_o, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(hd_g, hd_o, rtol=1e-6, atol=0)
+    s = g.get_state()
+    assert s["iteration"] == K
+    for k in ("br_x", "br_val", "br_tilde", "bus_w", "bus_th", "gen_pq", "gen_tilde"):
+        np.testing.assert_allclose(s[k], o.arrays[k], rtol=1e-6, atol=1e-8, err_msg=k)
+    np.testing.assert_allclose(s["br_lam"], o.arrays["br_lam"], rtol=1e-6, atol=1e-5)
+    np.testing.assert_allclose(s["gen_lam"], o.arrays["gen_lam"], rtol=1e-6, atol=1e-5)
+    g.close()
+
+
+def test_admm_larger_network_tracks_oracle():
+    net = small_net(400, 4)
+    K = 6
+    g = Admm(net)
+    g.step(K)
+    hp_g, hd_g = g.history(0, K)
+    hp_o, hd_o = oracle.Admm(net).run(K, nthreads=8)
+    np.testing.assert_allclose(hp_g, hp_o, rtol=1e-6)
+    np.testing.assert_allclose(hd_g, hd_o, rtol=1e-6)
+    counts = g.branch_status_counts()
+    assert counts.sum() == len(net["br_from"])
+    g.close()
+
+
+def test_admm_step_returns_last_residuals_and_counts_iterations():
+    net = small_net(30, 5)
+    g = Admm(net)
+    pr, du = g.step(9)
+    assert g.iterations == 9
+    hp, hd = g.history(8, 1)
+    assert pr == hp[0] and du == hd[0]
+    pr2, du2 = g.step(8)  # one full replayed graph chunk
+    assert g.iterations == 17
+    assert np.isfinite(pr2) and np.isfinite(du2)
+    g.close()
+
+
+def test_admm_checkpoint_resume_is_bitwise():
+    net = small_net(80, 6)
+    g = Admm(net)
+    g.step(7)
+    saved = g.get_state()
+    g.step(5)
+    ref = g.get_state()
+    ref_hist = g.history(7, 5)
+    g2 = Admm(net)
+    g2.set_state(saved)
+    assert g2.iterations == 7
+    g2.step(5)
+    got = g2.get_state()
+    for k, v in ref.items():
+        np.testing.assert_array_equal(got[k], v, err_msg=k)
+    h = g2.history(7, 5)
+    np.testing.assert_array_equal(h[0], ref_hist[0])
+    np.testing.assert_array_equal(h[1], ref_hist[1])
+    g.close()
+    g2.close()
+
+
+def _alone(net, iters):
+    p = AdmmPool(len(net["bus_pd"]) + 256, len(net["br_from"]) + 256,
+                 len(net["gen_bus"]) + 256, 1)
+    i = p.add(net)
+    p.step(iters)
+    st = p.get_state(i)
+    hist = p.history(i, 0, iters)
+    p.close()
+    return st, hist
+
+
+def test_pool_results_identical_alone_and_in_the_mix():
+    nets = [small_net(40, 11), small_net(130, 12), small_net(25, 13), small_net(70, 14)]
+    pool = AdmmPool(4000, 4000, 2000, 4)
+    a = pool.add(nets[0])
+    pool.step(5)
+    b = pool.add(nets[1])          # admitted while a is running
+    pool.step(3)
+    c = pool.add(nets[2])
+    pool.step(9)                   # a: 17, b: 12, c: 9 iterations
+    it, pr, du = pool.residuals()
+    assert it[a] == 17 and it[b] == 12 and it[c] == 9
+    sa, sb, sc = pool.get_state(a), pool.get_state(b), pool.get_state(c)
+    pool.remove(b)                 # free b's slots, admit d into them
+    d = pool.add(nets[3])
+    pool.step(4)                   # a: 21, c: 13, d: 4
+    sa2, sd = pool.get_state(a), pool.get_state(d)
+    for net, st, iters in ((nets[0], sa, 17), (nets[1], sb, 12), (nets[2], sc, 9),
+                           (nets[0], sa2, 21), (nets[3], sd, 4)):
+        ref, _ = _alone(net, iters)
+        for k in ref:
+            np.testing.assert_array_equal(st[k], ref[k], err_msg=k)
+    assert pool.live == 3
+    pool.close()
+
+
+def test_pool_rejects_when_full_and_reuses_slots():
+    pool = AdmmPool(250, 400, 200, 2)  # 256 bus slots after alignment
+    n1 = small_net(100, 21)
+    n2 = small_net(250, 22)  # does not fit next to n1 (bus slots are 128-aligned)
+    i1 = pool.add(n1)
+    assert i1 is not None
+    assert pool.add(n2) is None
+    pool.remove(i1)
+    assert pool.add(n2) is not None
+    pool.close()
