@@ -51,7 +51,7 @@ typedef enum tron_err {
  *     [16:24] targets (bus-side copies) of the same pairs
  *     [24:32] penalties rho of the same pairs
  *     [32]    smax^2        [33] rho_l        [34:36] unused
- * TRON_OBJ_DENSE_QUARTIC (any n <= 32): f = 1/2 x'Qx + c'x + sum_i d_i x_i^4.
+ * TRON_OBJ_DENSE_QUARTIC (any n <= 128): f = 1/2 x'Qx + c'x + sum_i d_i x_i^4.
  *   Record of n*n + 2n doubles: Q (row-major, symmetric), c, d.
  * TRON_OBJ_HS45 (n <= 8): the hs45 variant of Sec. 4.2, f = 120 - prod_i x_i.
  *   No record (d_params may be NULL); bounds are the caller's.
@@ -107,7 +107,9 @@ typedef struct tron_options {
                                     with S the sum of the magnitudes of the terms of f */
   int32_t schedule;       /* TRON_SCHED_PLAIN                                            */
   int32_t warps_per_block;/* 0      CTA size in warps (0 = library's choice)             */
-  int32_t reserved[8];    /* must be zero                                                */
+  int32_t layout;         /* 0      kernel storage variant: 0 = library's choice, else
+                                    1 + bits (bit 0: packed factor, bit 1: Q in global)  */
+  int32_t reserved[7];    /* must be zero                                                */
 } tron_options_t;
 
 typedef struct tron_batch tron_batch_t;
@@ -171,6 +173,22 @@ tron_err_t tron_solve_mixed_noalloc(tron_obj_t kind, int64_t nprob, const int32_
                                     const double* d_lower, const double* d_upper, double* d_x,
                                     double* d_delta, double* d_f, double* d_pgnorm,
                                     int32_t* d_iters, int32_t* d_status, void* stream);
+
+/* Autotuner: for every size class of the batch, time each compiled kernel variant
+ * (group size, storage layout) with 1, 2, 4 and 8 warps per CTA on the first `sample`
+ * problems of the class (plain schedule, inputs read from d_params, d_lower, d_upper,
+ * d_x0, d_delta0, which are not modified) and keep the fastest for later solves with
+ * options.group == 0.  A setup-time call: it allocates and frees temporary device
+ * buffers and synchronises the stream. */
+tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const double* d_lower,
+                               const double* d_upper, const double* d_x0,
+                               const double* d_delta0, int32_t sample, void* stream);
+
+/* Size classes of the batch and the variant each will run with. layout bits: 1 = packed
+ * factor, 2 = Q read from global memory. */
+int32_t tron_batch_buckets(const tron_batch_t* b);
+tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t* N, int32_t* G,
+                                 int32_t* layout, int32_t* warps_per_block, int64_t* count);
 
 /* Number of GPU kernel launches the last tron_batch_solve on this handle enqueued. */
 int32_t tron_batch_last_launches(const tron_batch_t* b);

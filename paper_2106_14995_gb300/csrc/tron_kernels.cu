@@ -31,6 +31,20 @@ void set_error(const char* fmt, ...) {
 }
 void clear_error() { g_err.clear(); }
 
+int device_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return v;
+}
+
+// warps per CTA, reduced until the CTA's shared memory fits the device
+static int fit_wpb(int wpb, int warp_doubles, int optin) {
+  while (wpb > 1 && (size_t)wpb * warp_doubles * sizeof(double) > (size_t)optin) --wpb;
+  return wpb;
+}
+
 int device_sm_count() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -61,9 +75,9 @@ struct KArgs {
   tron_options_t opt;
 };
 
-template <class Obj, int N, int G>
+template <class Obj, int N, int G, bool PK>
 __device__ __forceinline__ void solve_problem(const KArgs& a, int64_t idx, double* wsm) {
-  using S = Solver<Obj, N, G>;
+  using S = Solver<Obj, N, G, PK>;
   constexpr int R = S::R;
   S sv(a.opt, wsm);
   const int64_t q = a.plist ? (int64_t)a.plist[idx] : idx;
@@ -106,21 +120,21 @@ __device__ __forceinline__ void solve_problem(const KArgs& a, int64_t idx, doubl
   }
 }
 
-template <class Obj, int N, int G>
+template <class Obj, int N, int G, bool PK>
 __global__ void __launch_bounds__(256) k_tron_plain(const KArgs a) {
-  using S = Solver<Obj, N, G>;
+  using S = Solver<Obj, N, G, PK>;
   extern __shared__ double smem[];
   const int warp = threadIdx.x >> 5;
   double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int64_t idx = gw * S::PROBS_PER_WARP + (threadIdx.x & 31) / G;
   if (idx >= a.count) return;
-  solve_problem<Obj, N, G>(a, idx, wsm);
+  solve_problem<Obj, N, G, PK>(a, idx, wsm);
 }
 
-template <class Obj, int N, int G>
+template <class Obj, int N, int G, bool PK>
 __global__ void __launch_bounds__(256) k_tron_persistent(const KArgs a) {
-  using S = Solver<Obj, N, G>;
+  using S = Solver<Obj, N, G, PK>;
   extern __shared__ double smem[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -131,14 +145,17 @@ __global__ void __launch_bounds__(256) k_tron_persistent(const KArgs a) {
     base = __shfl_sync(0xffffffffu, base, 0);
     if ((int64_t)base >= a.count) break;
     const int64_t idx = (int64_t)base + lane / G;
-    if (idx < a.count) solve_problem<Obj, N, G>(a, idx, wsm);
+    if (idx < a.count) solve_problem<Obj, N, G, PK>(a, idx, wsm);
     __syncwarp();
   }
 }
 
 // ------------------------------------------------------------------ dispatch table
+// layout bits of a kernel variant: bit 0 = packed factor, bit 1 = Q read from global
+enum { kLayoutPacked = 1, kLayoutQGlobal = 2 };
+
 struct KernelEntry {
-  int kind, N, G;
+  int kind, N, G, layout;
   const void* plain;
   const void* persistent;
   int warp_doubles;
@@ -146,57 +163,76 @@ struct KernelEntry {
   int occupancy[9];  // CTAs per SM by warps per block (cached, 0 = unknown)
 };
 
-template <class Obj, int N, int G>
-static KernelEntry make_entry(int kind) {
-  using S = Solver<Obj, N, G>;
+template <class Obj, int N, int G, bool PK>
+static KernelEntry make_entry(int kind, int layout) {
+  using S = Solver<Obj, N, G, PK>;
   KernelEntry e;
   e.kind = kind;
   e.N = N;
   e.G = G;
-  e.plain = (const void*)k_tron_plain<Obj, N, G>;
-  e.persistent = (const void*)k_tron_persistent<Obj, N, G>;
+  e.layout = layout;
+  e.plain = (const void*)k_tron_plain<Obj, N, G, PK>;
+  e.persistent = (const void*)k_tron_persistent<Obj, N, G, PK>;
   e.warp_doubles = S::WARP_DOUBLES;
   e.probs_per_warp = S::PROBS_PER_WARP;
   for (int i = 0; i < 9; ++i) e.occupancy[i] = 0;
   return e;
 }
 
+// every compiled variant; the first entry of a (kind, N) pair is its default
 static std::vector<KernelEntry>& table() {
   static std::vector<KernelEntry> t = {
-      make_entry<BranchObj, 4, 1>(TRON_OBJ_ACOPF_BRANCH),
-      make_entry<DenseObj<4, 1>, 4, 1>(TRON_OBJ_DENSE_QUARTIC),
-      make_entry<DenseObj<4, 4>, 4, 4>(TRON_OBJ_DENSE_QUARTIC),
-      make_entry<DenseObj<8, 1>, 8, 1>(TRON_OBJ_DENSE_QUARTIC),
-      make_entry<DenseObj<8, 8>, 8, 8>(TRON_OBJ_DENSE_QUARTIC),
-      make_entry<DenseObj<16, 8>, 16, 8>(TRON_OBJ_DENSE_QUARTIC),
-      make_entry<DenseObj<16, 16>, 16, 16>(TRON_OBJ_DENSE_QUARTIC),
-      make_entry<DenseObj<32, 16>, 32, 16>(TRON_OBJ_DENSE_QUARTIC),
-      make_entry<DenseObj<32, 32>, 32, 32>(TRON_OBJ_DENSE_QUARTIC),
-      make_entry<Hs45Obj<8>, 8, 1>(TRON_OBJ_HS45),
+      make_entry<BranchObj, 4, 1, false>(TRON_OBJ_ACOPF_BRANCH, 0),
+      make_entry<DenseObj<4, 4>, 4, 4, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<4, 1>, 4, 1, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<8, 8>, 8, 8, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<8, 1>, 8, 1, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<16, 16>, 16, 16, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<16, 8>, 16, 8, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<32, 32>, 32, 32, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<32, 16>, 32, 16, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<64, 32, true>, 64, 32, true>(TRON_OBJ_DENSE_QUARTIC,
+                                                      kLayoutPacked | kLayoutQGlobal),
+      make_entry<DenseObj<64, 32>, 64, 32, true>(TRON_OBJ_DENSE_QUARTIC, kLayoutPacked),
+      make_entry<DenseObj<128, 32, true>, 128, 32, true>(TRON_OBJ_DENSE_QUARTIC,
+                                                        kLayoutPacked | kLayoutQGlobal),
+      make_entry<Hs45Obj<8>, 8, 1, false>(TRON_OBJ_HS45, 0),
   };
   return t;
 }
 static std::mutex g_table_mu;
 
-// size classes per family and the default group size of each
+// size classes (largest last); a problem of size n runs in the smallest class >= n
+static const int kClasses[] = {4, 8, 16, 32, 64, 128};
+constexpr int kNumClasses = 6;
+
 static int size_class(int kind, int n) {
   if (kind == TRON_OBJ_ACOPF_BRANCH) return n == 4 ? 4 : -1;
   if (kind == TRON_OBJ_HS45) return (n >= 1 && n <= 8) ? 8 : -1;
   if (kind == TRON_OBJ_DENSE_QUARTIC) {
     if (n < 1) return -1;
-    for (int c : {4, 8, 16, 32})
+    for (int c : kClasses)
       if (n <= c) return c;
   }
   return -1;
 }
-static int default_group(int kind, int N) {
-  if (kind == TRON_OBJ_DENSE_QUARTIC) return N <= 8 ? 1 : N;
-  return 1;
+static int class_slot(int c) {
+  for (int s = 0; s < kNumClasses; ++s)
+    if (kClasses[s] == c) return s;
+  return -1;
 }
-static KernelEntry* find_entry(int kind, int N, int G) {
+// default variant of a class, or the first variant with group G when G != 0 and with
+// the storage layout (options.layout - 1) when that option is not 0
+static KernelEntry* find_entry(int kind, int N, int G, int layout_opt = 0) {
   for (auto& e : table())
-    if (e.kind == kind && e.N == N && e.G == G) return &e;
+    if (e.kind == kind && e.N == N && (G == 0 || e.G == G) &&
+        (layout_opt == 0 || e.layout == layout_opt - 1))
+      return &e;
   return nullptr;
+}
+static int default_group(int kind, int N) {
+  KernelEntry* e = find_entry(kind, N, 0);
+  return e ? e->G : 1;
 }
 
 }  // namespace xt
@@ -215,12 +251,18 @@ struct tron_batch {
   struct Bucket {
     int N;
     int64_t count;
-    int32_t* d_list;  // NULL when the bucket is the whole (uniform) batch
+    int32_t* d_list;     // NULL when the bucket is the whole (uniform) batch
+    KernelEntry* tuned;  // variant chosen by tron_batch_autotune (NULL: options/default)
+    int tuned_wpb;
   };
   std::vector<Bucket> buckets;
   unsigned long long* d_counter;  // one work counter per bucket
+  cudaStream_t side[kNumClasses];  // forked streams of the persistent schedule
+  cudaEvent_t ev_fork, ev_join[kNumClasses];
+  int64_t total_n;  // length of the concatenated vectors
   int last_launches;
   int sms;
+  int smem_optin;
 };
 
 static int64_t record_size(int kind, int n) {
@@ -239,6 +281,7 @@ static tron_err_t check_options(const tron_options_t* o) {
              TRON_EINVAL, "options.schedule must be TRON_SCHED_PLAIN or TRON_SCHED_PERSISTENT");
   XT_REQUIRE(o->warps_per_block >= 0 && o->warps_per_block <= 8, TRON_EINVAL,
              "options.warps_per_block must be in [0, 8]");
+  XT_REQUIRE(o->layout >= 0 && o->layout <= 4, TRON_EINVAL, "options.layout must be in [0, 4]");
   return TRON_OK;
 }
 
@@ -302,8 +345,14 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
   b->d_poff = nullptr;
   b->d_voff = nullptr;
   b->d_counter = nullptr;
+  b->ev_fork = nullptr;
+  for (int i = 0; i < kNumClasses; ++i) {
+    b->side[i] = nullptr;
+    b->ev_join[i] = nullptr;
+  }
   b->last_launches = 0;
   b->sms = device_sm_count();
+  b->smem_optin = device_smem_optin();
   auto fail = [&](tron_err_t code) {
     tron_batch_destroy(b);
     return code;
@@ -318,11 +367,11 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
       return fail(TRON_EUNSUPPORTED);
     }
     b->n_uniform = n_uniform;
-    b->buckets.push_back({size_class(kind, n_uniform), nprob, nullptr});
+    b->total_n = nprob * (int64_t)n_uniform;
+    b->buckets.push_back({size_class(kind, n_uniform), nprob, nullptr, nullptr, 0});
   } else {
     std::vector<int64_t> poff(nprob), voff(nprob);
-    std::vector<std::vector<int32_t>> lists(5);
-    const int classes[5] = {4, 8, 16, 32, 0};
+    std::vector<std::vector<int32_t>> lists(kNumClasses);
     int64_t pa = 0, va = 0;
     for (int64_t p = 0; p < nprob; ++p) {
       const int n = n_host[p];
@@ -335,10 +384,9 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
       voff[p] = va;
       pa += record_size(kind, n);
       va += n;
-      int slot = 0;
-      while (classes[slot] != c) ++slot;
-      lists[slot].push_back((int32_t)p);
+      lists[class_slot(c)].push_back((int32_t)p);
     }
+    b->total_n = va;
     if (cudaMalloc(&b->d_n, sizeof(int32_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess ||
         cudaMalloc(&b->d_poff, sizeof(int64_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess ||
         cudaMalloc(&b->d_voff, sizeof(int64_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess) {
@@ -356,9 +404,9 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
       }
     }
     // largest class first: the longest solves start earliest
-    for (int slot = 3; slot >= 0; --slot) {
+    for (int slot = kNumClasses - 1; slot >= 0; --slot) {
       if (lists[slot].empty()) continue;
-      tron_batch::Bucket bk{classes[slot], (int64_t)lists[slot].size(), nullptr};
+      tron_batch::Bucket bk{kClasses[slot], (int64_t)lists[slot].size(), nullptr, nullptr, 0};
       if (cudaMalloc(&bk.d_list, sizeof(int32_t) * lists[slot].size()) != cudaSuccess) {
         set_error("tron_batch_create: cudaMalloc of a problem list failed");
         return fail(TRON_ENOMEM);
@@ -379,10 +427,21 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
     set_error("tron_batch_create: cudaMalloc of work counters failed");
     return fail(TRON_ENOMEM);
   }
+  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    set_error("tron_batch_create: cudaEventCreate failed");
+    return fail(TRON_ECUDA);
+  }
+  for (size_t i = 0; i < b->buckets.size(); ++i) {
+    if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+      set_error("tron_batch_create: stream/event creation failed");
+      return fail(TRON_ECUDA);
+    }
+  }
   // resolve the kernels now so that a bad group option fails here
   for (auto& bk : b->buckets) {
     const int G = o.group ? o.group : default_group(kind, bk.N);
-    if (!find_entry(kind, bk.N, G)) {
+    if (!find_entry(kind, bk.N, G, o.layout)) {
       set_error("tron_batch_create: no kernel for kind %d, size class %d, group %d", (int)kind,
                 bk.N, G);
       return fail(TRON_EUNSUPPORTED);
@@ -399,7 +458,7 @@ tron_err_t tron_batch_set_options(tron_batch_t* b, const tron_options_t* opt) {
   if (e != TRON_OK) return e;
   for (auto& bk : b->buckets) {
     const int G = opt->group ? opt->group : default_group(b->kind, bk.N);
-    XT_REQUIRE(find_entry(b->kind, bk.N, G), TRON_EUNSUPPORTED,
+    XT_REQUIRE(find_entry(b->kind, bk.N, G, opt->layout), TRON_EUNSUPPORTED,
                "no kernel for kind %d, size class %d, group %d", (int)b->kind, bk.N, G);
   }
   b->opt = *opt;
@@ -419,13 +478,30 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
   XT_REQUIRE(d_params || b->kind == TRON_OBJ_HS45, TRON_EINVAL,
              "tron_batch_solve: d_params is NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  const int wpb = b->opt.warps_per_block ? b->opt.warps_per_block : 4;
+  const bool persistent = b->opt.schedule == TRON_SCHED_PERSISTENT;
+  // persistent schedule with several size classes: every class on its own forked
+  // stream, so all classes share the GPU in one pass
+  const bool fork = persistent && b->buckets.size() > 1;
+  if (fork) XT_CUDA(cudaEventRecord(b->ev_fork, st));
   for (size_t bi = 0; bi < b->buckets.size(); ++bi) {
     const auto& bk = b->buckets[bi];
     if (bk.count == 0) continue;
-    const int G = b->opt.group ? b->opt.group : default_group(b->kind, bk.N);
-    KernelEntry* ke = find_entry(b->kind, bk.N, G);
-    XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d group %d", bk.N, G);
+    KernelEntry* ke = nullptr;
+    int wpb = b->opt.warps_per_block ? b->opt.warps_per_block : 4;
+    if (bk.tuned && b->opt.group == 0) {
+      ke = bk.tuned;
+      if (!b->opt.warps_per_block) wpb = bk.tuned_wpb;
+    } else {
+      const int G = b->opt.group ? b->opt.group : default_group(b->kind, bk.N);
+      ke = find_entry(b->kind, bk.N, G, b->opt.layout);
+    }
+    XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d", bk.N);
+    wpb = fit_wpb(wpb, ke->warp_doubles, b->smem_optin);
+    cudaStream_t ls = st;
+    if (fork) {
+      ls = b->side[bi];
+      XT_CUDA(cudaStreamWaitEvent(ls, b->ev_fork, 0));
+    }
     KArgs a;
     memset(&a, 0, sizeof(a));
     a.params = d_params;
@@ -447,13 +523,13 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
     a.counter = b->d_counter + bi;
     a.opt = b->opt;
     const size_t smem = (size_t)wpb * ke->warp_doubles * sizeof(double);
-    const void* fn = (b->opt.schedule == TRON_SCHED_PERSISTENT) ? ke->persistent : ke->plain;
+    const void* fn = persistent ? ke->persistent : ke->plain;
     {
       std::lock_guard<std::mutex> lk(g_table_mu);
       XT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     int64_t grid;
-    if (b->opt.schedule == TRON_SCHED_PERSISTENT) {
+    if (persistent) {
       int occ = 0;
       {
         std::lock_guard<std::mutex> lk(g_table_mu);
@@ -466,22 +542,165 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
       XT_REQUIRE(occ > 0, TRON_EUNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
       const int64_t per_cta = (int64_t)wpb * ke->probs_per_warp;
       grid = std::min<int64_t>((int64_t)occ * b->sms, (bk.count + per_cta - 1) / per_cta);
-      XT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st));
+      XT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), ls));
     } else {
       const int64_t per_cta = (int64_t)wpb * ke->probs_per_warp;
       grid = (bk.count + per_cta - 1) / per_cta;
     }
     void* args[] = {&a};
-    XT_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(wpb * 32), args, smem, st));
+    XT_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(wpb * 32), args, smem, ls));
     b->last_launches++;
+    if (fork) {
+      XT_CUDA(cudaEventRecord(b->ev_join[bi], ls));
+      XT_CUDA(cudaStreamWaitEvent(st, b->ev_join[bi], 0));
+    }
   }
   return TRON_OK;
 }
 
 int32_t tron_batch_last_launches(const tron_batch_t* b) { return b ? b->last_launches : 0; }
 
+int32_t tron_batch_buckets(const tron_batch_t* b) { return b ? (int32_t)b->buckets.size() : 0; }
+
+tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t* N, int32_t* G,
+                                 int32_t* layout, int32_t* warps_per_block, int64_t* count) {
+  clear_error();
+  XT_REQUIRE(b && bucket >= 0 && bucket < (int)b->buckets.size(), TRON_EINVAL,
+             "tron_batch_get_choice: bad bucket");
+  const auto& bk = b->buckets[bucket];
+  KernelEntry* ke = nullptr;
+  int wpb = b->opt.warps_per_block ? b->opt.warps_per_block : 4;
+  if (bk.tuned && b->opt.group == 0) {
+    ke = bk.tuned;
+    if (!b->opt.warps_per_block) wpb = bk.tuned_wpb;
+  } else {
+    ke = find_entry(b->kind, bk.N, b->opt.group ? b->opt.group : default_group(b->kind, bk.N),
+                    b->opt.layout);
+  }
+  XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d", bk.N);
+  wpb = fit_wpb(wpb, ke->warp_doubles, b->smem_optin);
+  if (N) *N = ke->N;
+  if (G) *G = ke->G;
+  if (layout) *layout = ke->layout;
+  if (warps_per_block) *warps_per_block = wpb;
+  if (count) *count = bk.count;
+  return TRON_OK;
+}
+
+tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const double* d_lower,
+                               const double* d_upper, const double* d_x0,
+                               const double* d_delta0, int32_t sample, void* stream) {
+  clear_error();
+  XT_REQUIRE(b && d_lower && d_upper && d_x0 && d_delta0 && sample > 0, TRON_EINVAL,
+             "tron_batch_autotune: bad argument");
+  XT_REQUIRE(d_params || b->kind == TRON_OBJ_HS45, TRON_EINVAL,
+             "tron_batch_autotune: d_params is NULL");
+  if (b->nprob == 0) return TRON_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // scratch outputs for the trial solves (freed before returning)
+  double *xt = nullptr, *dt = nullptr, *ft = nullptr, *pt = nullptr;
+  int32_t *it = nullptr, *stt = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  tron_err_t err = TRON_OK;
+  const size_t nx = (size_t)std::max<int64_t>(b->total_n, 1);
+  const size_t np = (size_t)b->nprob;
+  if (cudaMalloc(&xt, 8 * nx) || cudaMalloc(&dt, 8 * np) || cudaMalloc(&ft, 8 * np) ||
+      cudaMalloc(&pt, 8 * np) || cudaMalloc(&it, 4 * np) || cudaMalloc(&stt, 4 * np) ||
+      cudaEventCreate(&e0) || cudaEventCreate(&e1)) {
+    set_error("tron_batch_autotune: scratch allocation failed");
+    err = TRON_ENOMEM;
+  }
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (err == TRON_OK && (cudaGetDevice(&dev) || cudaGetDeviceProperties(&prop, dev))) {
+    set_error("tron_batch_autotune: device query failed");
+    err = TRON_ECUDA;
+  }
+  for (size_t bi = 0; err == TRON_OK && bi < b->buckets.size(); ++bi) {
+    auto& bk = b->buckets[bi];
+    const int64_t cs = std::min<int64_t>(bk.count, sample);
+    float best = 1e30f;
+    KernelEntry* best_e = nullptr;
+    int best_w = 4;
+    for (auto& ke : table()) {
+      if (ke.kind != b->kind || ke.N != bk.N) continue;
+      for (int wpb : {1, 2, 4, 8}) {
+        const size_t smem = (size_t)wpb * ke.warp_doubles * sizeof(double);
+        if (smem > prop.sharedMemPerBlockOptin) continue;
+        KArgs a;
+        memset(&a, 0, sizeof(a));
+        a.params = d_params;
+        a.lo = d_lower;
+        a.hi = d_upper;
+        a.x = xt;
+        a.delta = dt;
+        a.f = ft;
+        a.pg = pt;
+        a.iters = it;
+        a.status = stt;
+        a.nvec = b->d_n;
+        a.poff = b->d_poff;
+        a.voff = b->d_voff;
+        a.plist = bk.d_list;
+        a.count = cs;
+        a.n_uniform = b->n_uniform;
+        a.pstride = record_size(b->kind, b->n_uniform);
+        a.opt = b->opt;
+        const int64_t per_cta = (int64_t)wpb * ke.probs_per_warp;
+        const int64_t grid = (cs + per_cta - 1) / per_cta;
+        void* args[] = {&a};
+        float ms = 1e30f;
+        bool ok = cudaFuncSetAttribute(ke.plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem) == cudaSuccess;
+        for (int rep = 0; ok && rep < 2; ++rep) {
+          ok = cudaMemcpyAsync(xt, d_x0, 8 * (size_t)b->total_n, cudaMemcpyDeviceToDevice,
+                               st) == cudaSuccess &&
+               cudaMemcpyAsync(dt, d_delta0, 8 * np, cudaMemcpyDeviceToDevice, st) ==
+                   cudaSuccess &&
+               cudaEventRecord(e0, st) == cudaSuccess &&
+               cudaLaunchKernel(ke.plain, dim3((unsigned)grid), dim3(wpb * 32), args, smem,
+                                st) == cudaSuccess &&
+               cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+          if (ok && rep == 1) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        }
+        if (!ok) {
+          cudaGetLastError();  // a variant that cannot launch is skipped
+          continue;
+        }
+        if (ms < best) {
+          best = ms;
+          best_e = &ke;
+          best_w = wpb;
+        }
+      }
+    }
+    if (best_e) {
+      bk.tuned = best_e;
+      bk.tuned_wpb = best_w;
+    }
+  }
+  if (err == TRON_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("tron_batch_autotune: synchronisation failed");
+    err = TRON_ECUDA;
+  }
+  cudaFree(xt);
+  cudaFree(dt);
+  cudaFree(ft);
+  cudaFree(pt);
+  cudaFree(it);
+  cudaFree(stt);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return err;
+}
+
 void tron_batch_destroy(tron_batch_t* b) {
   if (!b) return;
+  for (int i = 0; i < kNumClasses; ++i) {
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   cudaFree(b->d_n);
   cudaFree(b->d_poff);
   cudaFree(b->d_voff);
@@ -507,7 +726,7 @@ void tron_batch_destroy(tron_batch_t* b) {
 namespace xt {
 
 constexpr int64_t kNoAllocMaxProblems = TRON_NOALLOC_MAX_PROBLEMS;
-constexpr size_t kNaCounters = 0;                                   // 8 x uint64
+constexpr size_t kNaCounters = 0;                                   // 8 x uint64 (<= 8 classes)
 constexpr size_t kNaN = 256;                                        // int32 [max]
 constexpr size_t kNaPoff = kNaN + 4 * kNoAllocMaxProblems;          // int64 [max]
 constexpr size_t kNaVoff = kNaPoff + 8 * kNoAllocMaxProblems;       // int64 [max]
@@ -568,11 +787,10 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
   if (e != TRON_OK) return e;
 
   // host-side tables (host memory only), then one upload of each into the array
-  const int classes[4] = {4, 8, 16, 32};
   std::vector<int64_t> poff(nprob), voff(nprob);
   std::vector<int32_t> lists;
   lists.reserve(nprob);
-  int64_t start[4] = {0, 0, 0, 0}, count[4] = {0, 0, 0, 0};
+  int64_t start[kNumClasses] = {0}, count[kNumClasses] = {0};
   {
     int64_t pa = 0, va = 0;
     for (int64_t p = 0; p < nprob; ++p) {
@@ -584,20 +802,18 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
       voff[p] = va;
       pa += record_size(kind, n_host[p]);
       va += n_host[p];
-      for (int s = 0; s < 4; ++s)
-        if (classes[s] == c) count[s]++;
+      count[class_slot(c)]++;
     }
     int64_t at = 0;
-    for (int s = 3; s >= 0; --s) {  // largest class first, as in tron_batch_solve
+    for (int s = kNumClasses - 1; s >= 0; --s) {  // largest class first
       start[s] = at;
       at += count[s];
     }
     lists.resize(nprob);
-    int64_t fill[4] = {0, 0, 0, 0};
+    int64_t fill[kNumClasses] = {0};
     for (int64_t p = 0; p < nprob; ++p) {
-      const int c = size_class(kind, n_host[p]);
-      for (int s = 0; s < 4; ++s)
-        if (classes[s] == c) lists[start[s] + fill[s]++] = (int32_t)p;
+      const int s = class_slot(size_class(kind, n_host[p]));
+      lists[start[s] + fill[s]++] = (int32_t)p;
     }
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -616,14 +832,16 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
   XT_CUDA(cudaMemcpyAsync(na_list, lists.data(), sizeof(int32_t) * nprob,
                           cudaMemcpyHostToDevice, st));
 
-  const int wpb = o.warps_per_block ? o.warps_per_block : 4;
-  for (int s = 3; s >= 0; --s) {
+  const int wpb0 = o.warps_per_block ? o.warps_per_block : 4;
+  const int optin = device_smem_optin();
+  for (int s = kNumClasses - 1; s >= 0; --s) {
     if (count[s] == 0) continue;
-    const int N = classes[s];
+    const int N = kClasses[s];
     const int G = o.group ? o.group : default_group(kind, N);
-    KernelEntry* ke = find_entry(kind, N, G);
+    KernelEntry* ke = find_entry(kind, N, G, o.layout);
     XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for kind %d, size class %d, group %d",
                (int)kind, N, G);
+    const int wpb = fit_wpb(wpb0, ke->warp_doubles, optin);
     KArgs a;
     memset(&a, 0, sizeof(a));
     a.params = d_params;

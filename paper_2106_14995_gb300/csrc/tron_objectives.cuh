@@ -17,38 +17,47 @@ namespace xt {
 
 // ------------------------------------------------------------------ dense quartic
 // f = 1/2 x'Qx + c'x + sum_i d_i x_i^4, record [Q (n x n) | c | d].
-// Q is staged once in shared memory and read by every Hessian product; the Hessian is
-// Q + diag(12 d_i x_i^2), kept as Q plus a diagonal vector.
-template <int N, int G>
+// QG = false: Q is staged once in shared memory (odd stride, conflict-free columns).
+// QG = true: Q stays in global memory (L2-resident while the problem runs) and is read
+// column-wise -- Q(i, j) as Q[j][i], Q being symmetric -- so the lanes of a group read
+// consecutive doubles; used where the factor alone fills the shared memory.
+// The Hessian is Q + diag(12 d_i x_i^2), kept as Q plus a diagonal vector.
+template <int N, int G, bool QG = false>
 struct DenseObj {
   static constexpr int R = N / G;
-  static constexpr int LDQ = (G == 1) ? N : N + 1;  // odd stride: conflict-free columns
-  static constexpr int SMEM = N * LDQ + 2 * N;      // Q, hd, staging
+  static constexpr int LDQ = (G == 1) ? N : N + 1;
+  static constexpr int SMEM = (QG ? 0 : N * LDQ) + 2 * N;  // Q, hd, staging
   static constexpr bool kHasHd = true;
 
   SV<G> Q, hdg, st;
+  const double* __restrict__ qg;
   double c[R], d[R], qy[R];
   double fsc;
   int n;
 
   __device__ __forceinline__ void bind(SV<G> base) {
     Q = base;
-    hdg = base.at(N * LDQ);
-    st = base.at(N * LDQ + N);
+    hdg = base.at(QG ? 0 : N * LDQ);
+    st = base.at((QG ? 0 : N * LDQ) + N);
   }
 
   __device__ __forceinline__ bool load(const Grp<G>& gp, const double* __restrict__ rec, int n_) {
     n = n_;
+    qg = rec;
     bool fin = true;
     const int nn = n * n;
-    // zero the padding rows/columns, then copy Q (coalesced over the group)
-    for (int e = gp.t; e < N * LDQ; e += G) Q[e] = 0.0;
-    gp.sync();
-    for (int e = gp.t; e < nn; e += G) {
-      double v = __ldg(rec + e);
-      fin = fin && isfinite(v);
-      int i = e / n, j = e - i * n;
-      Q[i * LDQ + j] = v;
+    if constexpr (QG) {
+      for (int e = gp.t; e < nn; e += G) fin = fin && isfinite(__ldg(rec + e));
+    } else {
+      // zero the padding rows/columns, then copy Q (coalesced over the group)
+      for (int e = gp.t; e < N * LDQ; e += G) Q[e] = 0.0;
+      gp.sync();
+      for (int e = gp.t; e < nn; e += G) {
+        double v = __ldg(rec + e);
+        fin = fin && isfinite(v);
+        int i = e / n, j = e - i * n;
+        Q[i * LDQ + j] = v;
+      }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -80,7 +89,7 @@ struct DenseObj {
       for (int r = 0; r < R; ++r) {
         const int i = r * G + gp.t;
         double s = 0.0;
-        for (int j = 0; j < n; ++j) s = fma(Q[i * LDQ + j], st[j], s);
+        for (int j = 0; j < n; ++j) s = fma(hq(i, j), st[j], s);
         y[r] = s;
       }
       gp.sync();
@@ -110,7 +119,10 @@ struct DenseObj {
     gp.sync();
   }
 
-  __device__ __forceinline__ double hq(int i, int j) const { return Q[i * LDQ + j]; }
+  __device__ __forceinline__ double hq(int i, int j) const {
+    if constexpr (QG) return (i < n && j < n) ? __ldg(qg + (size_t)j * n + i) : 0.0;
+    else return Q[i * LDQ + j];
+  }
   __device__ __forceinline__ double hd(int i) const { return hdg[i]; }
 
   __device__ __forceinline__ bool hess_finite(const Grp<G>& gp) const {

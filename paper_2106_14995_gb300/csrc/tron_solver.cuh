@@ -28,14 +28,19 @@ namespace xt {
 
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-template <class Obj, int N, int G>
+// PK selects the storage of the factor: false = full N x (N+1) array with L^T mirrored
+// into the upper triangle (Sec. 4.4); true = packed lower triangle, row c at c(c+1)/2,
+// half the shared memory.  Both keep every warp access conflict free: in the packed
+// layout the rows c(c+1)/2 of 16 consecutive c fall on 16 distinct 8-byte banks.
+template <class Obj, int N, int G, bool PK = false>
 struct Solver {
   static constexpr int R = N / G;
   static_assert(N % G == 0, "size class must be a multiple of the group size");
   static constexpr int LD = (G == 1) ? N : N + 1;
+  static constexpr int LSZ = PK ? N * (N + 1) / 2 : N * LD;
   // per-problem shared-memory slice, offsets in doubles
   static constexpr int OFF_L = 0;
-  static constexpr int OFF_VB = OFF_L + N * LD;
+  static constexpr int OFF_VB = OFF_L + LSZ;
   static constexpr int OFF_DINV = OFF_VB + N;
   static constexpr int OFF_FI = OFF_DINV + N;  // N ints (in N double slots)
   static constexpr int OFF_OBJ = OFF_FI + N;
@@ -64,6 +69,16 @@ struct Solver {
     Fi = SV<G, int>{(G == 1) ? reinterpret_cast<int*>(warp_smem + OFF_FI * 32) + gp.lane
                              : reinterpret_cast<int*>(base + OFF_FI)};
     obj.bind(sv.at(OFF_OBJ));
+  }
+
+  // L(c, j), c >= j, in the lower storage
+  __device__ __forceinline__ double& lo(int c, int j) const {
+    return PK ? Lm[c * (c + 1) / 2 + j] : Lm[c * LD + j];
+  }
+  // L(c, j), c >= j, read through the transposed copy (row j of L^T); the same element
+  // as lo(c, j) in the packed layout
+  __device__ __forceinline__ double& mt(int j, int c) const {
+    return PK ? Lm[c * (c + 1) / 2 + j] : Lm[j * LD + c];
   }
 
   // ------------------------------------------------------------------ vector helpers
@@ -143,13 +158,13 @@ struct Solver {
       for (int r = 0; r < R; ++r) {
         const int c = r * G + gp.t;
         if (c >= j && c < m) {
-          double v = Lm[c * LD + j];
-          for (int k = 0; k < j; ++k) v = fma(-Lm[k * LD + c], Lm[k * LD + j], v);
-          Lm[j * LD + c] = v;
+          double v = lo(c, j);
+          for (int k = 0; k < j; ++k) v = fma(-mt(k, c), mt(k, j), v);
+          mt(j, c) = v;
         }
       }
       gp.sync();
-      const double piv = Lm[j * LD + j];
+      const double piv = mt(j, j);
       if (!(piv > 0.0)) {
         gp.sync();
         return false;
@@ -159,13 +174,13 @@ struct Solver {
       for (int r = 0; r < R; ++r) {
         const int c = r * G + gp.t;
         if (c > j && c < m) {
-          const double lcj = Lm[j * LD + c] * rs;
-          Lm[j * LD + c] = lcj;
-          Lm[c * LD + j] = lcj;
+          const double lcj = mt(j, c) * rs;
+          mt(j, c) = lcj;
+          if (!PK) lo(c, j) = lcj;
         }
       }
       if (gp.t == (j & (G - 1))) {
-        Lm[j * LD + j] = piv * rs;
+        mt(j, j) = piv * rs;
         dinv[j] = rs;
       }
       gp.sync();
@@ -199,10 +214,10 @@ struct Solver {
         const int c = r * G + gp.t;
         if (c < m) {
           const int i = Fi[c];
-          for (int d = 0; d < c; ++d) Lm[c * LD + d] = obj.hq(i, Fi[d]);
+          for (int d = 0; d < c; ++d) lo(c, d) = obj.hq(i, Fi[d]);
           double a = obj.hq(i, i);
           if (Obj::kHasHd) a = a + obj.hd(i);
-          Lm[c * LD + c] = a + alpha;
+          lo(c, c) = a + alpha;
         }
       }
       gp.sync();
@@ -224,7 +239,7 @@ struct Solver {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int c = r * G + gp.t;
-          if (c > j && c < m) b[r] = fma(-Lm[j * LD + c], yj, b[r]);
+          if (c > j && c < m) b[r] = fma(-mt(j, c), yj, b[r]);
         }
       }
     }
@@ -242,7 +257,7 @@ struct Solver {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int c = r * G + gp.t;
-          if (c < j) z[r] = fma(-Lm[j * LD + c], zj, z[r]);
+          if (c < j) z[r] = fma(-lo(j, c), zj, z[r]);
         }
       }
     }

@@ -33,7 +33,7 @@ class TronOptions(C.Structure):
         ("sigma3", C.c_double), ("delta_max", C.c_double), ("delta_min_rel", C.c_double),
         ("cg_rtol", C.c_double), ("shift_frac", C.c_double), ("max_shift", C.c_int32),
         ("group", C.c_int32), ("ared_guard", C.c_double), ("schedule", C.c_int32),
-        ("warps_per_block", C.c_int32), ("reserved", C.c_int32 * 8),
+        ("warps_per_block", C.c_int32), ("layout", C.c_int32), ("reserved", C.c_int32 * 7),
     ]
 
 
@@ -83,6 +83,9 @@ def load(build_if_missing: bool = True):
             "tron_batch_set_options": (I32, [P, C.POINTER(TronOptions)]),
             "tron_batch_solve": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
             "tron_batch_last_launches": (I32, [P]),
+            "tron_batch_autotune": (I32, [P, P, P, P, P, P, I32, P]),
+            "tron_batch_buckets": (I32, [P]),
+            "tron_batch_get_choice": (I32, [P, I32, P, P, P, P, P]),
             "tron_solve_mixed_noalloc": (I32, [I32, I64, P, C.POINTER(TronOptions), P, P, P, P,
                                                P, P, P, P, P, P]),
             "tron_batch_destroy": (None, [P]),

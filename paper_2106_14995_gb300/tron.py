@@ -66,6 +66,25 @@ class TronBatch:
             "tron_batch_solve")
         return dict(x=x, delta=delta, f=f, pg=pg, iters=iters, status=status)
 
+    def autotune(self, params, lower, upper, x0, delta0, sample: int = 8192,
+                 stream=None) -> list:
+        """Time every kernel variant per size class on a sample; keep the fastest."""
+        nt.check(self._lib.tron_batch_autotune(
+            self._h, nt.ptr(params), nt.ptr(lower), nt.ptr(upper), nt.ptr(x0), nt.ptr(delta0),
+            int(sample), nt.stream_handle(stream)), "tron_batch_autotune")
+        return self.choices()
+
+    def choices(self) -> list:
+        out = []
+        for bi in range(int(self._lib.tron_batch_buckets(self._h))):
+            v = [C.c_int32() for _ in range(4)]
+            cnt = C.c_int64()
+            nt.check(self._lib.tron_batch_get_choice(self._h, bi, *[C.byref(x) for x in v],
+                                                     C.byref(cnt)), "tron_batch_get_choice")
+            out.append(dict(N=v[0].value, group=v[1].value, layout=v[2].value,
+                            warps_per_block=v[3].value, count=cnt.value))
+        return out
+
     @property
     def last_launches(self) -> int:
         return int(self._lib.tron_batch_last_launches(self._h))

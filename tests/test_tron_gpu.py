@@ -64,9 +64,9 @@ def test_dense_n32_parity_ragged():
     assert np.mean(g["iters"] == r["iters"]) >= 0.95
 
 
-@pytest.mark.parametrize("n", [1, 3, 4, 5, 7, 8, 12, 16, 20, 31, 32])
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 7, 8, 12, 16, 20, 31, 32, 33, 48, 64, 100, 128])
 def test_dense_sizes(n):
-    d = synth.dense_batch(97, n, seed_index=20 + n)
+    d = synth.dense_batch(97 if n <= 32 else 41, n, seed_index=20 + n)
     g = gpu_solve(d, n=n)
     r = oracle_solve(d)
     assert_convex_parity(g, r, d["l"], d["u"])
@@ -77,6 +77,16 @@ def test_dense_sizes(n):
 def test_dense_group_mappings(n, group):
     d = synth.dense_batch(133, n, seed_index=40 + n)
     g = gpu_solve(d, n=n, group=group)
+    r = oracle_solve(d)
+    assert_convex_parity(g, r, d["l"], d["u"])
+
+
+@pytest.mark.parametrize("n,layout", [(64, 2), (64, 4), (128, 4), (100, 4)])
+def test_dense_large_layouts(n, layout):
+    # layout option = 1 + bits: 2 = packed factor with Q in shared memory,
+    # 4 = packed factor with Q read from global memory
+    d = synth.dense_batch(37, n, seed_index=60 + n)
+    g = gpu_solve(d, n=n, layout=layout)
     r = oracle_solve(d)
     assert_convex_parity(g, r, d["l"], d["u"])
 
@@ -119,6 +129,33 @@ def test_uneven_sizes_one_batch():
     assert g["launches"] == len(classes)   # one launch per size class
     assert np.all(g["status"] == 0) and np.all(r["status"] == 0)
     np.testing.assert_allclose(g["x"], r["x"], rtol=0, atol=1e-6)
+
+
+def test_uneven_full_size_range_persistent_and_autotuned():
+    d = synth.uneven_batch(900, seed_index=3)      # n in {4, 6, 8, 16, 32, 64, 128}
+    nv = d["nvec"]
+    plain = gpu_solve(d, n_list=nv)
+    pers = gpu_solve(d, n_list=nv, schedule=native.TRON_SCHED_PERSISTENT)
+    for k in ("x", "f", "pg", "iters", "status", "delta"):
+        np.testing.assert_array_equal(plain[k], pers[k])
+    assert pers["launches"] == len({min(c for c in (4, 8, 16, 32, 64, 128) if n <= c)
+                                    for n in nv.tolist()})
+    r = oracle_solve(d, n_list=nv)
+    assert np.all(plain["status"] == 0) and np.all(r["status"] == 0)
+    np.testing.assert_allclose(plain["x"], r["x"], rtol=0, atol=1e-6)
+    # autotuned variants: same solutions within the tolerance
+    tb = TronBatch(2, nv.size, n_list=nv, opts=options(schedule=native.TRON_SCHED_PERSISTENT))
+    P, L, U, X0, D0 = (_t(d["params"]), _t(d["l"]), _t(d["u"]), _t(d["x0"]), _t(d["delta0"]))
+    ch = tb.autotune(P, L, U, X0, D0, sample=256)
+    assert [c["N"] for c in ch] == sorted({c["N"] for c in ch}, reverse=True)
+    assert all(c["warps_per_block"] in (1, 2, 3, 4, 5, 6, 7, 8) for c in ch)
+    np.testing.assert_array_equal(X0.cpu().numpy(), d["x0"])   # inputs untouched
+    x, de = X0.clone(), D0.clone()
+    out = tb.solve(P, L, U, x, de)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    np.testing.assert_allclose(x.cpu().numpy(), r["x"], rtol=0, atol=1e-6)
+    tb.close()
 
 
 def test_persistent_equals_plain_bitwise():
