@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batch", type=int, default=B_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ADMM, uneven-size and serving workloads")
+    ap.add_argument("--admm-iters", type=int, default=1000)
+    ap.add_argument("--serve-seconds", type=float, default=0.25)
+    ap.add_argument("--serve-max-iters", type=int, default=200)
     return ap.parse_args()
 
 
@@ -183,6 +188,111 @@ def cpu_baseline(d, budget_s=12.0):
     return ({"value": B * reps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
              "sample": f"the full {B}-problem batch solved {reps} time(s) on {cores} threads"},
             flops / B, r)
+
+
+# ---------------------------------------------------------------- extra workloads
+def bench_admm(args, dev):
+    """Component ADMM on a 10,000-bus network (13,000 branches, 3,000 generators):
+    ADMM iterations/s over args.admm_iters iterations (two launches per iteration,
+    replayed CUDA graphs), plus the oracle on the host cores for a few iterations."""
+    import torch
+    import oracle
+    from paper_2106_14995_gb300 import synth
+    from paper_2106_14995_gb300.admm import Admm
+    net = synth.network(10000, 3000, 3000, seed_index=2)
+    a = Admm(net)
+    a.step(16)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    pr, du = a.step(args.admm_iters)
+    dt = time.perf_counter() - t0
+    counts = a.branch_status_counts().tolist()
+    a.close()
+    cores = os.cpu_count() or 1
+    o = oracle.Admm(net)
+    t1 = time.perf_counter()
+    k = 0
+    while k < 3 or (time.perf_counter() - t1 < 4.0 and k < 20):
+        o.run(1, nthreads=cores)
+        k += 1
+    cpu = k / (time.perf_counter() - t1)
+    return {"value": args.admm_iters / dt, "unit": "ADMM iters/s",
+            "workload": "10,000 buses, 13,000 branches, 3,000 generators, rho=400",
+            "iterations": args.admm_iters, "ms_per_iter": dt / args.admm_iters * 1e3,
+            "gpu_launches": 2 * args.admm_iters, "final_primal": pr, "final_dual": du,
+            "branch_status_last_iter": counts,
+            "cpu_baseline": {"value": cpu, "unit": "ADMM iters/s", "cores": cores,
+                             "kind": "oracle", "sample": f"{k} iterations from the start"}}
+
+
+def bench_uneven(args, dev):
+    """100,000 dense problems, n in {4,...,128} with probabilities (0.4, ..., 0.02):
+    plain schedule (one launch per size class, in turn), persistent schedule (all
+    classes concurrently, device work counters) and persistent after autotuning."""
+    import torch
+    from paper_2106_14995_gb300 import native, synth
+    from paper_2106_14995_gb300.tron import TronBatch, options
+    d = synth.uneven_batch(100000, seed_index=3)
+    nv = d["nvec"]
+    B = nv.size
+
+    def t(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    P, L, U, X0, D0 = t(d["params"]), t(d["l"]), t(d["u"]), t(d["x0"]), t(d["delta0"])
+    res = {}
+    for name, sched, tune in (("plain", native.TRON_SCHED_PLAIN, False),
+                              ("persistent", native.TRON_SCHED_PERSISTENT, False),
+                              ("persistent_autotuned", native.TRON_SCHED_PERSISTENT, True)):
+        tb = TronBatch(2, B, n_list=nv, opts=options(schedule=sched))
+        if tune:
+            tb.autotune(P, L, U, X0, D0, sample=8192)
+        ts = []
+        for rep in range(4):
+            x, de = X0.clone(), D0.clone()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = tb.solve(P, L, U, x, de)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            if rep:
+                ts.append(e0.elapsed_time(e1))
+        ok = bool((out["status"].cpu().numpy() == 0).all())
+        res[name] = {"value": B / (np.median(ts) * 1e-3), "unit": UNIT,
+                     "ms": float(np.median(ts)), "launches": tb.last_launches,
+                     "all_converged": ok, "choices": tb.choices()}
+        tb.close()
+    res["workload"] = "100,000 dense problems, n in {4,6,8,16,32,64,128}"
+    return res
+
+
+def bench_serving(args, dev):
+    """Poisson arrivals (200/s for args.serve_seconds) of independent ADMM instances,
+    bus counts log-uniform in [500, 20000] (branches 1.3x, generators 0.3x), load
+    scaling U[0.8, 1.2]; served with continuous batching until primal and dual
+    residuals <= 1e-4 or args.serve_max_iters iterations, against the same requests
+    solved one at a time."""
+    from paper_2106_14995_gb300 import synth
+    from paper_2106_14995_gb300.serving import AdmmServer, serial_plain, summarize
+    specs = synth.serving_stream(duration_s=args.serve_seconds, rate_hz=200.0)
+    reqs = [dict(id=k, t=s["t"], net=synth.instance_network(s)) for k, s in enumerate(specs)]
+    nb = sum(r["net"]["nbus"] for r in reqs)
+    nl = sum(len(r["net"]["br_from"]) for r in reqs)
+    ng = sum(len(r["net"]["gen_bus"]) for r in reqs)
+    n = len(reqs)
+    srv = AdmmServer(nb + 128 * n, nl + 128 * n, ng + 128 * n, n, chunk=10, tol=1e-4,
+                     max_iters=args.serve_max_iters)
+    served = summarize(srv.run(reqs))
+    srv.close()
+    serial = summarize(serial_plain(reqs, chunk=10, tol=1e-4, max_iters=args.serve_max_iters))
+    return {"served": served, "serial_plain": serial, "unit": "s (time to solution)",
+            "workload": f"{n} instances over {args.serve_seconds} s at 200/s, buses "
+                        f"log-U[500, 20000], stop at residuals <= 1e-4 or "
+                        f"{args.serve_max_iters} iterations",
+            "speedup_p50": serial["p50_s"] / served["p50_s"],
+            "speedup_agg_iters": served["agg_iters_per_s"] / serial["agg_iters_per_s"]}
 
 
 # -------------------------------------------------------------------- main arm
@@ -335,9 +445,13 @@ def main():
             "launch_ms_median": float(np.median(launch_ms)),
             "note": "FP64 CUDA-core pipe; peak from 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
         line["cpu_baseline"] = cb
+    tb.close()
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["admm"] = bench_admm(args, dev)
+        line["uneven"] = bench_uneven(args, dev)
+        line["serving"] = bench_serving(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    tb.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -130,3 +130,32 @@ def test_pool_rejects_when_full_and_reuses_slots():
     pool.remove(i1)
     assert pool.add(n2) is not None
     pool.close()
+
+
+def test_serving_loop_admits_waits_retires_and_matches_alone_runs():
+    from paper_2106_14995_gb300.serving import AdmmServer, serial_plain, summarize
+    rng = np.random.default_rng(31)
+    reqs = []
+    for k in range(7):
+        nb = int(rng.integers(20, 160))
+        reqs.append(dict(id=k, t=0.002 * k, net=small_net(nb, 100 + k)))
+    # room for about two instances at a time: later arrivals wait for retirements
+    server = AdmmServer(cap_bus=384, cap_branch=512, cap_gen=256, cap_instances=3, chunk=4,
+                        tol=1e-4, max_iters=12)
+    recs = server.run(reqs, keep_state=True)
+    server.close()
+    assert sorted(r["id"] for r in recs) == list(range(7))
+    assert any(r["admitted"] > r["arrival"] + 1e-3 for r in recs)  # someone waited
+    for r in recs:
+        assert r["iterations"] == 12 or r["converged"]
+        alone = Admm(reqs[r["id"]]["net"])
+        alone.step(r["iterations"])
+        ref = alone.get_state()
+        alone.close()
+        for k in ref:
+            np.testing.assert_array_equal(r["state"][k], ref[k], err_msg=f"{r['id']} {k}")
+    s = summarize(recs)
+    assert s["instances"] == 7 and s["p99_s"] >= s["p50_s"] > 0
+    serial = serial_plain(reqs, chunk=4, max_iters=12)
+    assert [x["iterations"] for x in sorted(serial, key=lambda x: x["id"])] == \
+        [x["iterations"] for x in sorted(recs, key=lambda x: x["id"])]
