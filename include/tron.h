@@ -109,7 +109,9 @@ typedef struct tron_options {
   int32_t warps_per_block;/* 0      CTA size in warps (0 = library's choice)             */
   int32_t layout;         /* 0      kernel storage variant: 0 = library's choice, else
                                     1 + bits (bit 0: packed factor, bit 1: Q in global)  */
-  int32_t reserved[7];    /* must be zero                                                */
+  int32_t cholesky;       /* 0      0 = right-looking, trailing update over all lanes;
+                                    1 = left-looking (Sec. 4.3); both give the same bits */
+  int32_t reserved[6];    /* must be zero                                                */
 } tron_options_t;
 
 typedef struct tron_batch tron_batch_t;

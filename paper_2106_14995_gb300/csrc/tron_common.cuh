@@ -37,6 +37,46 @@ struct Grp {
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
     return v;
   }
+  // two and three sums at once: the first butterfly level sends each lane the value
+  // its partner does not keep, so both halves of the group reduce a different quantity
+  // and the remaining levels cost one addition for all of them (G = 32 and 16); the
+  // results are read back from the owning lanes, identical in every lane
+  __device__ __forceinline__ void sum2(double& a, double& b) const {
+    if constexpr (G >= 16) {
+      const bool hi = (t & (G / 2)) != 0;
+      double keep = hi ? b : a, send = hi ? a : b;
+      keep += __shfl_xor_sync(mask, send, G / 2, G);
+#pragma unroll
+      for (int o = G / 4; o > 0; o >>= 1) keep += __shfl_xor_sync(mask, keep, o, G);
+      a = __shfl_sync(mask, keep, 0, G);
+      b = __shfl_sync(mask, keep, G / 2, G);
+    } else {
+      a = sum(a);
+      b = sum(b);
+    }
+  }
+  __device__ __forceinline__ void sum3(double& a, double& b, double& c) const {
+    if constexpr (G == 32) {
+      // level 16: low half keeps (a, b), high half keeps (c, 0)
+      const bool hi = (t & 16) != 0;
+      double k0 = hi ? c : a, k1 = hi ? 0.0 : b;
+      double s0 = hi ? a : c, s1 = hi ? b : 0.0;
+      k0 += __shfl_xor_sync(mask, s0, 16);
+      k1 += __shfl_xor_sync(mask, s1, 16);
+      // level 8: in each half, lanes with bit 3 clear keep k0, set keep k1
+      const bool b3 = (t & 8) != 0;
+      double keep = b3 ? k1 : k0, send = b3 ? k0 : k1;
+      keep += __shfl_xor_sync(mask, send, 8);
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) keep += __shfl_xor_sync(mask, keep, o);
+      a = __shfl_sync(mask, keep, 0);
+      b = __shfl_sync(mask, keep, 8);
+      c = __shfl_sync(mask, keep, 16);
+    } else {
+      a = sum(a);
+      sum2(b, c);
+    }
+  }
   __device__ __forceinline__ double max(double v) const {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o, G));

@@ -282,6 +282,8 @@ static tron_err_t check_options(const tron_options_t* o) {
   XT_REQUIRE(o->warps_per_block >= 0 && o->warps_per_block <= 8, TRON_EINVAL,
              "options.warps_per_block must be in [0, 8]");
   XT_REQUIRE(o->layout >= 0 && o->layout <= 4, TRON_EINVAL, "options.layout must be in [0, 4]");
+  XT_REQUIRE(o->cholesky == 0 || o->cholesky == 1, TRON_EINVAL,
+             "options.cholesky must be 0 or 1");
   return TRON_OK;
 }
 

@@ -15,9 +15,12 @@
 // or rows of the mirrored upper part (forward, L y = b), so every shared-memory access
 // of a solve is contiguous across the group (Sec. 4.4).
 //
-// FP64 economy on this GPU: the pivot of each Cholesky column is taken with one rsqrt,
-// whose value scales the column and is kept as 1/L_jj for the triangular solves, which
-// then multiply instead of divide.
+// FP64 economy on this GPU (a warp FP64 instruction costs the same issue slot with one
+// active lane or 32): the factorization is right-looking with the trailing update
+// spread over all lanes (the paper's left-looking form remains as options.cholesky =
+// 1 and gives the same bits); the pivot of each column is taken with one rsqrt, kept
+// as 1/L_jj so that triangular solves multiply; norms are compared squared; dot
+// products that are needed together are reduced in one fused butterfly.
 #pragma once
 
 #include "../../include/tron.h"
@@ -188,6 +191,48 @@ struct Solver {
     return true;
   }
 
+  // right-looking with the trailing update spread over the whole group: after column j
+  // is scaled, the (m-j-1)(m-j)/2 elements of the trailing triangle are updated by
+  // all G lanes (element e of the triangle -> row cc, column dd), so no lane waits on
+  // the triangle's shape.  Every element receives the same fused multiply-adds in the
+  // same k order as in the left-looking form, hence the same factor bit for bit.
+  __device__ __forceinline__ bool chol_right(int m) {
+    for (int j = 0; j < m; ++j) {
+      const double piv = lo(j, j);
+      if (!(piv > 0.0)) {
+        gp.sync();
+        return false;
+      }
+      const double rs = rsqrt(piv);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = r * G + gp.t;
+        if (c > j && c < m) {
+          const double lcj = lo(c, j) * rs;
+          lo(c, j) = lcj;
+          if (!PK) mt(j, c) = lcj;
+        }
+      }
+      if (gp.t == (j & (G - 1))) {
+        lo(j, j) = piv * rs;
+        dinv[j] = rs;
+      }
+      gp.sync();
+      const int M = m - j - 1;
+      const int T = M * (M + 1) / 2;
+      for (int e = gp.t; e < T; e += G) {
+        int cc = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (cc * (cc + 1) / 2 > e) --cc;
+        while ((cc + 1) * (cc + 2) / 2 <= e) ++cc;
+        const int dd = e - cc * (cc + 1) / 2;
+        const int c = j + 1 + cc, d = j + 1 + dd;
+        lo(c, d) = fma(-lo(c, j), lo(d, j), lo(c, d));
+      }
+      gp.sync();
+    }
+    return true;
+  }
+
   // shifted factorization A + alpha I = L L^T, alpha from the sequence
   // 0 (or beta - min A_ii), then max(2 alpha, beta), beta = shift_frac * max |A_ii|
   __device__ __forceinline__ bool factor(int m) {
@@ -221,7 +266,7 @@ struct Solver {
         }
       }
       gp.sync();
-      if (chol_left(m)) return true;
+      if (o.cholesky == 1 ? chol_left(m) : chol_right(m)) return true;
       alpha = fmax(2.0 * alpha, beta);
     }
     return false;
@@ -266,7 +311,14 @@ struct Solver {
   // trqsol (Figure 2): sigma >= 0 with ||x + sigma p||_2 = delta
   __device__ __forceinline__ double trqsol(const double (&x)[R], const double (&p)[R],
                                            double delta) const {
-    const double ptx = dotv(p, x), ptp = dotv(p, p), xtx = dotv(x, x);
+    double ptx = 0.0, ptp = 0.0, xtx = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ptx = fma(p[r], x[r], ptx);
+      ptp = fma(p[r], p[r], ptp);
+      xtx = fma(x[r], x[r], xtx);
+    }
+    gp.sum3(ptx, ptp, xtx);
     const double dsq = delta * delta;
     double rad = ptx * ptx + ptp * (dsq - xtx);
     if (rad < 0.0) rad = 0.0;
@@ -286,10 +338,11 @@ struct Solver {
       p[r] = res[r];
     }
     double rr = dotv(res, res);
-    const double tol = o.cg_rtol * sqrt(rr);
+    const double tol2 = (o.cg_rtol * o.cg_rtol) * rr;  // ||res|| <= cg_rtol ||bhat||, squared
+    const double dsq = delta * delta;
     int info = 1;
     for (int it = 0; it < m; ++it) {
-      if (sqrt(rr) <= tol) {
+      if (rr <= tol2) {
         info = 0;
         break;
       }
@@ -310,7 +363,7 @@ struct Solver {
       double wn[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) wn[r] = fma(alpha, z[r], w[r]);
-      if (sqrt(dotv(wn, wn)) >= delta) {
+      if (dotv(wn, wn) >= dsq) {
         const double sg = trqsol(w, z, delta);
 #pragma unroll
         for (int r = 0; r < R; ++r) w[r] = fma(sg, z[r], w[r]);
@@ -338,10 +391,17 @@ struct Solver {
 #pragma unroll
     for (int r = 0; r < R; ++r) s[r] = P(fma(alpha, -g[r], x[r]), r) - x[r];
     hv(s, Hs);
-    const double gts = dotv(g, s);
-    const double q = gts + 0.5 * dotv(s, Hs);
-    const double snorm = sqrt(dotv(s, s));
-    return (q <= o.mu0 * gts) && (snorm <= o.mu1 * delta);
+    double gts = 0.0, sHs = 0.0, ss = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      gts = fma(g[r], s[r], gts);
+      sHs = fma(s[r], Hs[r], sHs);
+      ss = fma(s[r], s[r], ss);
+    }
+    gp.sum3(gts, sHs, ss);
+    const double q = gts + 0.5 * sHs;
+    const double bound = o.mu1 * delta;
+    return (q <= o.mu0 * gts) && (ss <= bound * bound);
   }
 
   // largest breakpoint along w = -g (breakpt of Figure 2), 0 if nothing can move
@@ -479,7 +539,7 @@ struct Solver {
           rF[r] = (c < m) ? vb[Fi[c]] : 0.0;
         }
         gp.sync();
-        if (pass == 0) rF0 = sqrt(dotv(rF, rF));
+        if (pass == 0) rF0 = dotv(rF, rF);  // squared
         if (!factor(m)) {
           status = TRON_CHOL_FAIL;
           break;
@@ -514,8 +574,13 @@ struct Solver {
             d[r] = yt[r] - y[r];
           }
           hv(d, Hd);
-          const double rtd = dotv(rv, d);
-          const double dHd = dotv(d, Hd);
+          double rtd = 0.0, dHd = 0.0;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            rtd = fma(rv[r], d[r], rtd);
+            dHd = fma(d[r], Hd[r], dHd);
+          }
+          gp.sum2(rtd, dHd);
           if (rtd + 0.5 * dHd <= o.mu0 * rtd) {
             found = true;
             break;
@@ -533,17 +598,26 @@ struct Solver {
           if (cidx[r] >= 0) ss = fma(rv[r], rv[r], ss);
         }
         const bool newly_active = gp.any(na);
-        const double rFn = sqrt(gp.sum(ss));
-        if (info == 2 || info == 3 || newly_active || rFn <= o.cg_rtol * rF0) break;
+        const double rFn2 = gp.sum(ss);
+        if (info == 2 || info == 3 || newly_active ||
+            rFn2 <= (o.cg_rtol * o.cg_rtol) * rF0)
+          break;
       }
       if (status == TRON_CHOL_FAIL) break;
 
       // ---- reduction ratio, acceptance, radius
-      double s2[R], Hs2[R];
+      // q(s) = g's + 1/2 s'Hs with s = y - x; the model gradient rv = g + H s was
+      // accumulated along the steps, so H s = rv - g needs no further product
+      double s2[R], gts = 0.0, sHs = 0.0, ss2 = 0.0;
 #pragma unroll
-      for (int r = 0; r < R; ++r) s2[r] = y[r] - x[r];
-      hv(s2, Hs2);
-      const double qs = dotv(g, s2) + 0.5 * dotv(s2, Hs2);
+      for (int r = 0; r < R; ++r) {
+        s2[r] = y[r] - x[r];
+        gts = fma(g[r], s2[r], gts);
+        sHs = fma(s2[r], rv[r] - g[r], sHs);
+        ss2 = fma(s2[r], s2[r], ss2);
+      }
+      gp.sum3(gts, sHs, ss2);
+      const double qs = gts + 0.5 * sHs;
       const double fy = obj.eval_f(gp, y);
       const double fsy = obj.fsc;
       // ratio guarded by the rounding level of f (Conn, Gould and Toint, Trust-Region
@@ -552,7 +626,7 @@ struct Solver {
       const double ared = f - fy;
       const double fl = o.ared_guard * fmax(fs, 1.0);
       const double rho = (pred > 0.0 && isfinite(fy)) ? (ared + fl) / (pred + fl) : -CUDART_INF;
-      const double snorm = sqrt(dotv(s2, s2));
+      const double snorm = sqrt(ss2);
       if (rho > o.eta0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = y[r];
