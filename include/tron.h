@@ -109,8 +109,10 @@ typedef struct tron_options {
   int32_t warps_per_block;/* 0      CTA size in warps (0 = library's choice)             */
   int32_t layout;         /* 0      kernel storage variant: 0 = library's choice, else
                                     1 + bits (bit 0: packed factor, bit 1: Q in global)  */
-  int32_t cholesky;       /* 0      0 = right-looking, trailing update over all lanes;
-                                    1 = left-looking (Sec. 4.3); both give the same bits */
+  int32_t cholesky;       /* 0      factorization form: 0 = per size class (right-looking
+                                    up to n = 32, left-looking above), 1 = left-looking
+                                    (Sec. 4.3), 2 = right-looking with the trailing update
+                                    spread over all lanes; all give the same bits         */
   int32_t reserved[6];    /* must be zero                                                */
 } tron_options_t;
 
@@ -187,7 +189,7 @@ tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const do
                                const double* d_delta0, int32_t sample, void* stream);
 
 /* Size classes of the batch and the variant each will run with. layout bits: 1 = packed
- * factor, 2 = Q read from global memory. */
+ * factor, 2 = Q read from global memory; bits 2-3: the options.cholesky value used. */
 int32_t tron_batch_buckets(const tron_batch_t* b);
 tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t* N, int32_t* G,
                                  int32_t* layout, int32_t* warps_per_block, int64_t* count);

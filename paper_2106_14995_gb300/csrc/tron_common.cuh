@@ -15,11 +15,15 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace xt {
 
 template <int G>
 struct Grp {
-  static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "group size");
+  static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32 || G == 64 ||
+                    G == 128,
+                "group size");
   int lane;       // lane in the warp
   int t;          // rank in the group
   unsigned mask;  // lanes of this group
@@ -94,6 +98,12 @@ struct Grp {
     return b >> (lane & ~(G - 1));
   }
   __device__ __forceinline__ bool any(bool p) const { return ballot(p) != 0u; }
+  // exclusive prefix count of p over the ranks below t, and the group total
+  __device__ __forceinline__ int prefix(bool p, int& total) const {
+    const unsigned b = ballot(p);
+    total = __popc(b);
+    return __popc(b & ((1u << t) - 1u));
+  }
   __device__ __forceinline__ double bcast(double v, int src) const {
     if (G == 1) return v;
     return __shfl_sync(mask, v, src, G);
@@ -103,6 +113,132 @@ struct Grp {
     return __shfl_sync(mask, v, src, G);
   }
 };
+
+// A group spanning a whole CTA (G = 64 or 128 threads, one problem per CTA) for the
+// large size classes: reductions combine warp butterflies with a fixed-order pass over
+// the warps' partial results in shared memory, so every thread gets the same bits.
+template <int G>
+struct GrpCta {
+  static_assert(G == 64 || G == 128, "CTA group size");
+  static constexpr int W = G / 32;
+  int lane;
+  int t;
+  unsigned mask;
+
+  __device__ __forceinline__ GrpCta() {
+    t = threadIdx.x;
+    lane = t & 31;
+    mask = 0xffffffffu;
+  }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ double wsum(double v) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  }
+  __device__ __forceinline__ double sum(double v) const {
+    __shared__ double red[W];
+    v = wsum(v);
+    if (lane == 0) red[t >> 5] = v;
+    __syncthreads();
+    double s = red[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) s += red[w];
+    __syncthreads();
+    return s;
+  }
+  __device__ __forceinline__ void sum2(double& a, double& b) const {
+    __shared__ double red[2][W];
+    a = wsum(a);
+    b = wsum(b);
+    if (lane == 0) {
+      red[0][t >> 5] = a;
+      red[1][t >> 5] = b;
+    }
+    __syncthreads();
+    a = red[0][0];
+    b = red[1][0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    __syncthreads();
+  }
+  __device__ __forceinline__ void sum3(double& a, double& b, double& c) const {
+    __shared__ double red[3][W];
+    a = wsum(a);
+    b = wsum(b);
+    c = wsum(c);
+    if (lane == 0) {
+      red[0][t >> 5] = a;
+      red[1][t >> 5] = b;
+      red[2][t >> 5] = c;
+    }
+    __syncthreads();
+    a = red[0][0];
+    b = red[1][0];
+    c = red[2][0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+      c += red[2][w];
+    }
+    __syncthreads();
+  }
+  __device__ __forceinline__ double max(double v) const {
+    __shared__ double red[W];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[t >> 5] = v;
+    __syncthreads();
+    double s = red[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) s = fmax(s, red[w]);
+    __syncthreads();
+    return s;
+  }
+  __device__ __forceinline__ double min(double v) const {
+    __shared__ double red[W];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[t >> 5] = v;
+    __syncthreads();
+    double s = red[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) s = fmin(s, red[w]);
+    __syncthreads();
+    return s;
+  }
+  __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+  __device__ __forceinline__ int prefix(bool p, int& total) const {
+    __shared__ int cnt[W];
+    const unsigned b = __ballot_sync(0xffffffffu, p);
+    if (lane == 0) cnt[t >> 5] = __popc(b);
+    __syncthreads();
+    int before = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      if (w < (t >> 5)) before += cnt[w];
+      total += cnt[w];
+    }
+    __syncthreads();
+    return before + __popc(b & ((1u << lane) - 1u));
+  }
+  __device__ __forceinline__ double bcast(double v, int src) const {
+    __shared__ double slot;
+    if (t == src) slot = v;
+    __syncthreads();
+    const double r = slot;
+    __syncthreads();
+    return r;
+  }
+};
+
+template <int G>
+using GroupOf = typename std::conditional<(G > 32), GrpCta<G>, Grp<G>>::type;
 
 // View of one problem's slice of shared memory.  With G = 1 the 32 problems of a warp
 // are interleaved element by element (element k of lane q at k*32 + q), so a warp-wide

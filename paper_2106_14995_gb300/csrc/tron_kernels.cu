@@ -124,29 +124,48 @@ template <class Obj, int N, int G, bool PK>
 __global__ void __launch_bounds__(256) k_tron_plain(const KArgs a) {
   using S = Solver<Obj, N, G, PK>;
   extern __shared__ double smem[];
-  const int warp = threadIdx.x >> 5;
-  double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
-  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  const int64_t idx = gw * S::PROBS_PER_WARP + (threadIdx.x & 31) / G;
-  if (idx >= a.count) return;
-  solve_problem<Obj, N, G, PK>(a, idx, wsm);
+  if constexpr (G > 32) {  // one problem per CTA
+    const int64_t idx = blockIdx.x;
+    if (idx >= a.count) return;
+    solve_problem<Obj, N, G, PK>(a, idx, smem);
+  } else {
+    const int warp = threadIdx.x >> 5;
+    double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t idx = gw * S::PROBS_PER_WARP + (threadIdx.x & 31) / G;
+    if (idx >= a.count) return;
+    solve_problem<Obj, N, G, PK>(a, idx, wsm);
+  }
 }
 
 template <class Obj, int N, int G, bool PK>
 __global__ void __launch_bounds__(256) k_tron_persistent(const KArgs a) {
   using S = Solver<Obj, N, G, PK>;
   extern __shared__ double smem[];
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
-  for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)S::PROBS_PER_WARP);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if ((int64_t)base >= a.count) break;
-    const int64_t idx = (int64_t)base + lane / G;
-    if (idx < a.count) solve_problem<Obj, N, G, PK>(a, idx, wsm);
-    __syncwarp();
+  if constexpr (G > 32) {  // the CTA pulls one problem at a time
+    __shared__ unsigned long long next;
+    for (;;) {
+      if (threadIdx.x == 0) next = atomicAdd(a.counter, 1ull);
+      __syncthreads();
+      const int64_t idx = (int64_t)next;
+      __syncthreads();
+      if (idx >= a.count) break;
+      solve_problem<Obj, N, G, PK>(a, idx, smem);
+      __syncthreads();
+    }
+  } else {
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
+    for (;;) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)S::PROBS_PER_WARP);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if ((int64_t)base >= a.count) break;
+      const int64_t idx = (int64_t)base + lane / G;
+      if (idx < a.count) solve_problem<Obj, N, G, PK>(a, idx, wsm);
+      __syncwarp();
+    }
   }
 }
 
@@ -158,10 +177,33 @@ struct KernelEntry {
   int kind, N, G, layout;
   const void* plain;
   const void* persistent;
-  int warp_doubles;
-  int probs_per_warp;
-  int occupancy[9];  // CTAs per SM by warps per block (cached, 0 = unknown)
+  int warp_doubles;    // shared memory per warp (per CTA for CTA groups)
+  int probs_per_warp;  // 0 for CTA groups
+  int occupancy[9];    // CTAs per SM by warps per block (cached, 0 = unknown)
 };
+
+// launch geometry of a variant for a requested number of warps per CTA
+struct Geometry {
+  int threads;
+  size_t smem;
+  int64_t per_cta;
+  int wpb;
+};
+static Geometry geometry(const KernelEntry& e, int wpb) {
+  Geometry g;
+  if (e.G > 32) {  // one problem per CTA of G threads
+    g.wpb = e.G / 32;
+    g.threads = e.G;
+    g.smem = (size_t)e.warp_doubles * sizeof(double);
+    g.per_cta = 1;
+  } else {
+    g.wpb = wpb;
+    g.threads = wpb * 32;
+    g.smem = (size_t)wpb * e.warp_doubles * sizeof(double);
+    g.per_cta = (int64_t)wpb * e.probs_per_warp;
+  }
+  return g;
+}
 
 template <class Obj, int N, int G, bool PK>
 static KernelEntry make_entry(int kind, int layout) {
@@ -190,10 +232,18 @@ static std::vector<KernelEntry>& table() {
       make_entry<DenseObj<16, 16>, 16, 16, false>(TRON_OBJ_DENSE_QUARTIC, 0),
       make_entry<DenseObj<16, 8>, 16, 8, false>(TRON_OBJ_DENSE_QUARTIC, 0),
       make_entry<DenseObj<32, 32>, 32, 32, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<32, 32>, 32, 32, true>(TRON_OBJ_DENSE_QUARTIC, kLayoutPacked),
+      make_entry<DenseObj<32, 32, true>, 32, 32, true>(TRON_OBJ_DENSE_QUARTIC,
+                                                      kLayoutPacked | kLayoutQGlobal),
       make_entry<DenseObj<32, 16>, 32, 16, false>(TRON_OBJ_DENSE_QUARTIC, 0),
+      make_entry<DenseObj<64, 64, true>, 64, 64, true>(TRON_OBJ_DENSE_QUARTIC,
+                                                      kLayoutPacked | kLayoutQGlobal),
+      make_entry<DenseObj<64, 64>, 64, 64, true>(TRON_OBJ_DENSE_QUARTIC, kLayoutPacked),
       make_entry<DenseObj<64, 32, true>, 64, 32, true>(TRON_OBJ_DENSE_QUARTIC,
                                                       kLayoutPacked | kLayoutQGlobal),
       make_entry<DenseObj<64, 32>, 64, 32, true>(TRON_OBJ_DENSE_QUARTIC, kLayoutPacked),
+      make_entry<DenseObj<128, 128, true>, 128, 128, true>(TRON_OBJ_DENSE_QUARTIC,
+                                                          kLayoutPacked | kLayoutQGlobal),
       make_entry<DenseObj<128, 32, true>, 128, 32, true>(TRON_OBJ_DENSE_QUARTIC,
                                                         kLayoutPacked | kLayoutQGlobal),
       make_entry<Hs45Obj<8>, 8, 1, false>(TRON_OBJ_HS45, 0),
@@ -254,6 +304,7 @@ struct tron_batch {
     int32_t* d_list;     // NULL when the bucket is the whole (uniform) batch
     KernelEntry* tuned;  // variant chosen by tron_batch_autotune (NULL: options/default)
     int tuned_wpb;
+    int tuned_chol;
   };
   std::vector<Bucket> buckets;
   unsigned long long* d_counter;  // one work counter per bucket
@@ -282,8 +333,8 @@ static tron_err_t check_options(const tron_options_t* o) {
   XT_REQUIRE(o->warps_per_block >= 0 && o->warps_per_block <= 8, TRON_EINVAL,
              "options.warps_per_block must be in [0, 8]");
   XT_REQUIRE(o->layout >= 0 && o->layout <= 4, TRON_EINVAL, "options.layout must be in [0, 4]");
-  XT_REQUIRE(o->cholesky == 0 || o->cholesky == 1, TRON_EINVAL,
-             "options.cholesky must be 0 or 1");
+  XT_REQUIRE(o->cholesky >= 0 && o->cholesky <= 2, TRON_EINVAL,
+             "options.cholesky must be 0, 1 or 2");
   return TRON_OK;
 }
 
@@ -370,7 +421,7 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
     }
     b->n_uniform = n_uniform;
     b->total_n = nprob * (int64_t)n_uniform;
-    b->buckets.push_back({size_class(kind, n_uniform), nprob, nullptr, nullptr, 0});
+    b->buckets.push_back({size_class(kind, n_uniform), nprob, nullptr, nullptr, 0, 0});
   } else {
     std::vector<int64_t> poff(nprob), voff(nprob);
     std::vector<std::vector<int32_t>> lists(kNumClasses);
@@ -408,7 +459,7 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
     // largest class first: the longest solves start earliest
     for (int slot = kNumClasses - 1; slot >= 0; --slot) {
       if (lists[slot].empty()) continue;
-      tron_batch::Bucket bk{kClasses[slot], (int64_t)lists[slot].size(), nullptr, nullptr, 0};
+      tron_batch::Bucket bk{kClasses[slot], (int64_t)lists[slot].size(), nullptr, nullptr, 0, 0};
       if (cudaMalloc(&bk.d_list, sizeof(int32_t) * lists[slot].size()) != cudaSuccess) {
         set_error("tron_batch_create: cudaMalloc of a problem list failed");
         return fail(TRON_ENOMEM);
@@ -499,6 +550,8 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
     }
     XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d", bk.N);
     wpb = fit_wpb(wpb, ke->warp_doubles, b->smem_optin);
+    const Geometry geo = geometry(*ke, wpb);
+    wpb = geo.wpb;
     cudaStream_t ls = st;
     if (fork) {
       ls = b->side[bi];
@@ -524,7 +577,8 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
     a.pstride = record_size(b->kind, b->n_uniform);
     a.counter = b->d_counter + bi;
     a.opt = b->opt;
-    const size_t smem = (size_t)wpb * ke->warp_doubles * sizeof(double);
+    if (bk.tuned && b->opt.group == 0 && b->opt.cholesky == 0) a.opt.cholesky = bk.tuned_chol;
+    const size_t smem = geo.smem;
     const void* fn = persistent ? ke->persistent : ke->plain;
     {
       std::lock_guard<std::mutex> lk(g_table_mu);
@@ -537,20 +591,18 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
         std::lock_guard<std::mutex> lk(g_table_mu);
         occ = ke->occupancy[wpb];
         if (occ == 0) {
-          XT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, wpb * 32, smem));
+          XT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, geo.threads, smem));
           ke->occupancy[wpb] = occ;
         }
       }
       XT_REQUIRE(occ > 0, TRON_EUNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
-      const int64_t per_cta = (int64_t)wpb * ke->probs_per_warp;
-      grid = std::min<int64_t>((int64_t)occ * b->sms, (bk.count + per_cta - 1) / per_cta);
+      grid = std::min<int64_t>((int64_t)occ * b->sms, (bk.count + geo.per_cta - 1) / geo.per_cta);
       XT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), ls));
     } else {
-      const int64_t per_cta = (int64_t)wpb * ke->probs_per_warp;
-      grid = (bk.count + per_cta - 1) / per_cta;
+      grid = (bk.count + geo.per_cta - 1) / geo.per_cta;
     }
     void* args[] = {&a};
-    XT_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(wpb * 32), args, smem, ls));
+    XT_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(geo.threads), args, smem, ls));
     b->last_launches++;
     if (fork) {
       XT_CUDA(cudaEventRecord(b->ev_join[bi], ls));
@@ -580,10 +632,14 @@ tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t*
                     b->opt.layout);
   }
   XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d", bk.N);
-  wpb = fit_wpb(wpb, ke->warp_doubles, b->smem_optin);
+  wpb = geometry(*ke, fit_wpb(wpb, ke->warp_doubles, b->smem_optin)).wpb;
   if (N) *N = ke->N;
   if (G) *G = ke->G;
-  if (layout) *layout = ke->layout;
+  if (layout) {
+    const int chol = (bk.tuned && b->opt.group == 0 && b->opt.cholesky == 0) ? bk.tuned_chol
+                                                                             : b->opt.cholesky;
+    *layout = ke->layout | (chol << 2);
+  }
   if (warps_per_block) *warps_per_block = wpb;
   if (count) *count = bk.count;
   return TRON_OK;
@@ -623,11 +679,16 @@ tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const do
     const int64_t cs = std::min<int64_t>(bk.count, sample);
     float best = 1e30f;
     KernelEntry* best_e = nullptr;
-    int best_w = 4;
+    int best_w = 4, best_c = 0;
     for (auto& ke : table()) {
       if (ke.kind != b->kind || ke.N != bk.N) continue;
-      for (int wpb : {1, 2, 4, 8}) {
-        const size_t smem = (size_t)wpb * ke.warp_doubles * sizeof(double);
+      for (int trial = 0; trial < 8; ++trial) {
+        const int wpb = 1 << (trial & 3);
+        const int chol = 1 + (trial >> 2);  // 1 left-looking, 2 right-looking
+        if (wpb > 8) continue;
+        if (ke.G > 32 && wpb != 1) continue;  // CTA groups have one geometry
+        const Geometry geo = geometry(ke, wpb);
+        const size_t smem = geo.smem;
         if (smem > prop.sharedMemPerBlockOptin) continue;
         KArgs a;
         memset(&a, 0, sizeof(a));
@@ -648,8 +709,8 @@ tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const do
         a.n_uniform = b->n_uniform;
         a.pstride = record_size(b->kind, b->n_uniform);
         a.opt = b->opt;
-        const int64_t per_cta = (int64_t)wpb * ke.probs_per_warp;
-        const int64_t grid = (cs + per_cta - 1) / per_cta;
+        a.opt.cholesky = chol;
+        const int64_t grid = (cs + geo.per_cta - 1) / geo.per_cta;
         void* args[] = {&a};
         float ms = 1e30f;
         bool ok = cudaFuncSetAttribute(ke.plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -660,7 +721,7 @@ tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const do
                cudaMemcpyAsync(dt, d_delta0, 8 * np, cudaMemcpyDeviceToDevice, st) ==
                    cudaSuccess &&
                cudaEventRecord(e0, st) == cudaSuccess &&
-               cudaLaunchKernel(ke.plain, dim3((unsigned)grid), dim3(wpb * 32), args, smem,
+               cudaLaunchKernel(ke.plain, dim3((unsigned)grid), dim3(geo.threads), args, smem,
                                 st) == cudaSuccess &&
                cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
           if (ok && rep == 1) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
@@ -672,13 +733,15 @@ tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const do
         if (ms < best) {
           best = ms;
           best_e = &ke;
-          best_w = wpb;
+          best_w = geo.wpb;
+          best_c = chol;
         }
       }
     }
     if (best_e) {
       bk.tuned = best_e;
       bk.tuned_wpb = best_w;
+      bk.tuned_chol = best_c;
     }
   }
   if (err == TRON_OK && cudaStreamSynchronize(st) != cudaSuccess) {
@@ -843,7 +906,8 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
     KernelEntry* ke = find_entry(kind, N, G, o.layout);
     XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for kind %d, size class %d, group %d",
                (int)kind, N, G);
-    const int wpb = fit_wpb(wpb0, ke->warp_doubles, optin);
+    const Geometry geo = geometry(*ke, fit_wpb(wpb0, ke->warp_doubles, optin));
+    const int wpb = geo.wpb;
     KArgs a;
     memset(&a, 0, sizeof(a));
     a.params = d_params;
@@ -864,7 +928,7 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
     a.pstride = 0;
     a.counter = na_ctr + s;
     a.opt = o;
-    const size_t smem = (size_t)wpb * ke->warp_doubles * sizeof(double);
+    const size_t smem = geo.smem;
     int occ = 0;
     {
       std::lock_guard<std::mutex> lk(g_table_mu);
@@ -872,16 +936,17 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
                                    (int)smem));
       occ = ke->occupancy[wpb];
       if (occ == 0) {
-        XT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ke->persistent, wpb * 32,
+        XT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ke->persistent, geo.threads,
                                                               smem));
         ke->occupancy[wpb] = occ;
       }
     }
     XT_REQUIRE(occ > 0, TRON_EUNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
-    const int64_t per_cta = (int64_t)wpb * ke->probs_per_warp;
-    const int64_t grid = std::min<int64_t>((int64_t)occ * sms, (count[s] + per_cta - 1) / per_cta);
+    const int64_t grid =
+        std::min<int64_t>((int64_t)occ * sms, (count[s] + geo.per_cta - 1) / geo.per_cta);
     void* args[] = {&a};
-    XT_CUDA(cudaLaunchKernel(ke->persistent, dim3((unsigned)grid), dim3(wpb * 32), args, smem, st));
+    XT_CUDA(cudaLaunchKernel(ke->persistent, dim3((unsigned)grid), dim3(geo.threads), args, smem,
+                             st));
   }
   return TRON_OK;
 }

@@ -41,7 +41,8 @@ struct DenseObj {
     st = base.at((QG ? 0 : N * LDQ) + N);
   }
 
-  __device__ __forceinline__ bool load(const Grp<G>& gp, const double* __restrict__ rec, int n_) {
+  template <class GP>
+  __device__ __forceinline__ bool load(const GP& gp, const double* __restrict__ rec, int n_) {
     n = n_;
     qg = rec;
     bool fin = true;
@@ -72,7 +73,8 @@ struct DenseObj {
   }
 
   // y_i = sum_j Q_ij v_j for the slots of this lane (v staged in st for G >= 2)
-  __device__ __forceinline__ void qmul(const Grp<G>& gp, const double (&v)[R], double (&y)[R]) {
+  template <class GP>
+  __device__ __forceinline__ void qmul(const GP& gp, const double (&v)[R], double (&y)[R]) {
     if constexpr (G == 1) {
 #pragma unroll
       for (int i = 0; i < N; ++i) {
@@ -96,7 +98,8 @@ struct DenseObj {
     }
   }
 
-  __device__ __forceinline__ double eval_f(const Grp<G>& gp, const double (&y)[R]) {
+  template <class GP>
+  __device__ __forceinline__ double eval_f(const GP& gp, const double (&y)[R]) {
     qmul(gp, y, qy);
     double s = 0.0, m = 0.0;
 #pragma unroll
@@ -109,7 +112,8 @@ struct DenseObj {
     return gp.sum(s);
   }
 
-  __device__ __forceinline__ void grad_hess(const Grp<G>& gp, const double (&x)[R], double (&g)[R]) {
+  template <class GP>
+  __device__ __forceinline__ void grad_hess(const GP& gp, const double (&x)[R], double (&g)[R]) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       double x2 = x[r] * x[r];
@@ -125,7 +129,8 @@ struct DenseObj {
   }
   __device__ __forceinline__ double hd(int i) const { return hdg[i]; }
 
-  __device__ __forceinline__ bool hess_finite(const Grp<G>& gp) const {
+  template <class GP>
+  __device__ __forceinline__ bool hess_finite(const GP& gp) const {
     bool fin = true;
 #pragma unroll
     for (int r = 0; r < R; ++r) fin = fin && isfinite(hdg[r * G + gp.t]);

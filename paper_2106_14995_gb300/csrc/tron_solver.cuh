@@ -52,10 +52,12 @@ struct Solver {
   // several problems share a warp)
   static constexpr int S = (G == 1 || G >= 16) ? round_up(S_RAW, 2)
                                                : S_RAW + ((G - S_RAW % 16) % 16 + 16) % 16;
-  static constexpr int PROBS_PER_WARP = 32 / G;
-  static constexpr int WARP_DOUBLES = (G == 1) ? S * 32 : S * PROBS_PER_WARP;
+  // problems per warp (warp groups) and shared memory per warp; a CTA group (G > 32)
+  // holds one problem per CTA and S doubles per CTA
+  static constexpr int PROBS_PER_WARP = (G > 32) ? 0 : 32 / G;
+  static constexpr int WARP_DOUBLES = (G == 1) ? S * 32 : (G > 32 ? S : S * PROBS_PER_WARP);
 
-  Grp<G> gp;
+  GroupOf<G> gp;
   const tron_options_t& o;
   Obj obj;
   int n;
@@ -64,7 +66,8 @@ struct Solver {
   double l[R], u[R];
 
   __device__ __forceinline__ Solver(const tron_options_t& opt, double* warp_smem) : o(opt) {
-    double* base = (G == 1) ? warp_smem + gp.lane : warp_smem + (gp.lane / G) * S;
+    double* base = (G == 1) ? warp_smem + gp.lane
+                            : (G > 32 ? warp_smem : warp_smem + (gp.lane / G) * S);
     SV<G> sv{base};
     Lm = sv.at(OFF_L);
     vb = sv.at(OFF_VB);
@@ -266,7 +269,9 @@ struct Solver {
         }
       }
       gp.sync();
-      if (o.cholesky == 1 ? chol_left(m) : chol_right(m)) return true;
+      // options.cholesky: 1 left-looking, 2 right-looking, 0 the size class's default
+      const bool right = (o.cholesky == 2) || (o.cholesky == 0 && N <= 32);
+      if (right ? chol_right(m) : chol_left(m)) return true;
       alpha = fmax(2.0 * alpha, beta);
     }
     return false;
@@ -521,9 +526,10 @@ struct Solver {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const bool fr = (l[r] < y[r]) && (y[r] < u[r]);
-          const unsigned b = gp.ballot(fr);
-          cidx[r] = fr ? m + __popc(b & ((1u << gp.t) - 1u)) : -1;
-          m += __popc(b);
+          int tot;
+          const int pre = gp.prefix(fr, tot);
+          cidx[r] = fr ? m + pre : -1;
+          m += tot;
         }
         if (m == 0) break;
 #pragma unroll

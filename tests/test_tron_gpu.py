@@ -81,7 +81,7 @@ def test_dense_group_mappings(n, group):
     assert_convex_parity(g, r, d["l"], d["u"])
 
 
-@pytest.mark.parametrize("n,layout", [(64, 2), (64, 4), (128, 4), (100, 4)])
+@pytest.mark.parametrize("n,layout", [(32, 2), (32, 4), (64, 2), (64, 4), (128, 4), (100, 4)])
 def test_dense_large_layouts(n, layout):
     # layout option = 1 + bits: 2 = packed factor with Q in shared memory,
     # 4 = packed factor with Q read from global memory
@@ -89,6 +89,20 @@ def test_dense_large_layouts(n, layout):
     g = gpu_solve(d, n=n, layout=layout)
     r = oracle_solve(d)
     assert_convex_parity(g, r, d["l"], d["u"])
+
+
+@pytest.mark.parametrize("n", [20, 32, 64, 128])
+def test_left_and_right_looking_factorizations_give_the_same_bits(n):
+    d = synth.dense_batch(61, n, seed_index=80 + n)
+    a = gpu_solve(d, n=n, cholesky=1)
+    b = gpu_solve(d, n=n, cholesky=2)
+    for k in ("x", "f", "pg", "iters", "status", "delta"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    br = synth.branch_batch(96, seed_index=81)
+    a = gpu_solve(br, n=4, cholesky=1)
+    b = gpu_solve(br, n=4, cholesky=2)
+    for k in ("x", "f", "iters"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
 def _branch_kkt(rec, x, l, u):
