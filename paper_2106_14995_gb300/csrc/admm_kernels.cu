@@ -30,7 +30,6 @@ namespace xt {
 
 constexpr int kAlign = 128;      // slot alignment of every instance range
 constexpr int kBusThreads = 128; // = kAlign: one bus block never spans two instances
-constexpr int kBranchWarps = 4;  // branch CTA = 4 warps x 32 lanes = 128 branches
 constexpr int kGraphChunk = 8;   // iterations per replayed graph
 constexpr double kTwoPi = 6.283185307179586;
 
@@ -91,18 +90,18 @@ struct PoolDev {
 struct AdmmArgs {
   PoolDev d;
   tron_options_t opt;
-  int32_t nbb;    // branch CTAs
+  int32_t nbb;    // branch CTAs (warps_per_block warps of 32 branches each)
   int32_t ngb;    // generator CTAs
 };
 
 using BranchSolver = Solver<BranchObj, 4, 1>;
 
-__global__ void __launch_bounds__(128) k_admm_branch_gen(const AdmmArgs a) {
+__global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
   const PoolDev& d = a.d;
   if ((int)blockIdx.x < a.nbb) {
     extern __shared__ double smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = ((int)blockIdx.x * kBranchWarps + warp) * 32 + lane;
+    const int k = ((int)blockIdx.x * (int)(blockDim.x >> 5) + warp) * 32 + lane;
     if (k >= d.cap_br) return;
     const int inst = d.br_inst[k];
     if (inst < 0 || !d.inst_active[inst]) return;
@@ -436,6 +435,7 @@ struct admm_pool {
   PoolDev d;
   tron_options_t opt;
   int nbb, ngb, nbusb;
+  int bw;  // warps per branch CTA
   RangeAlloc ab, al, ag;
   struct Inst {
     bool live;
@@ -480,10 +480,12 @@ static AdmmArgs make_args(const admm_pool* p) {
 
 static tron_err_t launch_iteration(admm_pool* p, cudaStream_t st) {
   AdmmArgs a = make_args(p);
-  const size_t smem = (size_t)kBranchWarps * BranchSolver::WARP_DOUBLES * sizeof(double);
+  const size_t smem = (size_t)p->bw * BranchSolver::WARP_DOUBLES * sizeof(double);
   void* args[] = {&a};
+  // every CTA has bw warps: a branch CTA solves 32 branches per warp (each warp owns
+  // its slice of the shared memory), a generator CTA updates one generator per thread
   XT_CUDA(cudaLaunchKernel((const void*)k_admm_branch_gen, dim3(p->nbb + p->ngb),
-                           dim3(kBranchWarps * 32), args, smem, st));
+                           dim3(p->bw * 32), args, smem, st));
   XT_CUDA(cudaLaunchKernel((const void*)k_admm_bus, dim3(p->nbusb), dim3(kBusThreads), args, 0,
                            st));
   return TRON_OK;
@@ -537,8 +539,11 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
   p->d.cap_gen = cg;
   p->d.cap_inst = cap_instances;
   p->d.H = history_len;
-  p->nbb = (cl + kBranchWarps * 32 - 1) / (kBranchWarps * 32);
-  p->ngb = (cg + kBranchWarps * 32 - 1) / (kBranchWarps * 32);
+  // branch CTA size: options.warps_per_block (default 1: spread the branch warps over
+  // every SM); one 32-branch warp per CTA warp
+  p->bw = p->opt.warps_per_block > 0 ? std::min(p->opt.warps_per_block, 8) : 1;
+  p->nbb = (cl + p->bw * 32 - 1) / (p->bw * 32);
+  p->ngb = (cg + p->bw * 32 - 1) / (p->bw * 32);
   p->nbusb = std::max(1, (cb + kBusThreads - 1) / kBusThreads);
   PA(br_from, cl);
   PA(br_to, cl);
@@ -605,7 +610,7 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
       cudaMemsetAsync(p->d.done, 0, sizeof(unsigned int), st) ||
       cudaMemsetAsync(p->d.part, 0, sizeof(double) * 2 * p->nbusb, st))
     return fail("workspace initialisation");
-  const size_t smem = (size_t)kBranchWarps * BranchSolver::WARP_DOUBLES * sizeof(double);
+  const size_t smem = (size_t)p->bw * BranchSolver::WARP_DOUBLES * sizeof(double);
   if (cudaFuncSetAttribute((const void*)k_admm_branch_gen,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
     return fail("cudaFuncSetAttribute");

@@ -155,6 +155,12 @@ struct Solver {
     gp.sync();
   }
 
+  // piv > 0 (and not NaN) decided on the bit pattern: no FP64 compare
+  __device__ __forceinline__ static bool positive(double piv) {
+    const long long b = __double_as_longlong(piv);
+    return b > 0 && b <= 0x7FF0000000000000LL;
+  }
+
   // ------------------------------------------------------------ Cholesky (Sec. 4.3)
   // left-looking: column j gathers the updates of columns 0..j-1 (read from the
   // mirrored rows of L^T), then scales by 1/sqrt(pivot); L^T mirrored as it goes.
@@ -171,7 +177,7 @@ struct Solver {
       }
       gp.sync();
       const double piv = mt(j, j);
-      if (!(piv > 0.0)) {
+      if (!positive(piv)) {
         gp.sync();
         return false;
       }
@@ -185,10 +191,7 @@ struct Solver {
           if (!PK) lo(c, j) = lcj;
         }
       }
-      if (gp.t == (j & (G - 1))) {
-        mt(j, j) = piv * rs;
-        dinv[j] = rs;
-      }
+      if (gp.t == (j & (G - 1))) dinv[j] = rs;
       gp.sync();
     }
     return true;
@@ -202,7 +205,7 @@ struct Solver {
   __device__ __forceinline__ bool chol_right(int m) {
     for (int j = 0; j < m; ++j) {
       const double piv = lo(j, j);
-      if (!(piv > 0.0)) {
+      if (!positive(piv)) {
         gp.sync();
         return false;
       }
@@ -216,10 +219,7 @@ struct Solver {
           if (!PK) mt(j, c) = lcj;
         }
       }
-      if (gp.t == (j & (G - 1))) {
-        lo(j, j) = piv * rs;
-        dinv[j] = rs;
-      }
+      if (gp.t == (j & (G - 1))) dinv[j] = rs;
       gp.sync();
       const int M = m - j - 1;
       const int T = M * (M + 1) / 2;
@@ -271,39 +271,71 @@ struct Solver {
       gp.sync();
       // options.cholesky: 1 left-looking, 2 right-looking, 0 the size class's default
       const bool right = (o.cholesky == 2) || (o.cholesky == 0 && N <= 32);
-      if (right ? chol_right(m) : chol_left(m)) return true;
+      if (right ? chol_right(m) : chol_left(m)) {
+        unitize(m);
+        return true;
+      }
       alpha = fmax(2.0 * alpha, beta);
     }
     return false;
   }
 
-  // b <- L^-1 b (column-oriented; column j of L is row j of the mirrored upper part)
+  // After a successful factorization the strictly lower part (and its mirror) is
+  // scaled column by column to the unit-diagonal factor Lu = L D^-1, D = diag(L_jj),
+  // spread over all lanes like the trailing update.  The solves then need one FMA per
+  // column plus one diagonal scaling: L y = b is Lu (D y) = b, and L^T z = p is
+  // Lu^T z = D^-1 p.
+  __device__ __forceinline__ void unitize(int m) {
+    const int T = m * (m - 1) / 2;
+    for (int e = gp.t; e < T; e += G) {
+      int c = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
+      while (c * (c - 1) / 2 > e) --c;
+      while ((c + 1) * c / 2 <= e) ++c;
+      const int j = e - c * (c - 1) / 2;  // 0 <= j < c
+      const double v = lo(c, j) * dinv[j];
+      lo(c, j) = v;
+      if (!PK) mt(j, c) = v;
+    }
+    gp.sync();
+  }
+
+  // b <- L^-1 b: unit forward substitution with Lu (column j of Lu is row j of the
+  // mirrored upper part), then b <- D^-1 b
   __device__ __forceinline__ void solve_L(int m, double (&b)[R]) {
 #pragma unroll
     for (int rj = 0; rj < R; ++rj) {
       for (int tj = 0; tj < G; ++tj) {
         const int j = rj * G + tj;
         if (j >= m) break;
-        const double yj = gp.bcast(b[rj], tj) * dinv[j];
-        if (gp.t == tj) b[rj] = yj;
+        const double uj = gp.bcast(b[rj], tj);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int c = r * G + gp.t;
-          if (c > j && c < m) b[r] = fma(-mt(j, c), yj, b[r]);
+          if (c > j && c < m) b[r] = fma(-mt(j, c), uj, b[r]);
         }
       }
     }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = r * G + gp.t;
+      if (c < m) b[r] = b[r] * dinv[c];
+    }
   }
 
-  // z <- L^-T z (column-oriented over L^T; column j of L^T is row j of L)
+  // z <- L^-T z: z <- D^-1 z, then unit backward substitution with Lu^T (column j of
+  // Lu^T is row j of Lu)
   __device__ __forceinline__ void solve_Lt(int m, double (&z)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = r * G + gp.t;
+      if (c < m) z[r] = z[r] * dinv[c];
+    }
 #pragma unroll
     for (int rj = R - 1; rj >= 0; --rj) {
       for (int tj = G - 1; tj >= 0; --tj) {
         const int j = rj * G + tj;
         if (j >= m) continue;
-        const double zj = gp.bcast(z[rj], tj) * dinv[j];
-        if (gp.t == tj) z[rj] = zj;
+        const double zj = gp.bcast(z[rj], tj);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int c = r * G + gp.t;
@@ -649,7 +681,11 @@ struct Solver {
       } else if (rho > o.eta2 && snorm >= 0.99 * delta) {
         delta = fmin(o.sigma3 * delta, o.delta_max);
       }
-      if (delta < o.delta_min_rel * (1.0 + sqrt(dotv(x, x)))) {
+      // delta < c (1 + ||x||), decided without a square root:
+      // delta - c < 0, or (delta - c)^2 < c^2 ||x||^2
+      const double xx = dotv(x, x);
+      const double dc = delta - o.delta_min_rel;
+      if (dc < 0.0 || dc * dc < (o.delta_min_rel * o.delta_min_rel) * xx) {
         status = TRON_TR_TOO_SMALL;
         break;
       }
