@@ -13,6 +13,7 @@ differences, autograd, complex power), ``chol_shifted``/``chol`` (numpy), ``trqs
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -93,7 +94,29 @@ def lib():
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(_LIB_PATH)
+            _lib = _load(_LIB_PATH)
+    return _lib
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Run the oracle functions against another build of the C code (the tests use
+    this to plant mistakes in a copy and check that the pins catch them)."""
+    global _lib
+    with _lock:
+        old = _lib
+        _lib = _load(path)
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = old
+
+
+def _load(path: str):
+    if True:
+        if True:
+            L = C.CDLL(path)
             P = C.c_void_p
             L.ot_default_opts.argtypes = [C.POINTER(Opts)]
             L.ot_tron_solve.argtypes = [C.c_int, C.c_int, P, P, P, P, P, C.POINTER(Opts), P, P,
@@ -119,8 +142,7 @@ def lib():
             L.ot_admm_run.argtypes = [C.POINTER(Net), C.POINTER(State), C.POINTER(Opts),
                                       C.c_int, C.c_int, P, P, P, C.POINTER(Counters)]
             L.ot_admm_branch_record.argtypes = [C.POINTER(Net), C.POINTER(State), C.c_int, P]
-            _lib = L
-    return _lib
+            return L
 
 
 def _p(a: np.ndarray) -> int:

@@ -1,0 +1,94 @@
+"""Planted mistakes: each case edits a copy of the oracle's C source (a flipped sign, a
+dropped term, a transposed operand, a wrong constant), builds it, and checks that at
+least one of the pins in test_oracle_pins.py fails against it.  This shows the pins
+would catch such a mistake in the oracle itself.  Everything runs on the CPU."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "tron_oracle.c")
+
+# (name, original text, mutated text, pins expected to catch it)
+MUTATIONS = [
+    ("flow p_ij: sign of the g_ij wR term",
+     "F[0] = cf[0] * wi - cf[2] * wR + cf[3] * wI;",
+     "F[0] = cf[0] * wi + cf[2] * wR + cf[3] * wI;",
+     [pins.test_branch_flows_match_complex_power]),
+    ("branch Hessian: sign of d2 wR / dv_i dth_i",
+     "HwR[0 * 4 + 2] = -vj * sn;", "HwR[0 * 4 + 2] = vj * sn;",
+     [pins.test_branch_gradient_hessian_finite_differences]),
+    ("line-limit gradient: factor 2 dropped",
+     "dm[a] = 2.0 * p * dF[kp][a] + 2.0 * q * dF[kq][a];",
+     "dm[a] = 1.0 * p * dF[kp][a] + 2.0 * q * dF[kq][a];",
+     [pins.test_branch_gradient_hessian_finite_differences]),
+    ("dense gradient: quartic coefficient",
+     "if (g) g[i] = qx + cv[i] + 4.0 * d[i] * x2 * x[i];",
+     "if (g) g[i] = qx + cv[i] + 3.0 * d[i] * x2 * x[i];",
+     [pins.test_dense_eval_closed_form, pins.test_separable_quartic_closed_form]),
+    ("Cholesky: transposed operand in the column update",
+     "for (int k = 0; k < j; k++) v -= L[(size_t)i * m + k] * L[(size_t)j * m + k];",
+     "for (int k = 0; k < j; k++) v -= L[(size_t)k * m + i] * L[(size_t)j * m + k];",
+     [pins.test_chol_matches_numpy]),
+    ("trqsol: wrong root",
+     "return (rad - ptx) / ptp;", "return (-rad - ptx) / ptp;",
+     [pins.test_trqsol_is_positive_root]),
+    ("projected gradient: upper-bound rule",
+     "if (x[i] >= u[i] && p < 0.0) p = 0.0;", "if (x[i] >= u[i] && p > 0.0) p = 0.0;",
+     [pins.test_pgnorm_definition_cases]),
+    ("PCG: residual not updated",
+     "res[i] -= alpha * q[i];", "res[i] -= 0.0 * q[i];",
+     [pins.test_steihaug_one_iteration_on_pd]),
+    ("Cauchy search: sufficient-decrease test reversed",
+     "ok = (q <= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta);",
+     "ok = (q >= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta);",
+     [pins.test_separable_quadratic_closed_form, pins.test_newton_step_solves_an_interior_quadratic_in_one_iteration]),
+    ("back transform: direction sign",
+     "for (int a = 0; a < m; a++) w[F[a]] = sh[a];",
+     "for (int a = 0; a < m; a++) w[F[a]] = -sh[a];",
+     [pins.test_newton_step_solves_an_interior_quadratic_in_one_iteration]),
+    ("hs45 gradient sign",
+     "g[i] = -q;", "g[i] = q;",
+     [pins.test_hs45_printed_solution]),
+    ("ADMM bus update: sign of mu on the flow copies",
+     "st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho + mu1 / rho;",
+     "st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho - mu1 / rho;",
+     [pins.test_admm_bus_update_kkt_and_multipliers]),
+    ("ADMM generator update: linear cost dropped",
+     "double p = (rho * pt - lp - net->gen_c1[g]) / (2.0 * net->gen_c2[g] + rho);",
+     "double p = (rho * pt - lp) / (2.0 * net->gen_c2[g] + rho);",
+     [pins.test_admm_generator_update_is_scalar_qp_minimiser]),
+    ("ADMM multiplier update sign",
+     "st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);",
+     "st->br_lam[8 * (size_t)k + a] -= rho * (xv - xt);",
+     [pins.test_admm_bus_update_kkt_and_multipliers]),
+]
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(SRC) as fh:
+        return fh.read()
+
+
+@pytest.mark.parametrize("case", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(case, source, tmp_path):
+    name, old, new, catchers = case
+    assert source.count(old) == 1, f"mutation site not unique: {old}"
+    src = tmp_path / "tron_oracle.c"
+    src.write_text(source.replace(old, new))
+    lib = tmp_path / "liboracle_mut.so"
+    hdr = os.path.dirname(SRC)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-I", hdr, "-o", str(lib), str(src), "-lm", "-lpthread"], check=True)
+    caught = []
+    with oracle.using_library(str(lib)):
+        for pin in catchers:
+            try:
+                pin()
+            except Exception:  # an assertion, or a numerical failure of the pin
+                caught.append(pin.__name__)
+    assert caught, f"no pin caught: {name}"

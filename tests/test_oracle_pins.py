@@ -440,6 +440,25 @@ def test_status_codes_for_bad_input():
     assert r["status"] == oracle.MAX_ITER and r["iters"] == 1
 
 
+def test_newton_step_solves_an_interior_quadratic_in_one_iteration():
+    """Strictly convex quadratic with its minimiser inside the box and a large radius:
+    the Cauchy point, the complete factorization (Sec. 4.3: one PCG iteration) and the
+    back transform give the exact Newton step, so one outer iteration converges."""
+    rng = np.random.default_rng(12)
+    for n in (3, 8, 20):
+        G = rng.standard_normal((n, n))
+        Q = G @ G.T + n * np.eye(n)
+        xs = rng.uniform(-0.5, 0.5, n)
+        c = -Q @ xs
+        rec = np.concatenate([Q.ravel(), c, np.zeros(n)])
+        r = oracle.tron_solve(oracle.OBJ_DENSE, rec, -np.ones(n) * 10, np.ones(n) * 10,
+                              np.zeros(n), 1e3)
+        assert r["status"] == oracle.CONVERGED
+        assert r["iters"] == 1, r["iters"]
+        np.testing.assert_allclose(r["x"], xs, rtol=0, atol=1e-9)
+        assert r["counters"]["cg_iters"] == 1
+
+
 def test_converged_start_takes_no_iteration():
     n = 4
     Q = np.eye(n)
