@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ADMM, uneven-size and serving workloads")
+    ap.add_argument("--extras", default="admm,uneven,serving",
+                    help="comma-separated subset of admm, uneven, serving")
     ap.add_argument("--admm-iters", type=int, default=1000)
     ap.add_argument("--serve-seconds", type=float, default=0.25)
     ap.add_argument("--serve-max-iters", type=int, default=200)
@@ -455,9 +457,13 @@ def main():
         line["cpu_baseline"] = cb
     tb.close()
     if rank == 0 and world == 1 and not args.no_extras:
-        line["admm"] = bench_admm(args, dev)
-        line["uneven"] = bench_uneven(args, dev)
-        line["serving"] = bench_serving(args, dev)
+        extras = set(args.extras.split(","))
+        if "admm" in extras:
+            line["admm"] = bench_admm(args, dev)
+        if "uneven" in extras:
+            line["uneven"] = bench_uneven(args, dev)
+        if "serving" in extras:
+            line["serving"] = bench_serving(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
