@@ -34,10 +34,10 @@ N_VARS = 32
 L2_BYTES = 129 * 2 ** 20
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 # DRAM bytes per launch of the timed kernel from one ncu capture (profiles/
-# tron_dense32_n10000.md: 19.12 MB for 2,000 problems, scaled by 5 to the 10,000-problem
+# tron_dense32_n10000.md: 19.06 MB for 2,000 problems, scaled by 5 to the 10,000-problem
 # launch), valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES_PER_PROBLEM = 19.12e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "bd4d3cac65420469ed74d7f5087a22ed073b3570"
+TRAFFIC_BYTES_PER_PROBLEM = 19.057e6 / 2000
+TRAFFIC_SOURCES_SHA1 = "2965590b5f48a6a20e3977f6f42f9b976edc7f16"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
