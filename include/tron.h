@@ -112,7 +112,8 @@ typedef struct tron_options {
   int32_t cholesky;       /* 0      factorization form: 0 = per size class (right-looking
                                     up to n = 32, left-looking above), 1 = left-looking
                                     (Sec. 4.3), 2 = right-looking with the trailing update
-                                    spread over all lanes; all give the same bits         */
+                                    spread over all lanes; both factor the same matrix as
+                                    Lu D Lu^T and agree to rounding                       */
   int32_t reserved[6];    /* must be zero                                                */
 } tron_options_t;
 

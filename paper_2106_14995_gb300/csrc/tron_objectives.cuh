@@ -6,6 +6,8 @@
 //   load(gp, rec, n)    stage the packed record; returns false if it holds a non-finite
 //   eval_f(gp, y)       f(y); caches what the gradient needs; sets fsc, the sum of the
 //                       magnitudes of the terms f is assembled from (its rounding scale)
+//   kStepEval           eval_f_step(gp, y, s, Hs) is available: f(y) at y = x + s from
+//                       the product Hs = H(x) s the solver already holds
 //   grad_hess(gp, x, g) gradient at the point of the last eval_f, Hessian made current
 //   hq(i,j), hd(i)      Hessian entries at the current point
 //   hess_finite(gp)     all Hessian entries finite
@@ -28,10 +30,12 @@ struct DenseObj {
   static constexpr int LDQ = (G == 1) ? N : N + 1;
   static constexpr int SMEM = (QG ? 0 : N * LDQ) + 2 * N;  // Q, hd, staging
   static constexpr bool kHasHd = true;
+  static constexpr bool kStepEval = true;
 
   SV<G> Q, hdg, st;
   const double* __restrict__ qg;
   double c[R], d[R], qy[R];
+  double qx[R];  // Q x at the current (accepted) point
   double fsc;
   int n;
 
@@ -101,6 +105,20 @@ struct DenseObj {
   template <class GP>
   __device__ __forceinline__ double eval_f(const GP& gp, const double (&y)[R]) {
     qmul(gp, y, qy);
+    return f_from_qy(gp, y);
+  }
+
+  // f(x + s) without a product with Q: Q (x + s) = Q x + H s - diag(hd) s, H and hd at x
+  template <class GP>
+  __device__ __forceinline__ double eval_f_step(const GP& gp, const double (&y)[R],
+                                                const double (&s)[R], const double (&Hs)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) qy[r] = qx[r] + fma(-hdg[r * G + gp.t], s[r], Hs[r]);
+    return f_from_qy(gp, y);
+  }
+
+  template <class GP>
+  __device__ __forceinline__ double f_from_qy(const GP& gp, const double (&y)[R]) {
     double s = 0.0, m = 0.0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -117,6 +135,7 @@ struct DenseObj {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       double x2 = x[r] * x[r];
+      qx[r] = qy[r];
       g[r] = qy[r] + c[r] + 4.0 * d[r] * x2 * x[r];
       hdg[r * G + gp.t] = 12.0 * d[r] * x[r] * x[r];
     }
@@ -147,6 +166,7 @@ struct BranchObj {
   static constexpr int R = 4;
   static constexpr int SMEM = 36 + 16;  // record, Hessian
   static constexpr bool kHasHd = false;
+  static constexpr bool kStepEval = false;
 
   SV<1> rec, H;
   double cs, sn, F[4];
@@ -335,6 +355,7 @@ struct Hs45Obj {
   static constexpr int R = N;
   static constexpr int SMEM = N * N;
   static constexpr bool kHasHd = false;
+  static constexpr bool kStepEval = false;
 
   SV<1> H;
   double xc[N];

@@ -3,25 +3,27 @@
 // Per outer iteration, all on the device (Sec. 4.1: single kernel, no host traffic):
 //   projected-gradient max-norm test (Sec. 5.1) -> Cauchy point with the
 //   interpolation/extrapolation search (line 4) -> free set of the current point and
-//   gather of H_FF (line 5, Sec. 5.3) -> shifted complete Cholesky, left-looking, with
-//   L^T mirrored into the upper triangle (lines 6-7, Sec. 4.3, 4.4) -> Steihaug PCG in
-//   the preconditioned variables with the step kept inside ||w||_2 <= delta (lines 8-9)
-//   -> projected search (line 10) -> reduction ratio, acceptance and radius update.
+//   gather of H_FF (line 5, Sec. 5.3) -> shifted complete factorization, left- or
+//   right-looking, with the factor mirrored into the upper triangle (lines 6-7,
+//   Sec. 4.3, 4.4) -> Steihaug PCG with the step kept inside ||w||_2 <= delta
+//   (lines 8-9) -> projected search (line 10) -> reduction ratio, acceptance and
+//   radius update.
 //
 // Storage: the vectors of a problem are register arrays spread over the group (slot r
-// of lane t holds variable r*G + t); the factor L (with L^T mirrored) and the objective
-// data sit in the problem's shared-memory slice; the free-set indices are an int list
-// in shared memory.  Triangular solves read rows of the lower part (backward, L^T z = p)
-// or rows of the mirrored upper part (forward, L y = b), so every shared-memory access
-// of a solve is contiguous across the group (Sec. 4.4).
+// of lane t holds variable r*G + t); the factor (with its transpose mirrored) and the
+// objective data sit in the problem's shared-memory slice; the free-set indices are an
+// int list in shared memory.  Triangular solves read rows of the lower part (backward)
+// or rows of the mirrored upper part (forward), so every shared-memory access of a
+// solve is contiguous across the group (Sec. 4.4).
 //
 // FP64 economy on this GPU (a warp FP64 instruction costs the same issue slot with one
-// active lane or 32): the factorization is right-looking with the trailing update
-// spread over all lanes (the paper's left-looking form remains as options.cholesky =
-// 1 and gives the same bits); the pivot of each column costs one reciprocal square
-// root (hardware approximation + one Newton step), kept as 1/L_jj; the factor is
-// rescaled to unit diagonal so triangular solves issue one FMA per column; norms are
-// compared squared; dot products needed together are reduced in one fused butterfly.
+// active lane or 32): the factorization is the square-root-free form A = Lu D Lu^T of
+// the paper's L L^T, one reciprocal per pivot (hardware approximation + one Newton
+// step); the right-looking form spreads the trailing update over all lanes (the
+// paper's left-looking form remains as options.cholesky = 1); the PCG runs in the step
+// itself, where only M^-1 = Lu^-T D^-1 Lu^-1 is needed, and takes the exact-
+// preconditioner step directly when no shift was needed; norms are compared squared;
+// dot products needed together are reduced in one fused butterfly.
 #pragma once
 
 #include "../../include/tron.h"
@@ -192,29 +194,40 @@ struct Solver {
     return b >= 0x0010000000000000LL && b < 0x7FF0000000000000LL;
   }
 
-  // 1/sqrt of a pivot: the hardware approximation (relative error below 2^-20 on
-  // this GPU) refined by one Newton step for the reciprocal square root,
-  // y <- y (3/2 - a y^2 / 2), relative error below 2^-39.  The factor only
-  // preconditions the CG, so this accuracy leaves the solve's result unchanged, at
-  // four FP64 instructions per column.
-  __device__ __forceinline__ static double pivot_rsqrt(double a) {
+  // 1/d of a pivot: the hardware reciprocal approximation refined by one Newton-Raphson
+  // step y <- y + y (1 - d y), which squares its relative error; two FP64 instructions.
+  // Pivots from 2^1022 up (whose reciprocal the approximation flushes to zero) divide.
+  __device__ __forceinline__ static double pivot_rcp(double a) {
+    if (__double_as_longlong(a) >= 0x7FD0000000000000LL) return 1.0 / a;
     double y;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-    const double t = (a * y) * y;
-    return y * fma(-0.5, t, 1.5);
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    return fma(y, fma(-a, y, 1.0), y);
   }
 
-  // ------------------------------------------------------------ Cholesky (Sec. 4.3)
+  // ------------------------------------------------ LDL^T factorization (Sec. 4.3)
+  // A = Lu D Lu^T with Lu unit lower triangular: the strictly lower part of the factor
+  // storage holds Lu (mirrored into the upper triangle in the full layout), the
+  // diagonal holds D and dinv holds 1/D.  The paper's L L^T is Lu D^(1/2); the PCG
+  // below needs only M^-1 = Lu^-T D^-1 Lu^-1, so no square root is ever taken and each
+  // column costs one reciprocal.
+
   // left-looking: column j gathers the updates of columns 0..j-1 (read from the
-  // mirrored rows of L^T), then scales by 1/sqrt(pivot); L^T mirrored as it goes.
+  // mirrored rows of Lu^T) against row j of D Lu^T, which is formed first over the
+  // group; the pivots sit in dinv until the end, when all are inverted at once.
   __device__ __forceinline__ bool chol_left(int m) {
     for (int j = 0; j < m; ++j) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int k = r * G + gp.t;
+        if (k < j) vb[k] = lo(j, k) * dinv[k];
+      }
+      gp.sync();
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int c = r * G + gp.t;
         if (c >= j && c < m) {
           double v = lo(c, j);
-          for (int k = 0; k < j; ++k) v = fma(-mt(k, c), mt(k, j), v);
+          for (int k = 0; k < j; ++k) v = fma(-mt(k, c), vb[k], v);
           mt(j, c) = v;
         }
       }
@@ -224,27 +237,34 @@ struct Solver {
         gp.sync();
         return false;
       }
-      const double rs = pivot_rsqrt(piv);
+      const double ri = pivot_rcp(piv);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int c = r * G + gp.t;
         if (c > j && c < m) {
-          const double lcj = mt(j, c) * rs;
+          const double lcj = mt(j, c) * ri;
           mt(j, c) = lcj;
           if (!PK) lo(c, j) = lcj;
         }
       }
-      if (gp.t == (j & (G - 1))) dinv[j] = rs;
+      if (gp.t == (j & (G - 1))) dinv[j] = piv;
       gp.sync();
     }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = r * G + gp.t;
+      if (c < m) dinv[c] = pivot_rcp(dinv[c]);
+    }
+    gp.sync();
     return true;
   }
 
-  // right-looking with the trailing update spread over the whole group: after column j
-  // is scaled, the (m-j-1)(m-j)/2 elements of the trailing triangle are updated by
-  // all G lanes (element e of the triangle -> row cc, column dd), so no lane waits on
-  // the triangle's shape.  Every element receives the same fused multiply-adds in the
-  // same k order as in the left-looking form, hence the same factor bit for bit.
+  // right-looking with the trailing update spread over the whole group: after the pivot
+  // of column j is inverted, the (m-j-1)(m-j)/2 elements of the trailing triangle are
+  // updated by all G lanes (element e of the triangle -> row cc, column ec), so no lane
+  // waits on the triangle's shape.  The update a_cd -= Lu_cj (D_j Lu_dj) reads the scaled
+  // column from vb and the still unscaled one from the factor storage, which takes the
+  // scaled values once the update is done.
   __device__ __forceinline__ bool chol_right(int m) {
     for (int j = 0; j < m; ++j) {
       const double piv = lo(j, j);
@@ -252,17 +272,18 @@ struct Solver {
         gp.sync();
         return false;
       }
-      const double rs = pivot_rsqrt(piv);
+      const double ri = pivot_rcp(piv);
+      double lc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int c = r * G + gp.t;
+        lc[r] = 0.0;
         if (c > j && c < m) {
-          const double lcj = lo(c, j) * rs;
-          lo(c, j) = lcj;
-          if (!PK) mt(j, c) = lcj;
+          lc[r] = lo(c, j) * ri;
+          vb[c] = lc[r];
         }
       }
-      if (gp.t == (j & (G - 1))) dinv[j] = rs;
+      if (gp.t == (j & (G - 1))) dinv[j] = ri;
       gp.sync();
       const int M = m - j - 1;
       const int T = M * (M + 1) / 2;
@@ -270,18 +291,29 @@ struct Solver {
         int cc = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
         while (cc * (cc + 1) / 2 > e) --cc;
         while ((cc + 1) * (cc + 2) / 2 <= e) ++cc;
-        const int dd = e - cc * (cc + 1) / 2;
-        const int c = j + 1 + cc, d = j + 1 + dd;
-        lo(c, d) = fma(-lo(c, j), lo(d, j), lo(c, d));
+        const int ec = e - cc * (cc + 1) / 2;
+        const int c = j + 1 + cc, d = j + 1 + ec;
+        lo(c, d) = fma(-vb[c], lo(d, j), lo(c, d));
       }
       gp.sync();
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = r * G + gp.t;
+        if (c > j && c < m) {
+          lo(c, j) = lc[r];
+          if (!PK) mt(j, c) = lc[r];
+        }
+      }
     }
+    gp.sync();
     return true;
   }
 
-  // shifted factorization A + alpha I = L L^T, alpha from the sequence
-  // 0 (or beta - min A_ii), then max(2 alpha, beta), beta = shift_frac * max |A_ii|
-  __device__ __forceinline__ bool factor(int m) {
+  // shifted factorization A + alpha I = Lu D Lu^T, alpha from the sequence
+  // 0 (or beta - min A_ii), then max(2 alpha, beta), beta = shift_frac * max |A_ii|.
+  // Returns 0 when every shift failed, 1 for a factor of A itself (alpha = 0), 2 for a
+  // shifted one.
+  __device__ __forceinline__ int factor(int m) {
     // the first shift is 0 when every diagonal entry is positive (decided by a vote);
     // the max/min reductions that set beta are paid only when a shift is needed
     bool nonpos = false;
@@ -337,76 +369,46 @@ struct Solver {
       gp.sync();
       // options.cholesky: 1 left-looking, 2 right-looking, 0 the size class's default
       const bool right = (o.cholesky == 2) || (o.cholesky == 0 && N <= 32);
-      if (right ? chol_right(m) : chol_left(m)) {
-        unitize(m);
-        return true;
-      }
+      if (right ? chol_right(m) : chol_left(m)) return alpha == 0.0 ? 1 : 2;
       if (!have_beta) shift_stats();
       alpha = fmax(2.0 * alpha, beta);
     }
-    return false;
+    return 0;
   }
 
-  // After a successful factorization the strictly lower part (and its mirror) is
-  // scaled column by column to the unit-diagonal factor Lu = L D^-1, D = diag(L_jj),
-  // spread over all lanes like the trailing update.  The solves then need one FMA per
-  // column plus one diagonal scaling: L y = b is Lu (D y) = b, and L^T z = p is
-  // Lu^T z = D^-1 p.
-  __device__ __forceinline__ void unitize(int m) {
-    const int T = m * (m - 1) / 2;
-    for (int e = gp.t; e < T; e += G) {
-      int c = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
-      while (c * (c - 1) / 2 > e) --c;
-      while ((c + 1) * c / 2 <= e) ++c;
-      const int j = e - c * (c - 1) / 2;  // 0 <= j < c
-      const double v = lo(c, j) * dinv[j];
-      lo(c, j) = v;
-      if (!PK) mt(j, c) = v;
-    }
-    gp.sync();
-  }
-
-  // b <- L^-1 b: unit forward substitution with Lu (column j of Lu is row j of the
-  // mirrored upper part), then b <- D^-1 b
-  __device__ __forceinline__ void solve_L(int m, double (&b)[R]) {
+  // v <- M^-1 v, M = Lu D Lu^T: unit forward substitution with Lu (column j of Lu is
+  // row j of the mirrored upper part), v <- D^-1 v, unit backward substitution with
+  // Lu^T (column j of Lu^T is row j of Lu); every shared-memory read of a column is
+  // contiguous across the group (Sec. 4.4)
+  __device__ __forceinline__ void precond(int m, double (&v)[R]) {
 #pragma unroll
     for (int rj = 0; rj < R; ++rj) {
       for (int tj = 0; tj < G; ++tj) {
         const int j = rj * G + tj;
         if (j >= m) break;
-        const double uj = gp.bcast(b[rj], tj);
+        const double vj = gp.bcast(v[rj], tj);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int c = r * G + gp.t;
-          if (c > j && c < m) b[r] = fma(-mt(j, c), uj, b[r]);
+          if (c > j && c < m) v[r] = fma(-mt(j, c), vj, v[r]);
         }
       }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int c = r * G + gp.t;
-      if (c < m) b[r] = b[r] * dinv[c];
-    }
-  }
-
-  // z <- L^-T z: z <- D^-1 z, then unit backward substitution with Lu^T (column j of
-  // Lu^T is row j of Lu)
-  __device__ __forceinline__ void solve_Lt(int m, double (&z)[R]) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int c = r * G + gp.t;
-      if (c < m) z[r] = z[r] * dinv[c];
+      if (c < m) v[r] = v[r] * dinv[c];
     }
 #pragma unroll
     for (int rj = R - 1; rj >= 0; --rj) {
       for (int tj = G - 1; tj >= 0; --tj) {
         const int j = rj * G + tj;
         if (j >= m) continue;
-        const double zj = gp.bcast(z[rj], tj);
+        const double vj = gp.bcast(v[rj], tj);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int c = r * G + gp.t;
-          if (c < j) z[r] = fma(-lo(j, c), zj, z[r]);
+          if (c < j) v[r] = fma(-lo(j, c), vj, v[r]);
         }
       }
     }
@@ -430,47 +432,60 @@ struct Solver {
     return (ptx >= 0.0) ? (dsq - xtx) / (ptx + rad) : (rad - ptx) / ptp;
   }
 
-  // Steihaug PCG on Ahat = L^-1 A L^-T, bhat given; w = L^-T s accumulated directly.
+  // Steihaug PCG (lines 8-9) for min rF'w + 1/2 w'Aw, ||w||_2 <= delta, run in the step
+  // w itself with the preconditioner M = A + alpha I = L L^T.  With phat = L^T p and
+  // rhat = L^-1 res this is CG on Ahat = L^-1 A L^-T in s = L^T w step for step: the
+  // same step lengths (rhat'rhat = res'M^-1 res, phat'Ahat phat = p'Ap), the same exits
+  // and the same w, which the trust region bounds directly.  When alpha = 0, M = A and
+  // Ahat = I: the first step, of length 1 along M^-1 res, is the minimiser and leaves a
+  // zero residual, so it is taken without forming A p.
   // Returns 0 converged, 1 iteration cap, 2 boundary, 3 negative curvature.
-  __device__ __forceinline__ int steihaug(int m, double delta, const double (&bh)[R],
-                                          double (&w)[R]) {
-    double res[R], p[R], z[R], q[R];
+  __device__ __forceinline__ int steihaug(int m, double delta, bool exact,
+                                          const double (&rF)[R], double (&w)[R]) {
+    double res[R], z[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       w[r] = 0.0;
-      res[r] = -bh[r];
-      p[r] = res[r];
+      res[r] = -rF[r];
+      z[r] = res[r];
     }
-    double rr = dotv(res, res);
-    const double tol2 = (o.cg_rtol * o.cg_rtol) * rr;  // ||res|| <= cg_rtol ||bhat||, squared
+    precond(m, z);
     const double dsq = delta * delta;
+    if (exact) {
+      const double zz = dotv(z, z);
+      const double sg = (zz >= dsq) ? delta / sqrt(zz) : 1.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) w[r] = sg * z[r];
+      return (zz >= dsq) ? 2 : 0;
+    }
+    double p[R], q[R];
+    double rz = dotv(res, z);
+    const double tol2 = (o.cg_rtol * o.cg_rtol) * rz;  // ||rhat|| <= cg_rtol ||rhat_0||, squared
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r] = z[r];
     int info = 1;
     for (int it = 0; it < m; ++it) {
-      if (rr <= tol2) {
+      if (rz <= tol2) {
         info = 0;
         break;
       }
-#pragma unroll
-      for (int r = 0; r < R; ++r) z[r] = p[r];
-      solve_Lt(m, z);
-      hv_free(m, z, q);
-      solve_L(m, q);
+      hv_free(m, p, q);
       const double kappa = dotv(p, q);
       if (kappa <= 0.0) {
-        const double sg = trqsol(w, z, delta);
+        const double sg = trqsol(w, p, delta);
 #pragma unroll
-        for (int r = 0; r < R; ++r) w[r] = fma(sg, z[r], w[r]);
+        for (int r = 0; r < R; ++r) w[r] = fma(sg, p[r], w[r]);
         info = 3;
         break;
       }
-      const double alpha = rr / kappa;
+      const double alpha = rz / kappa;
       double wn[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) wn[r] = fma(alpha, z[r], w[r]);
+      for (int r = 0; r < R; ++r) wn[r] = fma(alpha, p[r], w[r]);
       if (dotv(wn, wn) >= dsq) {
-        const double sg = trqsol(w, z, delta);
+        const double sg = trqsol(w, p, delta);
 #pragma unroll
-        for (int r = 0; r < R; ++r) w[r] = fma(sg, z[r], w[r]);
+        for (int r = 0; r < R; ++r) w[r] = fma(sg, p[r], w[r]);
         info = 2;
         break;
       }
@@ -478,12 +493,14 @@ struct Solver {
       for (int r = 0; r < R; ++r) {
         w[r] = wn[r];
         res[r] = fma(-alpha, q[r], res[r]);
+        z[r] = res[r];
       }
-      const double rrn = dotv(res, res);
-      const double beta = rrn / rr;
-      rr = rrn;
+      precond(m, z);
+      const double rzn = dotv(res, z);
+      const double beta = rzn / rz;
+      rz = rzn;
 #pragma unroll
-      for (int r = 0; r < R; ++r) p[r] = fma(beta, p[r], res[r]);
+      for (int r = 0; r < R; ++r) p[r] = fma(beta, p[r], z[r]);
     }
     return info;
   }
@@ -647,15 +664,13 @@ struct Solver {
         }
         gp.sync();
         if (pass == 0) rF0 = dotv(rF, rF);  // squared
-        if (!factor(m)) {
+        const int fac = factor(m);
+        if (fac == 0) {
           status = TRON_CHOL_FAIL;
           break;
         }
-        double bh[R], wF[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) bh[r] = rF[r];
-        solve_L(m, bh);
-        const int info = steihaug(m, delta, bh, wF);
+        double wF[R];
+        const int info = steihaug(m, delta, fac == 1, rF, wF);
         // scatter w_F to the full direction w
 #pragma unroll
         for (int r = 0; r < R; ++r) vb[r * G + gp.t] = 0.0;
@@ -715,17 +730,20 @@ struct Solver {
       // ---- reduction ratio, acceptance, radius
       // q(s) = g's + 1/2 s'Hs with s = y - x; the model gradient rv = g + H s was
       // accumulated along the steps, so H s = rv - g needs no further product
-      double s2[R], gts = 0.0, sHs = 0.0, ss2 = 0.0;
+      double s2[R], hs2[R], gts = 0.0, sHs = 0.0, ss2 = 0.0;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         s2[r] = y[r] - x[r];
+        hs2[r] = rv[r] - g[r];
         gts = fma(g[r], s2[r], gts);
-        sHs = fma(s2[r], rv[r] - g[r], sHs);
+        sHs = fma(s2[r], hs2[r], sHs);
         ss2 = fma(s2[r], s2[r], ss2);
       }
       gp.sum3(gts, sHs, ss2);
       const double qs = gts + 0.5 * sHs;
-      const double fy = obj.eval_f(gp, y);
+      double fy;
+      if constexpr (Obj::kStepEval) fy = obj.eval_f_step(gp, y, s2, hs2);
+      else fy = obj.eval_f(gp, y);
       const double fsy = obj.fsc;
       // ratio guarded by the rounding level of f (Conn, Gould and Toint, Trust-Region
       // Methods, Sec. 17.4.2), measured on the magnitudes of the terms of f
@@ -733,7 +751,6 @@ struct Solver {
       const double ared = f - fy;
       const double fl = o.ared_guard * fmax(fs, 1.0);
       const double rho = (pred > 0.0 && isfinite(fy)) ? (ared + fl) / (pred + fl) : -CUDART_INF;
-      const double snorm = sqrt(ss2);
       if (rho > o.eta0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = y[r];
@@ -745,9 +762,11 @@ struct Solver {
           break;
         }
       }
+      // (||s|| >= 0.99 delta compared squared; the norm itself only when it sets delta)
+      const double d99 = 0.99 * delta;
       if (rho < o.eta1) {
-        delta = o.sigma1 * fmin(snorm, delta);
-      } else if (rho > o.eta2 && snorm >= 0.99 * delta) {
+        delta = o.sigma1 * fmin(sqrt(ss2), delta);
+      } else if (rho > o.eta2 && ss2 >= d99 * d99) {
         delta = fmin(o.sigma3 * delta, o.delta_max);
       }
       // delta < c (1 + ||x||), decided without a square root:
