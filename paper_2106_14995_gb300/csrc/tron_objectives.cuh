@@ -94,9 +94,14 @@ struct DenseObj {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = r * G + gp.t;
-        double s = 0.0;
-        for (int j = 0; j < n; ++j) s = fma(hq(i, j), st[j], s);
-        y[r] = s;
+        double s0 = 0.0, s1 = 0.0;  // two chains: half the dependent FMA latency
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+          s0 = fma(hq(i, j), st[j], s0);
+          s1 = fma(hq(i, j + 1), st[j + 1], s1);
+        }
+        if (j < n) s0 = fma(hq(i, j), st[j], s0);
+        y[r] = s0 + s1;
       }
       gp.sync();
     }
@@ -126,8 +131,9 @@ struct DenseObj {
       s += y[r] * (0.5 * qy[r] + c[r]) + d[r] * y2 * y2;
       m += 0.5 * fabs(y[r] * qy[r]) + fabs(c[r] * y[r]) + fabs(d[r]) * y2 * y2;
     }
-    fsc = gp.sum(m);
-    return gp.sum(s);
+    gp.sum2(s, m);
+    fsc = m;
+    return s;
   }
 
   template <class GP>

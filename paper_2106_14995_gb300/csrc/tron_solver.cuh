@@ -159,10 +159,15 @@ struct Solver {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = r * G + gp.t;
-        double s = 0.0;
-        for (int j = 0; j < n; ++j) s = fma(obj.hq(i, j), vb[j], s);
-        if (Obj::kHasHd) s = fma(obj.hd(i), v[r], s);
-        y[r] = s;
+        double s0 = 0.0, s1 = 0.0;  // two chains: half the dependent FMA latency
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+          s0 = fma(obj.hq(i, j), vb[j], s0);
+          s1 = fma(obj.hq(i, j + 1), vb[j + 1], s1);
+        }
+        if (j < n) s0 = fma(obj.hq(i, j), vb[j], s0);
+        if (Obj::kHasHd) s0 = fma(obj.hd(i), v[r], s0);
+        y[r] = s0 + s1;
       }
       gp.sync();
     }
@@ -179,8 +184,15 @@ struct Solver {
       double s = 0.0;
       if (c < m) {
         const int i = Fi[c];
-        for (int d = 0; d < m; ++d) s = fma(obj.hq(i, Fi[d]), vb[d], s);
+        double s1 = 0.0;
+        int d = 0;
+        for (; d + 1 < m; d += 2) {
+          s = fma(obj.hq(i, Fi[d]), vb[d], s);
+          s1 = fma(obj.hq(i, Fi[d + 1]), vb[d + 1], s1);
+        }
+        if (d < m) s = fma(obj.hq(i, Fi[d]), vb[d], s);
         if (Obj::kHasHd) s = fma(obj.hd(i), z[r], s);
+        s += s1;
       }
       q[r] = s;
     }
@@ -579,6 +591,11 @@ struct Solver {
     }
     double alpha_c = 1.0;
     int status = TRON_MAX_ITER;
+    // ||x||^2 <= xb2 for every x in the box (infinite when a bound is)
+    double xb2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) xb2 = fma(fmax(fabs(l[r]), fabs(u[r])), fmax(fabs(l[r]), fabs(u[r])), xb2);
+    xb2 = gp.sum(xb2);
 
     for (;;) {
       // ||grad_P f||_inf <= gtol decided by a vote of the lanes; the norm itself is
@@ -770,10 +787,11 @@ struct Solver {
         delta = fmin(o.sigma3 * delta, o.delta_max);
       }
       // delta < c (1 + ||x||), decided without a square root:
-      // delta - c < 0, or (delta - c)^2 < c^2 ||x||^2
-      const double xx = dotv(x, x);
+      // delta - c < 0, or (delta - c)^2 < c^2 ||x||^2; ||x|| is reduced only when the
+      // box bound xb2 cannot decide
       const double dc = delta - o.delta_min_rel;
-      if (dc < 0.0 || dc * dc < (o.delta_min_rel * o.delta_min_rel) * xx) {
+      const double c2 = o.delta_min_rel * o.delta_min_rel;
+      if (dc < 0.0 || (dc * dc < c2 * xb2 && dc * dc < c2 * dotv(x, x))) {
         status = TRON_TR_TOO_SMALL;
         break;
       }
