@@ -108,7 +108,8 @@ typedef struct tron_options {
   int32_t schedule;       /* TRON_SCHED_PLAIN                                            */
   int32_t warps_per_block;/* 0      CTA size in warps (0 = library's choice)             */
   int32_t layout;         /* 0      kernel storage variant: 0 = library's choice, else
-                                    1 + bits (bit 0: packed factor, bit 1: Q in global)  */
+                                    1 + bits (bit 0: packed factor, bit 1: Q in global,
+                                    bit 2: Q as wrapped diagonals, n <= 32 only)         */
   int32_t cholesky;       /* 0      factorization form: 0 = per size class (right-looking
                                     up to n = 32, left-looking above), 1 = left-looking
                                     (Sec. 4.3), 2 = right-looking with the trailing update
@@ -190,7 +191,8 @@ tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const do
                                const double* d_delta0, int32_t sample, void* stream);
 
 /* Size classes of the batch and the variant each will run with. layout bits: 1 = packed
- * factor, 2 = Q read from global memory; bits 2-3: the options.cholesky value used. */
+ * factor, 2 = Q read from global memory, 4 = Q as wrapped diagonals in shared memory;
+ * bits 3-4: the options.cholesky value used. */
 int32_t tron_batch_buckets(const tron_batch_t* b);
 tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t* N, int32_t* G,
                                  int32_t* layout, int32_t* warps_per_block, int64_t* count);

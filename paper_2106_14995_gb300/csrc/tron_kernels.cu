@@ -170,8 +170,9 @@ __global__ void __launch_bounds__(256) k_tron_persistent(const KArgs a) {
 }
 
 // ------------------------------------------------------------------ dispatch table
-// layout bits of a kernel variant: bit 0 = packed factor, bit 1 = Q read from global
-enum { kLayoutPacked = 1, kLayoutQGlobal = 2 };
+// layout bits of a kernel variant: bit 0 = packed factor, bit 1 = Q read from global,
+// bit 2 = Q as wrapped diagonals in shared memory
+enum { kLayoutPacked = 1, kLayoutQGlobal = 2, kLayoutQDiag = 4 };
 
 struct KernelEntry {
   int kind, N, G, layout;
@@ -233,18 +234,20 @@ static std::vector<KernelEntry>& table() {
       make_entry<DenseObj<16, 8>, 16, 8, false>(TRON_OBJ_DENSE_QUARTIC, 0),
       make_entry<DenseObj<32, 32>, 32, 32, false>(TRON_OBJ_DENSE_QUARTIC, 0),
       make_entry<DenseObj<32, 32>, 32, 32, true>(TRON_OBJ_DENSE_QUARTIC, kLayoutPacked),
-      make_entry<DenseObj<32, 32, true>, 32, 32, true>(TRON_OBJ_DENSE_QUARTIC,
+      make_entry<DenseObj<32, 32, kQDiag>, 32, 32, true>(TRON_OBJ_DENSE_QUARTIC,
+                                                        kLayoutPacked | kLayoutQDiag),
+      make_entry<DenseObj<32, 32, kQGlobal>, 32, 32, true>(TRON_OBJ_DENSE_QUARTIC,
                                                       kLayoutPacked | kLayoutQGlobal),
       make_entry<DenseObj<32, 16>, 32, 16, false>(TRON_OBJ_DENSE_QUARTIC, 0),
-      make_entry<DenseObj<64, 64, true>, 64, 64, true>(TRON_OBJ_DENSE_QUARTIC,
+      make_entry<DenseObj<64, 64, kQGlobal>, 64, 64, true>(TRON_OBJ_DENSE_QUARTIC,
                                                       kLayoutPacked | kLayoutQGlobal),
       make_entry<DenseObj<64, 64>, 64, 64, true>(TRON_OBJ_DENSE_QUARTIC, kLayoutPacked),
-      make_entry<DenseObj<64, 32, true>, 64, 32, true>(TRON_OBJ_DENSE_QUARTIC,
+      make_entry<DenseObj<64, 32, kQGlobal>, 64, 32, true>(TRON_OBJ_DENSE_QUARTIC,
                                                       kLayoutPacked | kLayoutQGlobal),
       make_entry<DenseObj<64, 32>, 64, 32, true>(TRON_OBJ_DENSE_QUARTIC, kLayoutPacked),
-      make_entry<DenseObj<128, 128, true>, 128, 128, true>(TRON_OBJ_DENSE_QUARTIC,
+      make_entry<DenseObj<128, 128, kQGlobal>, 128, 128, true>(TRON_OBJ_DENSE_QUARTIC,
                                                           kLayoutPacked | kLayoutQGlobal),
-      make_entry<DenseObj<128, 32, true>, 128, 32, true>(TRON_OBJ_DENSE_QUARTIC,
+      make_entry<DenseObj<128, 32, kQGlobal>, 128, 32, true>(TRON_OBJ_DENSE_QUARTIC,
                                                         kLayoutPacked | kLayoutQGlobal),
       make_entry<Hs45Obj<8>, 8, 1, false>(TRON_OBJ_HS45, 0),
   };
@@ -332,7 +335,7 @@ static tron_err_t check_options(const tron_options_t* o) {
              TRON_EINVAL, "options.schedule must be TRON_SCHED_PLAIN or TRON_SCHED_PERSISTENT");
   XT_REQUIRE(o->warps_per_block >= 0 && o->warps_per_block <= 8, TRON_EINVAL,
              "options.warps_per_block must be in [0, 8]");
-  XT_REQUIRE(o->layout >= 0 && o->layout <= 4, TRON_EINVAL, "options.layout must be in [0, 4]");
+  XT_REQUIRE(o->layout >= 0 && o->layout <= 8, TRON_EINVAL, "options.layout must be in [0, 8]");
   XT_REQUIRE(o->cholesky >= 0 && o->cholesky <= 2, TRON_EINVAL,
              "options.cholesky must be 0, 1 or 2");
   return TRON_OK;
@@ -638,7 +641,7 @@ tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t*
   if (layout) {
     const int chol = (bk.tuned && b->opt.group == 0 && b->opt.cholesky == 0) ? bk.tuned_chol
                                                                              : b->opt.cholesky;
-    *layout = ke->layout | (chol << 2);
+    *layout = ke->layout | (chol << 3);
   }
   if (warps_per_block) *warps_per_block = wpb;
   if (count) *count = bk.count;

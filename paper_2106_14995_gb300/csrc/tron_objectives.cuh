@@ -18,17 +18,27 @@
 namespace xt {
 
 // ------------------------------------------------------------------ dense quartic
-// f = 1/2 x'Qx + c'x + sum_i d_i x_i^4, record [Q (n x n) | c | d].
-// QG = false: Q is staged once in shared memory (odd stride, conflict-free columns).
-// QG = true: Q stays in global memory (L2-resident while the problem runs) and is read
-// column-wise -- Q(i, j) as Q[j][i], Q being symmetric -- so the lanes of a group read
-// consecutive doubles; used where the factor alone fills the shared memory.
+// f = 1/2 x'Qx + c'x + sum_i d_i x_i^4, record [Q (n x n) | c | d], Q symmetric.
+// Storage of Q (QL):
+//   kQShared: staged once in shared memory (odd stride, conflict-free columns).
+//   kQGlobal: left in global memory (L2-resident while the problem runs) and read
+//             column-wise -- Q(i, j) as Q[j][i] -- so the lanes of a group read
+//             consecutive doubles; used where the factor alone fills the shared memory.
+//   kQDiag:   (one variable per lane, G = N <= 32) the wrapped diagonals
+//             D_k[i] = Q(i, (i + k) mod n), k = 0..n/2, in shared memory: about half of
+//             kQShared, so more problems fit on an SM.  Q(i, j) for (j - i) mod n > n/2 is
+//             D_{n-k}[j] by symmetry; a product walks the diagonals, and every access of
+//             the group is a rotation of one diagonal (conflict free).
 // The Hessian is Q + diag(12 d_i x_i^2), kept as Q plus a diagonal vector.
-template <int N, int G, bool QG = false>
+enum { kQShared = 0, kQGlobal = 1, kQDiag = 2 };
+
+template <int N, int G, int QL = kQShared>
 struct DenseObj {
+  static_assert(QL != kQDiag || (G == N && N <= 32), "diagonal storage needs G = N <= 32");
   static constexpr int R = N / G;
   static constexpr int LDQ = (G == 1) ? N : N + 1;
-  static constexpr int SMEM = (QG ? 0 : N * LDQ) + 2 * N;  // Q, hd, staging
+  static constexpr int QSZ = QL == kQShared ? N * LDQ : (QL == kQDiag ? N * (N / 2 + 1) : 0);
+  static constexpr int SMEM = QSZ + 2 * N;  // Q, hd, staging
   static constexpr bool kHasHd = true;
   static constexpr bool kStepEval = true;
 
@@ -41,8 +51,8 @@ struct DenseObj {
 
   __device__ __forceinline__ void bind(SV<G> base) {
     Q = base;
-    hdg = base.at(QG ? 0 : N * LDQ);
-    st = base.at((QG ? 0 : N * LDQ) + N);
+    hdg = base.at(QSZ);
+    st = base.at(QSZ + N);
   }
 
   template <class GP>
@@ -51,8 +61,22 @@ struct DenseObj {
     qg = rec;
     bool fin = true;
     const int nn = n * n;
-    if constexpr (QG) {
+    if constexpr (QL == kQGlobal) {
       for (int e = gp.t; e < nn; e += G) fin = fin && isfinite(__ldg(rec + e));
+    } else if constexpr (QL == kQDiag) {
+      // lane i gathers D_k[i] = Q(i, (i + k) mod n); entries outside n x n are zero
+      for (int e = gp.t; e < nn; e += G) fin = fin && isfinite(__ldg(rec + e));
+      const int i = gp.t;
+#pragma unroll 4
+      for (int k = 0; k <= N / 2; ++k) {
+        double v = 0.0;
+        if (i < n && 2 * k <= n) {
+          int j = i + k;
+          if (j >= n) j -= n;
+          v = __ldg(rec + i * n + j);
+        }
+        Q[k * N + i] = v;
+      }
     } else {
       // zero the padding rows/columns, then copy Q (coalesced over the group)
       for (int e = gp.t; e < N * LDQ; e += G) Q[e] = 0.0;
@@ -76,6 +100,34 @@ struct DenseObj {
     return !gp.any(!fin);
   }
 
+  // sum_j Q(i, j) v[j] for row i of this lane (G >= 2; v staged in shared memory), two
+  // independent FMA chains
+  __device__ __forceinline__ double row_dot(int i, SV<G> v) const {
+    double s0 = 0.0, s1 = 0.0;
+    if constexpr (QL == kQDiag) {
+      if (i < n) {
+        // k = t <= n/2: D_t[i] v[(i + t) mod n]; k = t + n/2 + 1: Q(i, j) = D_{n-k}[j]
+        const int h = n >> 1;
+        int j0 = i, j1 = i + h + 1;
+        if (j1 >= n) j1 -= n;
+        for (int t = 0; t <= h; ++t) {
+          s0 = fma(Q[t * N + i], v[j0], s0);
+          if (t + h + 1 < n) s1 = fma(Q[(n - t - h - 1) * N + j1], v[j1], s1);
+          j0 = (j0 + 1 == n) ? 0 : j0 + 1;
+          j1 = (j1 + 1 == n) ? 0 : j1 + 1;
+        }
+      }
+    } else {
+      int j = 0;
+      for (; j + 1 < n; j += 2) {
+        s0 = fma(hq(i, j), v[j], s0);
+        s1 = fma(hq(i, j + 1), v[j + 1], s1);
+      }
+      if (j < n) s0 = fma(hq(i, j), v[j], s0);
+    }
+    return s0 + s1;
+  }
+
   // y_i = sum_j Q_ij v_j for the slots of this lane (v staged in st for G >= 2)
   template <class GP>
   __device__ __forceinline__ void qmul(const GP& gp, const double (&v)[R], double (&y)[R]) {
@@ -92,17 +144,7 @@ struct DenseObj {
       for (int r = 0; r < R; ++r) st[r * G + gp.t] = v[r];
       gp.sync();
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = r * G + gp.t;
-        double s0 = 0.0, s1 = 0.0;  // two chains: half the dependent FMA latency
-        int j = 0;
-        for (; j + 1 < n; j += 2) {
-          s0 = fma(hq(i, j), st[j], s0);
-          s1 = fma(hq(i, j + 1), st[j + 1], s1);
-        }
-        if (j < n) s0 = fma(hq(i, j), st[j], s0);
-        y[r] = s0 + s1;
-      }
+      for (int r = 0; r < R; ++r) y[r] = row_dot(r * G + gp.t, st);
       gp.sync();
     }
   }
@@ -149,8 +191,16 @@ struct DenseObj {
   }
 
   __device__ __forceinline__ double hq(int i, int j) const {
-    if constexpr (QG) return (i < n && j < n) ? __ldg(qg + (size_t)j * n + i) : 0.0;
-    else return Q[i * LDQ + j];
+    if constexpr (QL == kQGlobal) {
+      return (i < n && j < n) ? __ldg(qg + (size_t)j * n + i) : 0.0;
+    } else if constexpr (QL == kQDiag) {
+      if (i >= n || j >= n) return 0.0;
+      int k = j - i;
+      if (k < 0) k += n;
+      return (2 * k <= n) ? Q[k * N + i] : Q[(n - k) * N + j];
+    } else {
+      return Q[i * LDQ + j];
+    }
   }
   __device__ __forceinline__ double hd(int i) const { return hdg[i]; }
 

@@ -159,15 +159,9 @@ struct Solver {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = r * G + gp.t;
-        double s0 = 0.0, s1 = 0.0;  // two chains: half the dependent FMA latency
-        int j = 0;
-        for (; j + 1 < n; j += 2) {
-          s0 = fma(obj.hq(i, j), vb[j], s0);
-          s1 = fma(obj.hq(i, j + 1), vb[j + 1], s1);
-        }
-        if (j < n) s0 = fma(obj.hq(i, j), vb[j], s0);
-        if (Obj::kHasHd) s0 = fma(obj.hd(i), v[r], s0);
-        y[r] = s0 + s1;
+        double s = obj.row_dot(i, vb);
+        if (Obj::kHasHd) s = fma(obj.hd(i), v[r], s);
+        y[r] = s;
       }
       gp.sync();
     }
@@ -197,6 +191,66 @@ struct Solver {
       q[r] = s;
     }
     gp.sync();
+  }
+
+  // y = H v for a v with few nonzero coordinates: one column of H per nonzero (lanes
+  // read column j of Q across the group); false, with nothing computed, when more than
+  // N/4 coordinates are nonzero or for groups wider than a warp or a single lane
+  __device__ __forceinline__ bool hv_sparse(const double (&v)[R], double (&y)[R]) {
+    if constexpr (G == 1 || G > 32) {
+      return false;
+    } else {
+      unsigned msk[R];
+      int cnt = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        msk[r] = gp.ballot(v[r] != 0.0);
+        cnt += __popc(msk[r]);
+      }
+      if (cnt > N / 4) return false;
+#pragma unroll
+      for (int r = 0; r < R; ++r) y[r] = 0.0;
+#pragma unroll
+      for (int rj = 0; rj < R; ++rj) {
+        unsigned mm = msk[rj];
+        while (mm) {
+          const int tj = __ffs(mm) - 1;
+          mm &= mm - 1u;
+          const int j = rj * G + tj;
+          const double vj = gp.bcast(v[rj], tj);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int i = r * G + gp.t;
+            double hij = obj.hq(i, j);
+            if (Obj::kHasHd && i == j) hij = hij + obj.hd(i);
+            y[r] = fma(hij, vj, y[r]);
+          }
+        }
+      }
+      return true;
+    }
+  }
+
+  // Along a projected path the trial steps scale with the step length wherever neither
+  // trial is clipped by the box (sn = kap so there, up to rounding), so H sn is
+  // kap H so plus the columns of the coordinates clipped in either trial (cl), with
+  // the full product when those are many.  Hs holds H so on entry, H sn on exit.
+  __device__ __forceinline__ void rescaled_product(const double (&sn)[R], double kap,
+                                                   const double (&so)[R], const bool (&cl)[R],
+                                                   double (&Hs)[R]) {
+    if constexpr (G == 1 || G > 32) {
+      hv(sn, Hs);
+      return;
+    }
+    double dl[R], Hd[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dl[r] = cl[r] ? fma(-kap, so[r], sn[r]) : 0.0;
+    if (hv_sparse(dl, Hd)) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) Hs[r] = fma(kap, Hs[r], Hd[r]);
+    } else {
+      hv(sn, Hs);
+    }
   }
 
   // pivot test on the bit pattern (no FP64 compare): a positive, normal, finite value;
@@ -517,16 +571,36 @@ struct Solver {
     return info;
   }
 
-  // Cauchy trial s(alpha) = P[x - alpha g] - x: q(s) <= mu0 g's and ||s|| <= mu1 delta
+  // Cauchy trial s(alpha) = P[x - alpha g] - x: q(s) <= mu0 g's and ||s|| <= mu1 delta.
+  // kap = 0 for the first trial of a search (full product); otherwise alpha is kap times
+  // the step length of the trial held in s, Hs, cl (clipped coordinates), and H s is
+  // rescaled from it.
   __device__ __forceinline__ bool cauchy_try(double alpha, const double (&x)[R],
                                              const double (&g)[R], double delta,
-                                             double (&s)[R], double (&Hs)[R]) {
+                                             double (&s)[R], double (&Hs)[R], bool (&cl)[R],
+                                             double kap) {
+    double sn[R];
+    bool cn[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) s[r] = P(fma(alpha, -g[r], x[r]), r) - x[r];
-    hv(s, Hs);
+    for (int r = 0; r < R; ++r) {
+      const double v = fma(alpha, -g[r], x[r]);
+      const long long k = okey(v);
+      cn[r] = (k < kl[r]) || (k > ku[r]);
+      sn[r] = P(v, r) - x[r];
+    }
+    if (kap != 0.0) {
+      bool both[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) both[r] = cn[r] || cl[r];
+      rescaled_product(sn, kap, s, both, Hs);
+    } else {
+      hv(sn, Hs);
+    }
     double gts = 0.0, sHs = 0.0, ss = 0.0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      s[r] = sn[r];
+      cl[r] = cn[r];
       gts = fma(g[r], s[r], gts);
       sHs = fma(s[r], Hs[r], sHs);
       ss = fma(s[r], s[r], ss);
@@ -612,8 +686,9 @@ struct Solver {
 
       // ---- Cauchy point (line 4)
       double s[R], Hs[R];
+      bool cl[R];
       double alpha = alpha_c;
-      if (cauchy_try(alpha, x, g, delta, s, Hs)) {
+      if (cauchy_try(alpha, x, g, delta, s, Hs, cl, 0.0)) {
         const double bmax = brptmax(x, g);
         double sb[R], Hsb[R];
 #pragma unroll
@@ -624,7 +699,7 @@ struct Solver {
         for (int t = 0; t < o.max_trials; ++t) {
           if (!(alpha < bmax)) break;
           const double a2 = alpha * o.extrapf;
-          if (!cauchy_try(a2, x, g, delta, s, Hs)) break;
+          if (!cauchy_try(a2, x, g, delta, s, Hs, cl, o.extrapf)) break;
           alpha = a2;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
@@ -640,7 +715,7 @@ struct Solver {
       } else {
         for (int t = 0; t < o.max_trials; ++t) {
           alpha = alpha * o.interpf;
-          if (cauchy_try(alpha, x, g, delta, s, Hs)) break;
+          if (cauchy_try(alpha, x, g, delta, s, Hs, cl, o.interpf)) break;
         }
       }
       alpha_c = alpha;
@@ -706,13 +781,33 @@ struct Solver {
         double beta = 1.0;
         bool found = false;
         double yt[R], d[R], Hd[R];
+        bool dcl[R];
         for (int t = 0; t < o.max_trials; ++t) {
+          double dn[R];
+          bool cn[R];
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            yt[r] = P(fma(beta, w[r], y[r]), r);
-            d[r] = yt[r] - y[r];
+            const double v = fma(beta, w[r], y[r]);
+            const long long k = okey(v);
+            cn[r] = (k < kl[r]) || (k > ku[r]);
+            yt[r] = P(v, r);
+            dn[r] = yt[r] - y[r];
           }
-          hv(d, Hd);
+          // after the first trial, H d is rescaled from the previous one (the step
+          // length shrinks by proj_shrink)
+          if (t == 0) {
+            hv(dn, Hd);
+          } else {
+            bool both[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) both[r] = cn[r] || dcl[r];
+            rescaled_product(dn, o.proj_shrink, d, both, Hd);
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            d[r] = dn[r];
+            dcl[r] = cn[r];
+          }
           double rtd = 0.0, dHd = 0.0;
 #pragma unroll
           for (int r = 0; r < R; ++r) {

@@ -7,7 +7,7 @@ none of the solver's or the ADMM's arithmetic.  The paper's MATPOWER/PGLIB cases
 
 Seeds are ``SEED_BASE + workload index`` with numpy's ``default_rng``.
 
-Packed layouts (shared contract with ``include/exatron.h``):
+Packed layouts (shared contract with ``include/tron.h``):
 
 * branch record, 36 doubles: ``[0:8]`` gc_ij, bc_ij, g_ij, b_ij, gc_ji, bc_ji, g_ji,
   b_ji (eqs. pij-qji); ``[8:16]`` multipliers, ``[16:24]`` targets and ``[24:32]``

@@ -81,10 +81,12 @@ def test_dense_group_mappings(n, group):
     assert_convex_parity(g, r, d["l"], d["u"])
 
 
-@pytest.mark.parametrize("n,layout", [(32, 2), (32, 4), (64, 2), (64, 4), (128, 4), (100, 4)])
+@pytest.mark.parametrize("n,layout", [(32, 2), (32, 4), (64, 2), (64, 4), (128, 4), (100, 4),
+                                      (32, 6), (31, 6), (20, 6), (17, 6)])
 def test_dense_large_layouts(n, layout):
     # layout option = 1 + bits: 2 = packed factor with Q in shared memory,
-    # 4 = packed factor with Q read from global memory
+    # 4 = packed factor with Q read from global memory, 6 = packed factor with Q as
+    # wrapped diagonals (odd and even n, wrapped modulo n inside the n = 32 class)
     d = synth.dense_batch(37, n, seed_index=60 + n)
     g = gpu_solve(d, n=n, layout=layout)
     r = oracle_solve(d)
