@@ -390,41 +390,33 @@ def main():
     total_ms = xdist.max_over_ranks(total_ms, device=dev)
     value = xdist.weak_scaling_throughput(B, world, args.steps, total_ms)
 
-    # end to end through the public API with host buffers (pinned), every step:
-    # H2D of the batch, the solve, D2H of x, f, pg, iters, status
-    host = {k: torch.as_tensor(np.ascontiguousarray(d[k]), dtype=torch.float64).pin_memory()
-            for k in ("params", "l", "u", "x0", "delta0")}
-    hres = dict(x=torch.empty(B, N_VARS, dtype=torch.float64).pin_memory(),
-                f=torch.empty(B, dtype=torch.float64).pin_memory(),
-                pg=torch.empty(B, dtype=torch.float64).pin_memory(),
-                iters=torch.empty(B, dtype=torch.int32).pin_memory(),
-                status=torch.empty(B, dtype=torch.int32).pin_memory())
-    dbuf = dict(params=torch.empty_like(params), l=torch.empty_like(lo),
-                u=torch.empty_like(hi), x0=torch.empty_like(x0), delta0=torch.empty_like(d0))
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = sum(v.numel() * v.element_size() for v in hres.values())
+    # end to end through the C ABI's host-buffer path (tron_batch_solve_host): every step
+    # copies its inputs from pinned host memory to the device and its results (x, delta,
+    # f, pg, iters, status) back; consecutive steps overlap through the library's two
+    # device buffer sets.  Wall clock from the first call to the last result in host memory.
+    host_in = {k: torch.as_tensor(np.ascontiguousarray(d[k]), dtype=torch.float64).pin_memory()
+               for k in ("params", "l", "u", "x0", "delta0")}
+    tb.host_enable()
+    hout = [tb.host_outputs(B * N_VARS) for _ in range(2)]
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in hout[0].values())
 
-    def e2e_step():
-        for k in dbuf:
-            dbuf[k].copy_(host[k], non_blocking=True)
-        tb.solve(dbuf["params"], dbuf["l"], dbuf["u"], dbuf["x0"], dbuf["delta0"],
-                 stream=stream, **out)
-        hres["x"].copy_(dbuf["x0"], non_blocking=True)
-        for k in ("f", "pg", "iters", "status"):
-            hres[k].copy_(out[k], non_blocking=True)
+    def e2e_step(i):
+        tb.solve_host(host_in["params"], host_in["l"], host_in["u"], host_in["x0"],
+                      host_in["delta0"], hout[i % 2])
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            e2e_step()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1)
+    for i in range(args.warmup):
+        e2e_step(i)
+    tb.host_sync()
+    if world > 1:
+        dist.barrier()
+    e0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_step(k)
+    tb.host_sync()
+    e2e_ms = (time.perf_counter() - e0) * 1e3
+    e2e_ok = all(bool((h["status"].numpy() == 0).all()) for h in hout)
+    ok = ok and e2e_ok
     e2e_ms = xdist.max_over_ranks(e2e_ms, device=dev)
     e2e_value = xdist.weak_scaling_throughput(B, world, args.steps, e2e_ms)
 
@@ -442,7 +434,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "path": "tron_batch_solve_host (pinned host buffers)"},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, flops_per_problem, _ = cpu_baseline(d)

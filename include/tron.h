@@ -200,6 +200,41 @@ tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t*
 /* Number of GPU kernel launches the last tron_batch_solve on this handle enqueued. */
 int32_t tron_batch_last_launches(const tron_batch_t* b);
 
+/* ---- Host-buffer path (a batch whose arrays live in host memory).
+ * The same solve as tron_batch_solve (Sec. 4.1), with the copies to and from the device
+ * made by the library.  The paper's solver works on device arrays only; this path lets
+ * a stream of batches keep the GPU busy while the next batch is copied in and the
+ * previous one's results are copied out.
+ *
+ * tron_batch_host_enable: setup-time call that allocates two device buffer sets (each
+ * the size of one batch: records, l, u, x, delta, f, pgnorm, iters, status) and three
+ * streams (copy in, solve, copy out).  Idempotent.  TRON_ENOMEM when the buffers do not
+ * fit.
+ *
+ * tron_batch_solve_host: enqueues, for the next buffer set in turn, the copy of h_params,
+ * h_lower, h_upper, h_x0, h_delta0 (layouts as in tron_batch_solve) to the device, the
+ * solve, and the copy of x*, the final radius, f*, ||grad_P f||_inf, the iteration
+ * counts and the statuses to h_x, h_delta, h_f, h_pgnorm, h_iters, h_status; returns
+ * without waiting.  A set is reused only after its previous results have been copied
+ * out, so two calls can be in flight: the inputs of one are copied while the other
+ * solves.  The host arrays belong to the caller and must stay valid and unchanged until
+ * tron_batch_host_sync returns; the inputs (const) may be shared by calls in flight, and
+ * results are copied out in call order, so calls that share output arrays leave the
+ * last call's results there.  Copies overlap with compute only from
+ * page-locked host memory (pageable memory works, serialised).  h_params may be NULL
+ * for TRON_OBJ_HS45.  TRON_EINVAL without tron_batch_host_enable or for NULL arrays;
+ * TRON_ECUDA on a CUDA error.  Does not mix with tron_batch_solve calls on other
+ * streams that are still running on the same handle (they share the work counters).
+ *
+ * tron_batch_host_sync: waits until every call's results are in host memory. */
+tron_err_t tron_batch_host_enable(tron_batch_t* b);
+tron_err_t tron_batch_solve_host(tron_batch_t* b, const double* h_params, const double* h_lower,
+                                 const double* h_upper, const double* h_x0,
+                                 const double* h_delta0, double* h_x, double* h_delta,
+                                 double* h_f, double* h_pgnorm, int32_t* h_iters,
+                                 int32_t* h_status);
+tron_err_t tron_batch_host_sync(tron_batch_t* b);
+
 /* Release the handle and its workspace (NULL is ignored).  Synchronises nothing; the
  * caller must not destroy a handle whose solve is still running on the GPU. */
 void tron_batch_destroy(tron_batch_t* b);

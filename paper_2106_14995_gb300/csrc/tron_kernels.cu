@@ -313,10 +313,22 @@ struct tron_batch {
   unsigned long long* d_counter;  // one work counter per bucket
   cudaStream_t side[kNumClasses];  // forked streams of the persistent schedule
   cudaEvent_t ev_fork, ev_join[kNumClasses];
-  int64_t total_n;  // length of the concatenated vectors
+  int64_t total_n;     // length of the concatenated vectors
+  int64_t params_len;  // doubles of the packed parameter records
   int last_launches;
   int sms;
   int smem_optin;
+  // host-buffer path (tron_batch_host_enable): two device buffer sets used in turn, so
+  // the copies of one call overlap the solve of the previous one
+  struct HostSet {
+    double *params, *lo, *hi, *x, *delta, *f, *pg;
+    int32_t *iters, *status;
+    cudaEvent_t in_done, solved, out_done;
+  };
+  HostSet hs[2];
+  bool host_ready;
+  int host_next;
+  cudaStream_t s_in, s_run, s_out;
 };
 
 static int64_t record_size(int kind, int n) {
@@ -407,6 +419,11 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
     b->ev_join[i] = nullptr;
   }
   b->last_launches = 0;
+  b->params_len = 0;
+  memset(b->hs, 0, sizeof(b->hs));
+  b->host_ready = false;
+  b->host_next = 0;
+  b->s_in = b->s_run = b->s_out = nullptr;
   b->sms = device_sm_count();
   b->smem_optin = device_smem_optin();
   auto fail = [&](tron_err_t code) {
@@ -424,6 +441,7 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
     }
     b->n_uniform = n_uniform;
     b->total_n = nprob * (int64_t)n_uniform;
+    b->params_len = nprob * record_size(kind, n_uniform);
     b->buckets.push_back({size_class(kind, n_uniform), nprob, nullptr, nullptr, 0, 0});
   } else {
     std::vector<int64_t> poff(nprob), voff(nprob);
@@ -443,6 +461,7 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
       lists[class_slot(c)].push_back((int32_t)p);
     }
     b->total_n = va;
+    b->params_len = pa;
     if (cudaMalloc(&b->d_n, sizeof(int32_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess ||
         cudaMalloc(&b->d_poff, sizeof(int64_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess ||
         cudaMalloc(&b->d_voff, sizeof(int64_t) * std::max<int64_t>(nprob, 1)) != cudaSuccess) {
@@ -774,7 +793,113 @@ void tron_batch_destroy(tron_batch_t* b) {
   cudaFree(b->d_voff);
   cudaFree(b->d_counter);
   for (auto& bk : b->buckets) cudaFree(bk.d_list);
+  for (auto& h : b->hs) {
+    cudaFree(h.params);
+    cudaFree(h.lo);
+    cudaFree(h.hi);
+    cudaFree(h.x);
+    cudaFree(h.delta);
+    cudaFree(h.f);
+    cudaFree(h.pg);
+    cudaFree(h.iters);
+    cudaFree(h.status);
+    if (h.in_done) cudaEventDestroy(h.in_done);
+    if (h.solved) cudaEventDestroy(h.solved);
+    if (h.out_done) cudaEventDestroy(h.out_done);
+  }
+  if (b->s_in) cudaStreamDestroy(b->s_in);
+  if (b->s_run) cudaStreamDestroy(b->s_run);
+  if (b->s_out) cudaStreamDestroy(b->s_out);
   delete b;
+}
+
+// ------------------------------------------------------------------- host buffers
+tron_err_t tron_batch_host_enable(tron_batch_t* b) {
+  clear_error();
+  XT_REQUIRE(b != nullptr, TRON_EINVAL, "tron_batch_host_enable: null handle");
+  if (b->host_ready) return TRON_OK;
+  const size_t np = (size_t)std::max<int64_t>(b->nprob, 1);
+  const size_t nv = (size_t)std::max<int64_t>(b->total_n, 1);
+  const size_t npar = (size_t)std::max<int64_t>(b->params_len, 1);
+  for (auto& h : b->hs) {
+    if (cudaMalloc(&h.params, npar * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h.lo, nv * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h.hi, nv * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h.x, nv * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h.delta, np * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h.f, np * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h.pg, np * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h.iters, np * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&h.status, np * sizeof(int32_t)) != cudaSuccess) {
+      set_error("tron_batch_host_enable: cudaMalloc of the device buffer sets failed");
+      return TRON_ENOMEM;
+    }
+    XT_CUDA(cudaEventCreateWithFlags(&h.in_done, cudaEventDisableTiming));
+    XT_CUDA(cudaEventCreateWithFlags(&h.solved, cudaEventDisableTiming));
+    XT_CUDA(cudaEventCreateWithFlags(&h.out_done, cudaEventDisableTiming));
+  }
+  XT_CUDA(cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
+  XT_CUDA(cudaStreamCreateWithFlags(&b->s_run, cudaStreamNonBlocking));
+  XT_CUDA(cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
+  b->host_ready = true;
+  return TRON_OK;
+}
+
+tron_err_t tron_batch_solve_host(tron_batch_t* b, const double* h_params, const double* h_lower,
+                                 const double* h_upper, const double* h_x0,
+                                 const double* h_delta0, double* h_x, double* h_delta,
+                                 double* h_f, double* h_pgnorm, int32_t* h_iters,
+                                 int32_t* h_status) {
+  clear_error();
+  XT_REQUIRE(b != nullptr, TRON_EINVAL, "tron_batch_solve_host: null handle");
+  XT_REQUIRE(b->host_ready, TRON_EINVAL,
+             "tron_batch_solve_host: call tron_batch_host_enable first");
+  if (b->nprob == 0) return TRON_OK;
+  XT_REQUIRE(h_lower && h_upper && h_x0 && h_delta0 && h_x && h_delta && h_f && h_pgnorm &&
+                 h_iters && h_status,
+             TRON_EINVAL, "tron_batch_solve_host: null host array");
+  XT_REQUIRE(h_params || b->params_len == 0, TRON_EINVAL,
+             "tron_batch_solve_host: h_params is NULL");
+  auto& h = b->hs[b->host_next];
+  b->host_next ^= 1;
+  const size_t np = (size_t)b->nprob, nv = (size_t)b->total_n;
+  const cudaMemcpyKind up = cudaMemcpyHostToDevice, down = cudaMemcpyDeviceToHost;
+  // inputs, once the previous use of this buffer set has been copied out
+  XT_CUDA(cudaStreamWaitEvent(b->s_in, h.out_done, 0));
+  if (b->params_len > 0)
+    XT_CUDA(cudaMemcpyAsync(h.params, h_params, (size_t)b->params_len * sizeof(double), up,
+                            b->s_in));
+  XT_CUDA(cudaMemcpyAsync(h.lo, h_lower, nv * sizeof(double), up, b->s_in));
+  XT_CUDA(cudaMemcpyAsync(h.hi, h_upper, nv * sizeof(double), up, b->s_in));
+  XT_CUDA(cudaMemcpyAsync(h.x, h_x0, nv * sizeof(double), up, b->s_in));
+  XT_CUDA(cudaMemcpyAsync(h.delta, h_delta0, np * sizeof(double), up, b->s_in));
+  XT_CUDA(cudaEventRecord(h.in_done, b->s_in));
+  // the solve
+  XT_CUDA(cudaStreamWaitEvent(b->s_run, h.in_done, 0));
+  tron_err_t e = tron_batch_solve(b, b->params_len > 0 ? h.params : nullptr, h.lo, h.hi, h.x,
+                                  h.delta, h.f, h.pg, h.iters, h.status, b->s_run);
+  if (e != TRON_OK) return e;
+  XT_CUDA(cudaEventRecord(h.solved, b->s_run));
+  // results
+  XT_CUDA(cudaStreamWaitEvent(b->s_out, h.solved, 0));
+  XT_CUDA(cudaMemcpyAsync(h_x, h.x, nv * sizeof(double), down, b->s_out));
+  XT_CUDA(cudaMemcpyAsync(h_delta, h.delta, np * sizeof(double), down, b->s_out));
+  XT_CUDA(cudaMemcpyAsync(h_f, h.f, np * sizeof(double), down, b->s_out));
+  XT_CUDA(cudaMemcpyAsync(h_pgnorm, h.pg, np * sizeof(double), down, b->s_out));
+  XT_CUDA(cudaMemcpyAsync(h_iters, h.iters, np * sizeof(int32_t), down, b->s_out));
+  XT_CUDA(cudaMemcpyAsync(h_status, h.status, np * sizeof(int32_t), down, b->s_out));
+  XT_CUDA(cudaEventRecord(h.out_done, b->s_out));
+  return TRON_OK;
+}
+
+tron_err_t tron_batch_host_sync(tron_batch_t* b) {
+  clear_error();
+  XT_REQUIRE(b != nullptr, TRON_EINVAL, "tron_batch_host_sync: null handle");
+  if (!b->host_ready) return TRON_OK;
+  XT_CUDA(cudaStreamSynchronize(b->s_in));
+  XT_CUDA(cudaStreamSynchronize(b->s_run));
+  XT_CUDA(cudaStreamSynchronize(b->s_out));
+  return TRON_OK;
 }
 
 }  // extern "C"

@@ -862,8 +862,15 @@ struct Solver {
       const double pred = -qs;
       const double ared = f - fy;
       const double fl = o.ared_guard * fmax(fs, 1.0);
-      const double rho = (pred > 0.0 && isfinite(fy)) ? (ared + fl) / (pred + fl) : -CUDART_INF;
-      if (rho > o.eta0) {
+      // rho = (ared + fl) / (pred + fl) is compared with each eta as
+      // ared + fl > eta (pred + fl), the denominator being positive: no division; an
+      // invalid ratio (pred <= 0 or f(y) not finite) counts as -infinity
+      const bool valid = (pred > 0.0) && isfinite(fy);
+      const double num = ared + fl, den = pred + fl;
+      const bool above0 = valid && num > o.eta0 * den;
+      const bool below1 = !valid || num < o.eta1 * den;
+      const bool above2 = valid && num > o.eta2 * den;
+      if (above0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = y[r];
         f = fy;
@@ -876,9 +883,9 @@ struct Solver {
       }
       // (||s|| >= 0.99 delta compared squared; the norm itself only when it sets delta)
       const double d99 = 0.99 * delta;
-      if (rho < o.eta1) {
+      if (below1) {
         delta = o.sigma1 * fmin(sqrt(ss2), delta);
-      } else if (rho > o.eta2 && ss2 >= d99 * d99) {
+      } else if (above2 && ss2 >= d99 * d99) {
         delta = fmin(o.sigma3 * delta, o.delta_max);
       }
       // delta < c (1 + ||x||), decided without a square root:

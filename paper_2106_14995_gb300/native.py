@@ -89,6 +89,9 @@ def load(build_if_missing: bool = True):
             "tron_batch_get_choice": (I32, [P, I32, P, P, P, P, P]),
             "tron_solve_mixed_noalloc": (I32, [I32, I64, P, C.POINTER(TronOptions), P, P, P, P,
                                                P, P, P, P, P, P]),
+            "tron_batch_host_enable": (I32, [P]),
+            "tron_batch_solve_host": (I32, [P, P, P, P, P, P, P, P, P, P, P, P]),
+            "tron_batch_host_sync": (I32, [P]),
             "tron_batch_destroy": (None, [P]),
             "tron_last_error": (C.c_char_p, []),
             "tron_version": (C.c_char_p, []),
@@ -127,6 +130,17 @@ def check(code: int, what: str) -> None:
     if code != 0:
         msg = load().tron_last_error().decode(errors="replace")
         raise TronError(f"{what}: {ERR_NAMES.get(code, code)}: {msg}")
+
+
+def hptr(t) -> int:
+    """Host pointer of a contiguous torch CPU tensor (None -> NULL)."""
+    if t is None:
+        return 0
+    if t.is_cuda:
+        raise TronError("expected a host tensor")
+    if not t.is_contiguous():
+        raise TronError("expected a contiguous tensor")
+    return t.data_ptr()
 
 
 def ptr(t) -> int:

@@ -66,6 +66,35 @@ class TronBatch:
             "tron_batch_solve")
         return dict(x=x, delta=delta, f=f, pg=pg, iters=iters, status=status)
 
+    # ---- host-buffer path: arrays in (page-locked) host memory, copies by the library
+    def host_enable(self) -> None:
+        """Allocate the two device buffer sets of the host-buffer path (setup time)."""
+        nt.check(self._lib.tron_batch_host_enable(self._h), "tron_batch_host_enable")
+
+    def solve_host(self, params, lower, upper, x0, delta0, out: dict) -> dict:
+        """Enqueue one solve of host arrays (torch CPU tensors, pinned for overlap); the
+        results land in ``out`` (x, delta, f, pg, iters, status host tensors) once
+        ``host_sync`` returns.  Inputs may be shared by calls in flight; results are
+        copied out in call order."""
+        hp = nt.hptr
+        nt.check(self._lib.tron_batch_solve_host(
+            self._h, hp(params), hp(lower), hp(upper), hp(x0), hp(delta0), hp(out["x"]),
+            hp(out["delta"]), hp(out["f"]), hp(out["pg"]), hp(out["iters"]),
+            hp(out["status"])), "tron_batch_solve_host")
+        return out
+
+    def host_sync(self) -> None:
+        nt.check(self._lib.tron_batch_host_sync(self._h), "tron_batch_host_sync")
+
+    def host_outputs(self, total_n: int, pin: bool = True) -> dict:
+        """A set of host result tensors for solve_host (total_n = length of x)."""
+        B = self.nprob
+        mk = lambda n, dt: torch.empty(n, dtype=dt).pin_memory() if pin else \
+            torch.empty(n, dtype=dt)
+        return dict(x=mk(total_n, torch.float64), delta=mk(B, torch.float64),
+                    f=mk(B, torch.float64), pg=mk(B, torch.float64),
+                    iters=mk(B, torch.int32), status=mk(B, torch.int32))
+
     def autotune(self, params, lower, upper, x0, delta0, sample: int = 8192,
                  stream=None) -> list:
         """Time every kernel variant per size class on a sample; keep the fastest."""

@@ -193,6 +193,48 @@ def test_persistent_equals_plain_bitwise():
         np.testing.assert_array_equal(a[k], b[k])
 
 
+def _host(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).pin_memory()
+
+
+@pytest.mark.parametrize("case", ["dense32", "mixed", "hs45"])
+def test_host_buffer_path_equals_device_path(case):
+    # three calls in flight through tron_batch_solve_host (shared inputs, distinct
+    # outputs, the two device buffer sets reused) give the device path's bits
+    if case == "dense32":
+        d, n, n_list = synth.dense_batch(700, 32, seed_index=12), 32, None
+    elif case == "mixed":
+        d = synth.uneven_batch(900, seed_index=13)
+        n, n_list = None, d["nvec"]
+    else:
+        d, n, n_list = synth.hs45_batch(50, 6), 6, None
+    ref = gpu_solve(d, n=n, n_list=n_list, schedule=native.TRON_SCHED_PERSISTENT)
+    B = d["delta0"].shape[0]
+    tb = TronBatch(d["kind"], B, n=n if n_list is None else None, n_list=n_list,
+                   opts=options(schedule=native.TRON_SCHED_PERSISTENT))
+    tb.host_enable()
+    params = _host(d["params"]) if np.size(d["params"]) else None
+    ins = [params, _host(d["l"]), _host(d["u"]), _host(d["x0"]), _host(d["delta0"])]
+    outs = [tb.host_outputs(int(np.size(d["x0"]))) for _ in range(3)]
+    for o in outs:
+        tb.solve_host(*ins, o)
+    tb.host_sync()
+    tb.close()
+    for o in outs:
+        for k in ("x", "delta", "f", "pg", "iters", "status"):
+            np.testing.assert_array_equal(o[k].numpy().reshape(ref[k].shape), ref[k],
+                                          err_msg=k)
+
+
+def test_host_buffer_path_requires_enable():
+    d = synth.dense_batch(4, 8, seed_index=14)
+    tb = TronBatch(2, 4, n=8)
+    with pytest.raises(native.TronError, match="EINVAL"):
+        tb.solve_host(_host(d["params"]), _host(d["l"]), _host(d["u"]), _host(d["x0"]),
+                      _host(d["delta0"]), tb.host_outputs(32))
+    tb.close()
+
+
 def test_edge_cases_status_codes():
     n = 6
     d = synth.dense_batch(8, n, seed_index=9)
