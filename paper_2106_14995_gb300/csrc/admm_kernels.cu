@@ -191,18 +191,23 @@ __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
   if (b < d.cap_bus) {
     const int inst = d.bus_inst[b];
     if (inst >= 0 && d.inst_active[inst]) {
+      // one thread per bus, so a hub bus's chain sets the launch: every division by rho
+      // or by a per-bus quantity is one reciprocal, and the incidence loops are unrolled
+      // so that their gathers are in flight together
       const double rho = d.inst_param[4 * inst];
+      const double irho = 1.0 / rho;
       const int g0 = d.bus_goff[b], gn = d.bus_gcnt[b];
       const int e0 = d.bus_eoff[b], en = d.bus_ecnt[b];
       // a = x + lambda / rho for every copy; balance rows A a - (p_d, q_d)
       double rhsP = -d.bus_pd[b], rhsQ = -d.bus_qd[b];
-      double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
+      double awn = 0.0, athn = 0.0;
+#pragma unroll 2
       for (int t = 0; t < gn; ++t) {
         const int g = d.gen_list[g0 + t];
-        rhsP += d.gen_pq[2 * g] + d.gen_lam[2 * g] / rho;
-        rhsQ += d.gen_pq[2 * g + 1] + d.gen_lam[2 * g + 1] / rho;
-        sinv += 1.0 / rho;
+        rhsP += fma(d.gen_lam[2 * g], irho, d.gen_pq[2 * g]);
+        rhsQ += fma(d.gen_lam[2 * g + 1], irho, d.gen_pq[2 * g + 1]);
       }
+#pragma unroll 4
       for (int t = 0; t < en; ++t) {
         const int e = d.end_list[e0 + t];
         const size_t k = (size_t)(e >> 1);
@@ -210,47 +215,52 @@ __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
         const int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
         const double* val = d.br_val + 8 * k;
         const double* lam = d.br_lam + 8 * k;
-        rhsP -= val[kp] + lam[kp] / rho;
-        rhsQ -= val[kq] + lam[kq] / rho;
-        sinv += 1.0 / rho;
-        Dw += rho;
-        awn += rho * (val[kw] + lam[kw] / rho);
-        athn += rho * (val[kt] + lam[kt] / rho);
+        rhsP -= fma(lam[kp], irho, val[kp]);
+        rhsQ -= fma(lam[kq], irho, val[kq]);
+        awn += fma(rho, val[kw], lam[kw]);    // rho (x + lambda / rho)
+        athn += fma(rho, val[kt], lam[kt]);
       }
+      const double sinv = (double)(gn + en) * irho;  // sum of 1/rho over the copies
+      const double Dw = (double)en * rho;
+      const double iDw = en > 0 ? 1.0 / Dw : 0.0;
       const double gsh = d.bus_gsh[b], bsh = d.bus_bsh[b];
       const double w_old = d.bus_w[b], th_old = d.bus_th[b];
-      const double aw = Dw > 0.0 ? awn / Dw : w_old;
+      const double aw = en > 0 ? awn * iDw : w_old;
       rhsP -= gsh * aw;
       rhsQ += bsh * aw;
       double M11 = sinv, M22 = sinv, M12 = 0.0;
-      if (Dw > 0.0) {
-        M11 += gsh * gsh / Dw;
-        M22 += bsh * bsh / Dw;
-        M12 = -gsh * bsh / Dw;
+      if (en > 0) {
+        M11 += gsh * gsh * iDw;
+        M22 += bsh * bsh * iDw;
+        M12 = -gsh * bsh * iDw;
       }
       const double det = M11 * M22 - M12 * M12;
       double mu1 = 0.0, mu2 = 0.0;
       if (det != 0.0) {
-        mu1 = (M22 * rhsP - M12 * rhsQ) / det;
-        mu2 = (M11 * rhsQ - M12 * rhsP) / det;
+        const double idet = 1.0 / det;
+        mu1 = (M22 * rhsP - M12 * rhsQ) * idet;
+        mu2 = (M11 * rhsQ - M12 * rhsP) * idet;
       }
-      const double w_new = Dw > 0.0 ? aw - (-gsh * mu1 + bsh * mu2) / Dw : w_old;
-      const double th_new = Dw > 0.0 ? athn / Dw : th_old;
+      const double w_new = en > 0 ? aw - (-gsh * mu1 + bsh * mu2) * iDw : w_old;
+      const double th_new = en > 0 ? athn * iDw : th_old;
+      const double m1r = mu1 * irho, m2r = mu2 * irho;
       // new copies, multipliers lambda += rho (x - xt), residual sums
+#pragma unroll 2
       for (int t = 0; t < gn; ++t) {
         const int g = d.gen_list[g0 + t];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const double xv = d.gen_pq[2 * g + c];
           const double lam = d.gen_lam[2 * g + c];
-          const double xt = xv + lam / rho - (c == 0 ? mu1 : mu2) / rho;
+          const double xt = fma(lam, irho, xv) - (c == 0 ? m1r : m2r);
           const double old = d.gen_tilde[2 * g + c];
           d.gen_tilde[2 * g + c] = xt;
-          d.gen_lam[2 * g + c] = lam + rho * (xv - xt);
-          pr2 += (xv - xt) * (xv - xt);
-          du2 += (xt - old) * (xt - old);
+          d.gen_lam[2 * g + c] = fma(rho, xv - xt, lam);
+          pr2 = fma(xv - xt, xv - xt, pr2);
+          du2 = fma(xt - old, xt - old, du2);
         }
       }
+#pragma unroll 4
       for (int t = 0; t < en; ++t) {
         const int e = d.end_list[e0 + t];
         const size_t k = (size_t)(e >> 1);
@@ -263,24 +273,24 @@ __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
           const int kk = c == 0 ? kp : kq;
           const double xv = val[kk];
           const double l = lam[kk];
-          const double xt = xv + l / rho + (c == 0 ? mu1 : mu2) / rho;
+          const double xt = fma(l, irho, xv) + (c == 0 ? m1r : m2r);
           const double old = d.br_tilde[4 * k + kk];
           d.br_tilde[4 * k + kk] = xt;
-          lam[kk] = l + rho * (xv - xt);
-          pr2 += (xv - xt) * (xv - xt);
-          du2 += (xt - old) * (xt - old);
+          lam[kk] = fma(rho, xv - xt, l);
+          pr2 = fma(xv - xt, xv - xt, pr2);
+          du2 = fma(xt - old, xt - old, du2);
         }
         {
           const double xv = val[kw];
-          lam[kw] = lam[kw] + rho * (xv - w_new);
-          pr2 += (xv - w_new) * (xv - w_new);
-          du2 += (w_new - w_old) * (w_new - w_old);
+          lam[kw] = fma(rho, xv - w_new, lam[kw]);
+          pr2 = fma(xv - w_new, xv - w_new, pr2);
+          du2 = fma(w_new - w_old, w_new - w_old, du2);
         }
         {
           const double xv = val[kt];
-          lam[kt] = lam[kt] + rho * (xv - th_new);
-          pr2 += (xv - th_new) * (xv - th_new);
-          du2 += (th_new - th_old) * (th_new - th_old);
+          lam[kt] = fma(rho, xv - th_new, lam[kt]);
+          pr2 = fma(xv - th_new, xv - th_new, pr2);
+          du2 = fma(th_new - th_old, th_new - th_old, du2);
         }
       }
       d.bus_w[b] = w_new;

@@ -92,11 +92,18 @@ struct Solver {
   }
 
   // ------------------------------------------------------------------ vector helpers
-  // order-preserving integer key of a double (two's-complement order of the keys is
-  // the numeric order, -0 just below +0), so that projections need no FP64 compare
+  // order-preserving integer key of a double: the two's-complement order of the keys is
+  // the numeric order, and -0 takes the key of +0, so for non-NaN values every
+  // comparison of keys gives the IEEE comparison's answer without an FP64 instruction
+  // (projections, bound and sign tests)
   __device__ __forceinline__ static long long okey(double v) {
-    const long long b = __double_as_longlong(v);
+    long long b = __double_as_longlong(v);
+    if (b == (long long)0x8000000000000000ULL) b = 0;
     return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+  }
+  // |v| > t for t >= 0 (magnitude bits compared as integers)
+  __device__ __forceinline__ static bool abs_above(double v, long long tkey) {
+    return (__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL) > tkey;
   }
   __device__ __forceinline__ double P(double v, int r) const {
     const long long k = okey(v);
@@ -115,30 +122,31 @@ struct Solver {
     for (int r = 0; r < R; ++r) s = fma(a[r], b[r], s);
     return gp.sum(s);
   }
+  // (grad_P f)_i: g_i, or 0 where x_i sits on a bound that g_i pushes against
+  __device__ __forceinline__ double pgi(double x, double g, int r) const {
+    const long long kx = okey(x), kg = okey(g);
+    return ((kx <= kl[r] && kg > 0) || (kx >= ku[r] && kg < 0)) ? 0.0 : g;
+  }
   __device__ __forceinline__ double pgnorm(const double (&x)[R], const double (&g)[R]) const {
     double m = 0.0;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      double p = g[r];
-      if (x[r] <= l[r] && p > 0.0) p = 0.0;
-      if (x[r] >= u[r] && p < 0.0) p = 0.0;
-      m = fmax(m, fabs(p));
-    }
+    for (int r = 0; r < R; ++r) m = fmax(m, fabs(pgi(x[r], g[r], r)));
     return gp.max(m);
   }
 
-  // some |(grad_P f)_i| > tol
+  // some |(grad_P f)_i| > tol (tol >= 0), decided on integer keys
   __device__ __forceinline__ bool pg_above(const double (&x)[R], const double (&g)[R],
                                            double tol) const {
+    const long long tk = __double_as_longlong(tol);
     bool above = false;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      double p = g[r];
-      if (x[r] <= l[r] && p > 0.0) p = 0.0;
-      if (x[r] >= u[r] && p < 0.0) p = 0.0;
-      above = above || (fabs(p) > tol);
-    }
+    for (int r = 0; r < R; ++r) above = above || abs_above(pgi(x[r], g[r], r), tk);
     return gp.any(above);
+  }
+  // l_i < v < u_i on integer keys
+  __device__ __forceinline__ bool strictly_inside(double v, int r) const {
+    const long long k = okey(v);
+    return kl[r] < k && k < ku[r];
   }
 
   // y = H v over the full vector (H at the current accepted point)
@@ -617,8 +625,9 @@ struct Solver {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const double w = -g[r];
-      if (x[r] < u[r] && w > 0.0) bmax = fmax(bmax, (u[r] - x[r]) / w);
-      else if (x[r] > l[r] && w < 0.0) bmax = fmax(bmax, (l[r] - x[r]) / w);
+      const long long kx = okey(x[r]), kw = okey(w);
+      if (kx < ku[r] && kw > 0) bmax = fmax(bmax, (u[r] - x[r]) / w);
+      else if (kx > kl[r] && kw < 0) bmax = fmax(bmax, (l[r] - x[r]) / w);
     }
     bmax = gp.max(bmax);
     return (bmax == -CUDART_INF) ? 0.0 : bmax;
@@ -735,7 +744,7 @@ struct Solver {
         int m = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const bool fr = (l[r] < y[r]) && (y[r] < u[r]);
+          const bool fr = strictly_inside(y[r], r);
           int tot;
           const int pre = gp.prefix(fr, tot);
           cidx[r] = fr ? m + pre : -1;
@@ -826,7 +835,7 @@ struct Solver {
         double ss = 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          if (cidx[r] >= 0 && !((l[r] < yt[r]) && (yt[r] < u[r]))) na = true;
+          if (cidx[r] >= 0 && !strictly_inside(yt[r], r)) na = true;
           y[r] = yt[r];
           rv[r] = rv[r] + Hd[r];
           if (cidx[r] >= 0) ss = fma(rv[r], rv[r], ss);
