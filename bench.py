@@ -33,23 +33,33 @@ B_DEFAULT = 10000
 N_VARS = 32
 L2_BYTES = 129 * 2 ** 20
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
-# DRAM bytes per launch of the timed kernel from one ncu capture (profiles/
-# tron_dense32_n10000.md: 19.06 MB for 2,000 problems, scaled by 5 to the 10,000-problem
-# launch), valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES_PER_PROBLEM = 19.057e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "2965590b5f48a6a20e3977f6f42f9b976edc7f16"
+# From one ncu capture of the timed kernel (profiles/tron_dense32_n10000.md, 2,000
+# problems, scaled per problem to the launch), valid only for the kernel sources it was
+# taken on: DRAM bytes (19.05 MB per 2,000 problems) and the FP64 flops the kernel
+# executes (thread-level DFMA x 2 + DADD + DMUL: 326.4 Mflop per 2,000 problems).
+TRAFFIC_BYTES_PER_PROBLEM = 19.049728e6 / 2000
+EXEC_FLOPS_PER_PROBLEM = 326.41e6 / 2000
+TRAFFIC_SOURCES_SHA1 = "6cd155f835f38666f6fcca9e4e3fa04716e68ef5"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
-def traffic_per_launch(nprob: int):
+def _sources_match() -> bool:
     import hashlib
     h = hashlib.sha1()
     for name in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_2106_14995_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != TRAFFIC_SOURCES_SHA1:
-        return None  # kernel changed since the counters were taken
-    return TRAFFIC_BYTES_PER_PROBLEM * nprob
+    return h.hexdigest() == TRAFFIC_SOURCES_SHA1
+
+
+def traffic_per_launch(nprob: int):
+    """DRAM bytes of one launch, or None when the kernel changed since the capture."""
+    return TRAFFIC_BYTES_PER_PROBLEM * nprob if _sources_match() else None
+
+
+def executed_flops_per_launch(nprob: int):
+    """FP64 flops the kernel executes per launch, or None when it changed since."""
+    return EXEC_FLOPS_PER_PROBLEM * nprob if _sources_match() else None
 
 
 def parse():
@@ -439,13 +449,19 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, flops_per_problem, _ = cpu_baseline(d)
         achieved = flops_per_problem * B / (float(np.median(launch_ms)) * 1e-3) / 1e9
+        lms = float(np.median(launch_ms))
+        ex = executed_flops_per_launch(B)
         line["roofline"] = {
             "bound": "alu", "kernel": "k_tron_persistent<DenseObj<32,32>,32,32>",
             "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
             "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic_per_launch(B),
             "flops_per_launch": flops_per_problem * B,
-            "launch_ms_median": float(np.median(launch_ms)),
-            "note": "FP64 CUDA-core pipe; peak from 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
+            "executed_flops_per_launch": ex,
+            "executed_frac": (ex / (lms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS) if ex else None,
+            "launch_ms_median": lms,
+            "note": "FP64 CUDA-core pipe; peak from 2 DFMA/clk/SM x 152 SMs x 2.07 GHz; "
+                    "achieved counts the oracle's algorithmic flops, executed_frac the "
+                    "FP64 flops the kernel issues (ncu thread-level counts)"}
         line["cpu_baseline"] = cb
     tb.close()
     if rank == 0 and world == 1 and not args.no_extras:

@@ -244,23 +244,28 @@ __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
       const double w_new = en > 0 ? aw - (-gsh * mu1 + bsh * mu2) * iDw : w_old;
       const double th_new = en > 0 ? athn * iDw : th_old;
       const double m1r = mu1 * irho, m2r = mu2 * irho;
-      // new copies, multipliers lambda += rho (x - xt), residual sums
+      // new copies, multipliers lambda += rho (x - xt), residual sums; every copy's
+      // loads are issued before its stores, so they travel together
 #pragma unroll 2
       for (int t = 0; t < gn; ++t) {
         const int g = d.gen_list[g0 + t];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const double xv = d.gen_pq[2 * g + c];
-          const double lam = d.gen_lam[2 * g + c];
-          const double xt = fma(lam, irho, xv) - (c == 0 ? m1r : m2r);
-          const double old = d.gen_tilde[2 * g + c];
-          d.gen_tilde[2 * g + c] = xt;
-          d.gen_lam[2 * g + c] = fma(rho, xv - xt, lam);
-          pr2 = fma(xv - xt, xv - xt, pr2);
-          du2 = fma(xt - old, xt - old, du2);
-        }
+        const double xv0 = d.gen_pq[2 * g], xv1 = d.gen_pq[2 * g + 1];
+        const double l0 = d.gen_lam[2 * g], l1 = d.gen_lam[2 * g + 1];
+        const double o0 = d.gen_tilde[2 * g], o1 = d.gen_tilde[2 * g + 1];
+        const double xt0 = fma(l0, irho, xv0) - m1r;
+        const double xt1 = fma(l1, irho, xv1) - m2r;
+        d.gen_tilde[2 * g] = xt0;
+        d.gen_tilde[2 * g + 1] = xt1;
+        d.gen_lam[2 * g] = fma(rho, xv0 - xt0, l0);
+        d.gen_lam[2 * g + 1] = fma(rho, xv1 - xt1, l1);
+        pr2 = fma(xv0 - xt0, xv0 - xt0, pr2);
+        du2 = fma(xt0 - o0, xt0 - o0, du2);
+        pr2 = fma(xv1 - xt1, xv1 - xt1, pr2);
+        du2 = fma(xt1 - o1, xt1 - o1, du2);
       }
-#pragma unroll 4
+      const double dw2 = (w_new - w_old) * (w_new - w_old);
+      const double dt2 = (th_new - th_old) * (th_new - th_old);
+#pragma unroll 2
       for (int t = 0; t < en; ++t) {
         const int e = d.end_list[e0 + t];
         const size_t k = (size_t)(e >> 1);
@@ -268,30 +273,26 @@ __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
         const int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
         double* lam = d.br_lam + 8 * k;
         const double* val = d.br_val + 8 * k;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int kk = c == 0 ? kp : kq;
-          const double xv = val[kk];
-          const double l = lam[kk];
-          const double xt = fma(l, irho, xv) + (c == 0 ? m1r : m2r);
-          const double old = d.br_tilde[4 * k + kk];
-          d.br_tilde[4 * k + kk] = xt;
-          lam[kk] = fma(rho, xv - xt, l);
-          pr2 = fma(xv - xt, xv - xt, pr2);
-          du2 = fma(xt - old, xt - old, du2);
-        }
-        {
-          const double xv = val[kw];
-          lam[kw] = fma(rho, xv - w_new, lam[kw]);
-          pr2 = fma(xv - w_new, xv - w_new, pr2);
-          du2 = fma(w_new - w_old, w_new - w_old, du2);
-        }
-        {
-          const double xv = val[kt];
-          lam[kt] = fma(rho, xv - th_new, lam[kt]);
-          pr2 = fma(xv - th_new, xv - th_new, pr2);
-          du2 = fma(th_new - th_old, th_new - th_old, du2);
-        }
+        double* tl = d.br_tilde + 4 * k;
+        const double vp = val[kp], vq = val[kq], vw = val[kw], vt = val[kt];
+        const double lp = lam[kp], lq = lam[kq], lw = lam[kw], lt = lam[kt];
+        const double op = tl[kp], oq = tl[kq];
+        const double xp = fma(lp, irho, vp) + m1r;
+        const double xq = fma(lq, irho, vq) + m2r;
+        tl[kp] = xp;
+        tl[kq] = xq;
+        lam[kp] = fma(rho, vp - xp, lp);
+        lam[kq] = fma(rho, vq - xq, lq);
+        lam[kw] = fma(rho, vw - w_new, lw);
+        lam[kt] = fma(rho, vt - th_new, lt);
+        pr2 = fma(vp - xp, vp - xp, pr2);
+        du2 = fma(xp - op, xp - op, du2);
+        pr2 = fma(vq - xq, vq - xq, pr2);
+        du2 = fma(xq - oq, xq - oq, du2);
+        pr2 = fma(vw - w_new, vw - w_new, pr2);
+        du2 += dw2;
+        pr2 = fma(vt - th_new, vt - th_new, pr2);
+        du2 += dt2;
       }
       d.bus_w[b] = w_new;
       d.bus_th[b] = th_new;
@@ -325,19 +326,30 @@ __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // last CTA: per-instance residuals from that instance's blocks, in block order
-  for (int i = threadIdx.x; i < d.cap_inst; i += blockDim.x) {
+  // last CTA: each warp reduces whole instances, its lanes summing the instance's block
+  // partials strided by 32 and then combining them in a fixed butterfly; the result
+  // depends only on the instance's own blocks (the same bits alone or in a mix)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < d.cap_inst; i += kBusThreads / 32) {
     if (!d.inst_active[i]) continue;
     double p = 0.0, q = 0.0;
-    for (int bk = d.inst_blk[2 * i]; bk < d.inst_blk[2 * i + 1]; ++bk) {
+    const int b0 = d.inst_blk[2 * i], b1 = d.inst_blk[2 * i + 1];
+    for (int bk = b0 + lane; bk < b1; bk += 32) {
       p += __ldcg(d.part + 2 * bk);
       q += __ldcg(d.part + 2 * bk + 1);
     }
-    const int64_t it = d.inst_iter[i];
-    const size_t slot = ((size_t)i * d.H + (size_t)(it % d.H)) * 2;
-    d.hist[slot] = sqrt(p);
-    d.hist[slot + 1] = d.inst_param[4 * i] * sqrt(q);
-    d.inst_iter[i] = it + 1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      p += __shfl_xor_sync(0xffffffffu, p, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if (lane == 0) {
+      const int64_t it = d.inst_iter[i];
+      const size_t slot = ((size_t)i * d.H + (size_t)(it % d.H)) * 2;
+      d.hist[slot] = sqrt(p);
+      d.hist[slot + 1] = d.inst_param[4 * i] * sqrt(q);
+      d.inst_iter[i] = it + 1;
+    }
   }
   if (threadIdx.x == 0) *d.done = 0u;
 }
