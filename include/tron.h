@@ -115,7 +115,10 @@ typedef struct tron_options {
                                     (Sec. 4.3), 2 = right-looking with the trailing update
                                     spread over all lanes; both factor the same matrix as
                                     Lu D Lu^T and agree to rounding                       */
-  int32_t reserved[6];    /* must be zero                                                */
+  int32_t ctas_per_sm;    /* 0      persistent schedule: resident CTAs per SM (0 = as many
+                                    as fit); fewer shorten each problem's time and so the
+                                    launch's last-wave tail                                */
+  int32_t reserved[5];    /* must be zero                                                */
 } tron_options_t;
 
 typedef struct tron_batch tron_batch_t;
@@ -148,8 +151,12 @@ tron_err_t tron_batch_set_options(tron_batch_t* b, const tron_options_t* opt);
  *   d_f, d_pgnorm   out: objective and projected-gradient max-norm at x, [nprob]
  *   d_iters   out: outer iterations taken, [nprob]
  *   d_status  out: tron_status_t, [nprob]
- * Enqueues one launch (or one per size class for mixed sizes with the plain schedule)
- * on `stream`. */
+ * Enqueues one launch per size class on `stream` (with the persistent schedule and
+ * several classes, on streams forked from it and joined back).  Successive calls take
+ * the handle's four sets of work counters and forked streams in turn, so up to four
+ * solves of independent arrays may run at once on different streams (the last wave of
+ * one overlapping the start of the next); a fifth call reuses the first call's set and
+ * must be ordered after it (for example on the same stream). */
 tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const double* d_lower,
                             const double* d_upper, double* d_x, double* d_delta,
                             double* d_f, double* d_pgnorm, int32_t* d_iters,
@@ -221,10 +228,11 @@ int32_t tron_batch_last_launches(const tron_batch_t* b);
  * tron_batch_host_sync returns; the inputs (const) may be shared by calls in flight, and
  * results are copied out in call order, so calls that share output arrays leave the
  * last call's results there.  Copies overlap with compute only from
- * page-locked host memory (pageable memory works, serialised).  h_params may be NULL
- * for TRON_OBJ_HS45.  TRON_EINVAL without tron_batch_host_enable or for NULL arrays;
- * TRON_ECUDA on a CUDA error.  Does not mix with tron_batch_solve calls on other
- * streams that are still running on the same handle (they share the work counters).
+ * page-locked host memory (pageable memory works, serialised).  The two sets solve on
+ * two streams, so one call's solve may overlap the previous one's last wave.  h_params
+ * may be NULL for TRON_OBJ_HS45.  TRON_EINVAL without tron_batch_host_enable or for
+ * NULL arrays; TRON_ECUDA on a CUDA error.  Counts toward the four solves in flight of
+ * tron_batch_solve.
  *
  * tron_batch_host_sync: waits until every call's results are in host memory. */
 tron_err_t tron_batch_host_enable(tron_batch_t* b);

@@ -310,9 +310,15 @@ struct tron_batch {
     int tuned_chol;
   };
   std::vector<Bucket> buckets;
-  unsigned long long* d_counter;  // one work counter per bucket
-  cudaStream_t side[kNumClasses];  // forked streams of the persistent schedule
-  cudaEvent_t ev_fork, ev_join[kNumClasses];
+  // Work counters (one per bucket), forked streams and events of the persistent
+  // schedule, in kSolveSets sets taken in turn by successive solves, so that solves of
+  // independent batches on different streams can run at the same time (one's last wave
+  // overlapping the next one's start)
+  static constexpr int kSolveSets = 4;
+  unsigned long long* d_counter;  // [kSolveSets][8]
+  cudaStream_t side[kSolveSets][kNumClasses];
+  cudaEvent_t ev_fork[kSolveSets], ev_join[kSolveSets][kNumClasses];
+  int next_set;
   int64_t total_n;     // length of the concatenated vectors
   int64_t params_len;  // doubles of the packed parameter records
   int last_launches;
@@ -328,7 +334,7 @@ struct tron_batch {
   HostSet hs[2];
   bool host_ready;
   int host_next;
-  cudaStream_t s_in, s_run, s_out;
+  cudaStream_t s_in, s_run[2], s_out;  // copy in, solve (one per buffer set), copy out
 };
 
 static int64_t record_size(int kind, int n) {
@@ -350,6 +356,7 @@ static tron_err_t check_options(const tron_options_t* o) {
   XT_REQUIRE(o->layout >= 0 && o->layout <= 8, TRON_EINVAL, "options.layout must be in [0, 8]");
   XT_REQUIRE(o->cholesky >= 0 && o->cholesky <= 2, TRON_EINVAL,
              "options.cholesky must be 0, 1 or 2");
+  XT_REQUIRE(o->ctas_per_sm >= 0, TRON_EINVAL, "options.ctas_per_sm must be >= 0");
   return TRON_OK;
 }
 
@@ -413,17 +420,20 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
   b->d_poff = nullptr;
   b->d_voff = nullptr;
   b->d_counter = nullptr;
-  b->ev_fork = nullptr;
-  for (int i = 0; i < kNumClasses; ++i) {
-    b->side[i] = nullptr;
-    b->ev_join[i] = nullptr;
+  b->next_set = 0;
+  for (int k = 0; k < tron_batch::kSolveSets; ++k) {
+    b->ev_fork[k] = nullptr;
+    for (int i = 0; i < kNumClasses; ++i) {
+      b->side[k][i] = nullptr;
+      b->ev_join[k][i] = nullptr;
+    }
   }
   b->last_launches = 0;
   b->params_len = 0;
   memset(b->hs, 0, sizeof(b->hs));
   b->host_ready = false;
   b->host_next = 0;
-  b->s_in = b->s_run = b->s_out = nullptr;
+  b->s_in = b->s_run[0] = b->s_run[1] = b->s_out = nullptr;
   b->sms = device_sm_count();
   b->smem_optin = device_smem_optin();
   auto fail = [&](tron_err_t code) {
@@ -498,19 +508,23 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
       return fail(TRON_ECUDA);
     }
   }
-  if (cudaMalloc(&b->d_counter, sizeof(unsigned long long) * 8) != cudaSuccess) {
+  if (cudaMalloc(&b->d_counter, sizeof(unsigned long long) * 8 * tron_batch::kSolveSets) !=
+      cudaSuccess) {
     set_error("tron_batch_create: cudaMalloc of work counters failed");
     return fail(TRON_ENOMEM);
   }
-  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
-    set_error("tron_batch_create: cudaEventCreate failed");
-    return fail(TRON_ECUDA);
-  }
-  for (size_t i = 0; i < b->buckets.size(); ++i) {
-    if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
-      set_error("tron_batch_create: stream/event creation failed");
+  for (int k = 0; k < tron_batch::kSolveSets; ++k) {
+    if (cudaEventCreateWithFlags(&b->ev_fork[k], cudaEventDisableTiming) != cudaSuccess) {
+      set_error("tron_batch_create: cudaEventCreate failed");
       return fail(TRON_ECUDA);
+    }
+    if (b->buckets.size() < 2) continue;  // one class: nothing to fork
+    for (size_t i = 0; i < b->buckets.size(); ++i) {
+      if (cudaStreamCreateWithFlags(&b->side[k][i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->ev_join[k][i], cudaEventDisableTiming) != cudaSuccess) {
+        set_error("tron_batch_create: stream/event creation failed");
+        return fail(TRON_ECUDA);
+      }
     }
   }
   // resolve the kernels now so that a bad group option fails here
@@ -557,7 +571,9 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
   // persistent schedule with several size classes: every class on its own forked
   // stream, so all classes share the GPU in one pass
   const bool fork = persistent && b->buckets.size() > 1;
-  if (fork) XT_CUDA(cudaEventRecord(b->ev_fork, st));
+  const int cs = b->next_set;
+  b->next_set = (cs + 1) % tron_batch::kSolveSets;
+  if (fork) XT_CUDA(cudaEventRecord(b->ev_fork[cs], st));
   for (size_t bi = 0; bi < b->buckets.size(); ++bi) {
     const auto& bk = b->buckets[bi];
     if (bk.count == 0) continue;
@@ -576,8 +592,8 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
     wpb = geo.wpb;
     cudaStream_t ls = st;
     if (fork) {
-      ls = b->side[bi];
-      XT_CUDA(cudaStreamWaitEvent(ls, b->ev_fork, 0));
+      ls = b->side[cs][bi];
+      XT_CUDA(cudaStreamWaitEvent(ls, b->ev_fork[cs], 0));
     }
     KArgs a;
     memset(&a, 0, sizeof(a));
@@ -597,7 +613,7 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
     a.count = bk.count;
     a.n_uniform = b->n_uniform;
     a.pstride = record_size(b->kind, b->n_uniform);
-    a.counter = b->d_counter + bi;
+    a.counter = b->d_counter + 8 * cs + bi;
     a.opt = b->opt;
     if (bk.tuned && b->opt.group == 0 && b->opt.cholesky == 0) a.opt.cholesky = bk.tuned_chol;
     const size_t smem = geo.smem;
@@ -618,6 +634,7 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
         }
       }
       XT_REQUIRE(occ > 0, TRON_EUNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
+      if (b->opt.ctas_per_sm > 0) occ = std::min(occ, (int)b->opt.ctas_per_sm);
       grid = std::min<int64_t>((int64_t)occ * b->sms, (bk.count + geo.per_cta - 1) / geo.per_cta);
       XT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), ls));
     } else {
@@ -627,8 +644,8 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
     XT_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(geo.threads), args, smem, ls));
     b->last_launches++;
     if (fork) {
-      XT_CUDA(cudaEventRecord(b->ev_join[bi], ls));
-      XT_CUDA(cudaStreamWaitEvent(st, b->ev_join[bi], 0));
+      XT_CUDA(cudaEventRecord(b->ev_join[cs][bi], ls));
+      XT_CUDA(cudaStreamWaitEvent(st, b->ev_join[cs][bi], 0));
     }
   }
   return TRON_OK;
@@ -783,11 +800,13 @@ tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const do
 
 void tron_batch_destroy(tron_batch_t* b) {
   if (!b) return;
-  for (int i = 0; i < kNumClasses; ++i) {
-    if (b->side[i]) cudaStreamDestroy(b->side[i]);
-    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+  for (int k = 0; k < tron_batch::kSolveSets; ++k) {
+    for (int i = 0; i < kNumClasses; ++i) {
+      if (b->side[k][i]) cudaStreamDestroy(b->side[k][i]);
+      if (b->ev_join[k][i]) cudaEventDestroy(b->ev_join[k][i]);
+    }
+    if (b->ev_fork[k]) cudaEventDestroy(b->ev_fork[k]);
   }
-  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   cudaFree(b->d_n);
   cudaFree(b->d_poff);
   cudaFree(b->d_voff);
@@ -808,7 +827,8 @@ void tron_batch_destroy(tron_batch_t* b) {
     if (h.out_done) cudaEventDestroy(h.out_done);
   }
   if (b->s_in) cudaStreamDestroy(b->s_in);
-  if (b->s_run) cudaStreamDestroy(b->s_run);
+  if (b->s_run[0]) cudaStreamDestroy(b->s_run[0]);
+  if (b->s_run[1]) cudaStreamDestroy(b->s_run[1]);
   if (b->s_out) cudaStreamDestroy(b->s_out);
   delete b;
 }
@@ -839,7 +859,8 @@ tron_err_t tron_batch_host_enable(tron_batch_t* b) {
     XT_CUDA(cudaEventCreateWithFlags(&h.out_done, cudaEventDisableTiming));
   }
   XT_CUDA(cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
-  XT_CUDA(cudaStreamCreateWithFlags(&b->s_run, cudaStreamNonBlocking));
+  XT_CUDA(cudaStreamCreateWithFlags(&b->s_run[0], cudaStreamNonBlocking));
+  XT_CUDA(cudaStreamCreateWithFlags(&b->s_run[1], cudaStreamNonBlocking));
   XT_CUDA(cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
   b->host_ready = true;
   return TRON_OK;
@@ -860,7 +881,9 @@ tron_err_t tron_batch_solve_host(tron_batch_t* b, const double* h_params, const 
              TRON_EINVAL, "tron_batch_solve_host: null host array");
   XT_REQUIRE(h_params || b->params_len == 0, TRON_EINVAL,
              "tron_batch_solve_host: h_params is NULL");
-  auto& h = b->hs[b->host_next];
+  const int hi = b->host_next;
+  auto& h = b->hs[hi];
+  cudaStream_t run = b->s_run[hi];
   b->host_next ^= 1;
   const size_t np = (size_t)b->nprob, nv = (size_t)b->total_n;
   const cudaMemcpyKind up = cudaMemcpyHostToDevice, down = cudaMemcpyDeviceToHost;
@@ -874,12 +897,13 @@ tron_err_t tron_batch_solve_host(tron_batch_t* b, const double* h_params, const 
   XT_CUDA(cudaMemcpyAsync(h.x, h_x0, nv * sizeof(double), up, b->s_in));
   XT_CUDA(cudaMemcpyAsync(h.delta, h_delta0, np * sizeof(double), up, b->s_in));
   XT_CUDA(cudaEventRecord(h.in_done, b->s_in));
-  // the solve
-  XT_CUDA(cudaStreamWaitEvent(b->s_run, h.in_done, 0));
+  // the solve, on this set's stream: the previous call's solve (other set) may still be
+  // finishing its last wave
+  XT_CUDA(cudaStreamWaitEvent(run, h.in_done, 0));
   tron_err_t e = tron_batch_solve(b, b->params_len > 0 ? h.params : nullptr, h.lo, h.hi, h.x,
-                                  h.delta, h.f, h.pg, h.iters, h.status, b->s_run);
+                                  h.delta, h.f, h.pg, h.iters, h.status, run);
   if (e != TRON_OK) return e;
-  XT_CUDA(cudaEventRecord(h.solved, b->s_run));
+  XT_CUDA(cudaEventRecord(h.solved, run));
   // results
   XT_CUDA(cudaStreamWaitEvent(b->s_out, h.solved, 0));
   XT_CUDA(cudaMemcpyAsync(h_x, h.x, nv * sizeof(double), down, b->s_out));
@@ -897,7 +921,8 @@ tron_err_t tron_batch_host_sync(tron_batch_t* b) {
   XT_REQUIRE(b != nullptr, TRON_EINVAL, "tron_batch_host_sync: null handle");
   if (!b->host_ready) return TRON_OK;
   XT_CUDA(cudaStreamSynchronize(b->s_in));
-  XT_CUDA(cudaStreamSynchronize(b->s_run));
+  XT_CUDA(cudaStreamSynchronize(b->s_run[0]));
+  XT_CUDA(cudaStreamSynchronize(b->s_run[1]));
   XT_CUDA(cudaStreamSynchronize(b->s_out));
   return TRON_OK;
 }
@@ -1070,6 +1095,7 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
       }
     }
     XT_REQUIRE(occ > 0, TRON_EUNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
+    if (o.ctas_per_sm > 0) occ = std::min(occ, (int)o.ctas_per_sm);
     const int64_t grid =
         std::min<int64_t>((int64_t)occ * sms, (count[s] + geo.per_cta - 1) / geo.per_cta);
     void* args[] = {&a};

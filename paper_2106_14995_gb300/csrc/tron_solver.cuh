@@ -513,9 +513,12 @@ struct Solver {
   // and the same w, which the trust region bounds directly.  When alpha = 0, M = A and
   // Ahat = I: the first step, of length 1 along M^-1 res, is the minimiser and leaves a
   // zero residual, so it is taken without forming A p.
-  // Returns 0 converged, 1 iteration cap, 2 boundary, 3 negative curvature.
+  // Returns 0 converged, 1 iteration cap, 2 boundary, 3 negative curvature; wscale is
+  // sigma > 0 when w was taken that way (then A w = -sigma rF), else 0.
   __device__ __forceinline__ int steihaug(int m, double delta, bool exact,
-                                          const double (&rF)[R], double (&w)[R]) {
+                                          const double (&rF)[R], double (&w)[R],
+                                          double& wscale) {
+    wscale = 0.0;
     double res[R], z[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -530,6 +533,7 @@ struct Solver {
       const double sg = (zz >= dsq) ? delta / sqrt(zz) : 1.0;
 #pragma unroll
       for (int r = 0; r < R; ++r) w[r] = sg * z[r];
+      wscale = sg;  // A w = -sg rF
       return (zz >= dsq) ? 2 : 0;
     }
     double p[R], q[R];
@@ -638,6 +642,43 @@ struct Solver {
 #pragma unroll
     for (int r = 0; r < R; ++r) fin = fin && isfinite(v[r]);
     return !gp.any(!fin);
+  }
+
+  // H d for the projected search's first trial d = P[y + w] - y when nothing is clipped
+  // and w came from the exact-preconditioner step: on the free rows H_FF w_F = -sigma rF
+  // (rF is rv there), so only the rows of the bound variables (at most 3, d = 0 on
+  // them) need their dot products, reduced in one fused butterfly.  One variable per
+  // lane only; false, with nothing computed, otherwise.
+  __device__ __forceinline__ bool first_trial_known(double wscale, const int (&cidx)[R],
+                                                    const bool (&cn)[R], const double (&rv)[R],
+                                                    const double (&d)[R], double (&Hd)[R]) {
+    if constexpr (R != 1 || G == 1 || G > 32) {
+      return false;
+    } else {
+      if (wscale == 0.0 || gp.any(cn[0])) return false;
+      const bool bnd = cidx[0] < 0 && gp.t < n;
+      const unsigned msk = gp.ballot(bnd);
+      if (__popc(msk) > 3) return false;
+      int ib[3] = {-1, -1, -1};
+      unsigned mm = msk;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (mm) {
+          ib[q] = __ffs(mm) - 1;
+          mm &= mm - 1u;
+        }
+      }
+      double p0 = ib[0] >= 0 ? obj.hq(ib[0], gp.t) * d[0] : 0.0;
+      double p1 = ib[1] >= 0 ? obj.hq(ib[1], gp.t) * d[0] : 0.0;
+      double p2 = ib[2] >= 0 ? obj.hq(ib[2], gp.t) * d[0] : 0.0;
+      gp.sum3(p0, p1, p2);
+      double h = (cidx[0] >= 0) ? -wscale * rv[0] : 0.0;
+      if (gp.t == ib[0]) h = p0;
+      if (gp.t == ib[1]) h = p1;
+      if (gp.t == ib[2]) h = p2;
+      Hd[0] = h;
+      return true;
+    }
   }
 
   // ------------------------------------------------------------------- Algorithm 1
@@ -770,8 +811,8 @@ struct Solver {
           status = TRON_CHOL_FAIL;
           break;
         }
-        double wF[R];
-        const int info = steihaug(m, delta, fac == 1, rF, wF);
+        double wF[R], wscale;
+        const int info = steihaug(m, delta, fac == 1, rF, wF, wscale);
         // scatter w_F to the full direction w
 #pragma unroll
         for (int r = 0; r < R; ++r) vb[r * G + gp.t] = 0.0;
@@ -805,7 +846,7 @@ struct Solver {
           // after the first trial, H d is rescaled from the previous one (the step
           // length shrinks by proj_shrink)
           if (t == 0) {
-            hv(dn, Hd);
+            if (!first_trial_known(wscale, cidx, cn, rv, dn, Hd)) hv(dn, Hd);
           } else {
             bool both[R];
 #pragma unroll

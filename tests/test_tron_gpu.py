@@ -193,6 +193,36 @@ def test_persistent_equals_plain_bitwise():
         np.testing.assert_array_equal(a[k], b[k])
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_concurrent_solves_on_two_streams_equal_sequential(mixed):
+    # one handle, four solves of different batches alternating between two streams (each
+    # takes its own work counters): the same bits as solving them one after another
+    if mixed:
+        # one size layout, four starting points inside the box
+        base = synth.uneven_batch(600, seed_index=90)
+        ds = [dict(base, x0=base["x0"] + 0.01 * i) for i in range(4)]
+        kw = dict(n=None, n_list=base["nvec"])
+    else:
+        ds = [synth.dense_batch(800, 32, seed_index=95 + i) for i in range(4)]
+        kw = dict(n=32, n_list=None)
+    refs = [gpu_solve(d, schedule=native.TRON_SCHED_PERSISTENT, **kw) for d in ds]
+    B = ds[0]["delta0"].shape[0]
+    tb = TronBatch(2, B, n=kw["n"], n_list=kw["n_list"],
+                   opts=options(schedule=native.TRON_SCHED_PERSISTENT))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for i, d in enumerate(ds):
+        st = streams[i % 2]
+        with torch.cuda.stream(st):
+            x, dl = _t(d["x0"]), _t(d["delta0"])
+            outs.append(tb.solve(_t(d["params"]), _t(d["l"]), _t(d["u"]), x, dl, stream=st))
+    torch.cuda.synchronize()
+    tb.close()
+    for o, r in zip(outs, refs):
+        for k in ("x", "delta", "f", "pg", "iters", "status"):
+            np.testing.assert_array_equal(o[k].cpu().numpy(), r[k], err_msg=k)
+
+
 def _host(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).pin_memory()
 
