@@ -340,6 +340,12 @@ struct Solver {
   // column from vb and the still unscaled one from the factor storage, which takes the
   // scaled values once the update is done.
   __device__ __forceinline__ bool chol_right(int m) {
+    // row/column of element gp.t of a trailing triangle (the same for every j); later
+    // elements of this lane follow by stepping G positions along the rows
+    int cc0 = (int)((sqrtf(8.0f * (float)gp.t + 1.0f) - 1.0f) * 0.5f);
+    while (cc0 * (cc0 + 1) / 2 > gp.t) --cc0;
+    while ((cc0 + 1) * (cc0 + 2) / 2 <= gp.t) ++cc0;
+    const int ec0 = gp.t - cc0 * (cc0 + 1) / 2;
     for (int j = 0; j < m; ++j) {
       const double piv = lo(j, j);
       if (!positive(piv)) {
@@ -361,13 +367,15 @@ struct Solver {
       gp.sync();
       const int M = m - j - 1;
       const int T = M * (M + 1) / 2;
+      int cc = cc0, ec = ec0;
       for (int e = gp.t; e < T; e += G) {
-        int cc = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while (cc * (cc + 1) / 2 > e) --cc;
-        while ((cc + 1) * (cc + 2) / 2 <= e) ++cc;
-        const int ec = e - cc * (cc + 1) / 2;
         const int c = j + 1 + cc, d = j + 1 + ec;
         lo(c, d) = fma(-vb[c], lo(d, j), lo(c, d));
+        ec += G;
+        while (ec > cc) {
+          ec -= cc + 1;
+          ++cc;
+        }
       }
       gp.sync();
 #pragma unroll
