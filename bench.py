@@ -37,9 +37,9 @@ FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.0
 # problems, scaled per problem to the launch), valid only for the kernel sources it was
 # taken on: DRAM bytes (19.05 MB per 2,000 problems) and the FP64 flops the kernel
 # executes (thread-level DFMA x 2 + DADD + DMUL: 317.5 Mflop per 2,000 problems).
-TRAFFIC_BYTES_PER_PROBLEM = 19.05152e6 / 2000
+TRAFFIC_BYTES_PER_PROBLEM = 19.051776e6 / 2000
 EXEC_FLOPS_PER_PROBLEM = 317.48e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "a0b6526bbd61612d82114226fbc7f2d1cc7815da"
+TRAFFIC_SOURCES_SHA1 = "361994aff232ddd33419be12174fe4930325a4f3"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
