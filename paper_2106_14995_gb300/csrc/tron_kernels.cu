@@ -798,6 +798,8 @@ tron_err_t tron_batch_autotune(tron_batch_t* b, const double* d_params, const do
   return err;
 }
 
+static void host_release(tron_batch* b);
+
 void tron_batch_destroy(tron_batch_t* b) {
   if (!b) return;
   for (int k = 0; k < tron_batch::kSolveSets; ++k) {
@@ -812,6 +814,12 @@ void tron_batch_destroy(tron_batch_t* b) {
   cudaFree(b->d_voff);
   cudaFree(b->d_counter);
   for (auto& bk : b->buckets) cudaFree(bk.d_list);
+  host_release(b);
+  delete b;
+}
+
+// ------------------------------------------------------------------- host buffers
+static void host_release(tron_batch* b) {
   for (auto& h : b->hs) {
     cudaFree(h.params);
     cudaFree(h.lo);
@@ -826,18 +834,27 @@ void tron_batch_destroy(tron_batch_t* b) {
     if (h.solved) cudaEventDestroy(h.solved);
     if (h.out_done) cudaEventDestroy(h.out_done);
   }
+  memset(b->hs, 0, sizeof(b->hs));
   if (b->s_in) cudaStreamDestroy(b->s_in);
   if (b->s_run[0]) cudaStreamDestroy(b->s_run[0]);
   if (b->s_run[1]) cudaStreamDestroy(b->s_run[1]);
   if (b->s_out) cudaStreamDestroy(b->s_out);
-  delete b;
+  b->s_in = b->s_run[0] = b->s_run[1] = b->s_out = nullptr;
+  b->host_ready = false;
 }
 
-// ------------------------------------------------------------------- host buffers
+static tron_err_t host_setup(tron_batch* b);
+
 tron_err_t tron_batch_host_enable(tron_batch_t* b) {
   clear_error();
   XT_REQUIRE(b != nullptr, TRON_EINVAL, "tron_batch_host_enable: null handle");
   if (b->host_ready) return TRON_OK;
+  const tron_err_t e = host_setup(b);
+  if (e != TRON_OK) host_release(b);  // nothing half-made stays behind
+  return e;
+}
+
+static tron_err_t host_setup(tron_batch* b) {
   const size_t np = (size_t)std::max<int64_t>(b->nprob, 1);
   const size_t nv = (size_t)std::max<int64_t>(b->total_n, 1);
   const size_t npar = (size_t)std::max<int64_t>(b->params_len, 1);
