@@ -9,7 +9,9 @@ Functions whose result is pinned by the tests: ``tron_solve``/``tron_batch`` (cl
 forms, brute force, the hs45 solution printed in Sec. 4.2, KKT), ``eval_obj`` (finite
 differences, autograd, complex power), ``chol_shifted``/``chol`` (numpy), ``trqsol``
 (quadratic roots), ``steihaug`` (one iteration when A is positive definite, Sec. 4.3),
-``admm_run`` (closed-form bus/generator KKT, residual decay).
+``admm_run`` (closed-form bus/generator KKT, residual decay), ``MultiPeriodAdmm`` (equal
+to independent single-period runs when no ramp binds; brute force on the generator
+chain).
 """
 from __future__ import annotations
 
@@ -27,7 +29,7 @@ _SRC = [os.path.join(_HERE, "tron_oracle.c")]
 _lock = threading.Lock()
 _lib = None
 
-OBJ_BRANCH, OBJ_DENSE, OBJ_HS45 = 1, 2, 3
+OBJ_BRANCH, OBJ_DENSE, OBJ_HS45, OBJ_GENRAMP = 1, 2, 3, 4
 CONVERGED, MAX_ITER, TR_TOO_SMALL, CHOL_FAIL, NONFINITE, BAD_BOUNDS = range(6)
 STATUS_NAMES = ["CONVERGED", "MAX_ITER", "TR_TOO_SMALL", "CHOL_FAIL", "NONFINITE", "BAD_BOUNDS"]
 
@@ -142,6 +144,10 @@ def _load(path: str):
             L.ot_admm_run.argtypes = [C.POINTER(Net), C.POINTER(State), C.POINTER(Opts),
                                       C.c_int, C.c_int, P, P, P, C.POINTER(Counters)]
             L.ot_admm_branch_record.argtypes = [C.POINTER(Net), C.POINTER(State), C.c_int, P]
+            L.ot_admm_mp_init.argtypes = [C.POINTER(MP)]
+            L.ot_admm_mp_run.argtypes = [C.POINTER(MP), C.POINTER(Opts), C.c_int, C.c_int, P, P,
+                                         C.POINTER(Counters)]
+            L.ot_genramp_record.argtypes = [C.POINTER(MP), C.c_int, P]
             return L
 
 
@@ -345,3 +351,55 @@ class Admm:
         rec = np.zeros(36)
         lib().ot_admm_branch_record(C.byref(self.net), C.byref(self.state), int(k), _p(rec))
         return rec
+
+
+# ----------------------------------------------------------- multi-period ADMM
+
+class MP(C.Structure):
+    _fields_ = [("T", C.c_int32), ("nets", C.c_void_p), ("states", C.c_void_p),
+                ("ramp", C.c_void_p), ("rho_ramp", C.c_double), ("gen_delta", C.c_void_p)]
+
+
+class MultiPeriodAdmm:
+    """Oracle multi-period ADMM: T periods of ``net`` with loads scaled by
+    ``load_scale[t]``, generators coupled across periods by the ramp penalty
+    rho_ramp/2 max(0, |p_t - p_{t-1}| - ramp[g])^2 (``ramp`` scalar or [ngen])."""
+
+    def __init__(self, net: dict, load_scale, ramp, rho_ramp: float = 400.0,
+                 rho: float = 400.0, rho_line: float | None = None, vmin: float = 0.9,
+                 vmax: float = 1.1):
+        self.T = T = len(load_scale)
+        ng = len(net["gen_bus"])
+        self.periods = []
+        for t in range(T):
+            nt = dict(net)
+            nt["bus_pd"] = np.asarray(net["bus_pd"], dtype=np.float64) * float(load_scale[t])
+            nt["bus_qd"] = np.asarray(net["bus_qd"], dtype=np.float64) * float(load_scale[t])
+            self.periods.append(Admm(nt, rho=rho, rho_line=rho_line, vmin=vmin, vmax=vmax))
+        self._nets = (Net * T)(*[a.net for a in self.periods])
+        self._states = (State * T)(*[a.state for a in self.periods])
+        self.ramp = np.ascontiguousarray(np.broadcast_to(np.asarray(ramp, dtype=np.float64),
+                                                         (ng,)))
+        self.gen_delta = np.zeros(ng)
+        self.mp = MP(T=T, nets=C.cast(self._nets, C.c_void_p).value,
+                     states=C.cast(self._states, C.c_void_p).value,
+                     ramp=self.ramp.ctypes.data, rho_ramp=float(rho_ramp),
+                     gen_delta=self.gen_delta.ctypes.data)
+        lib().ot_admm_mp_init(C.byref(self.mp))
+        self.counters = Counters()
+
+    def run(self, niters: int, opts: Opts | None = None, nthreads: int = 1):
+        o = opts or default_opts()
+        hp = np.zeros(niters)
+        hd = np.zeros(niters)
+        lib().ot_admm_mp_run(C.byref(self.mp), C.byref(o), int(niters), int(nthreads),
+                             _p(hp), _p(hd), C.byref(self.counters))
+        return hp, hd
+
+    def genramp_record(self, g: int) -> np.ndarray:
+        rec = np.zeros(8 + 2 * self.T)
+        lib().ot_genramp_record(C.byref(self.mp), int(g), _p(rec))
+        return rec
+
+    def state(self, t: int) -> dict:
+        return self.periods[t].arrays

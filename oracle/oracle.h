@@ -22,7 +22,7 @@ extern "C" {
 #endif
 
 /* objective kinds (same numbering as the public C-ABI, defined independently) */
-enum { OT_OBJ_BRANCH = 1, OT_OBJ_DENSE = 2, OT_OBJ_HS45 = 3 };
+enum { OT_OBJ_BRANCH = 1, OT_OBJ_DENSE = 2, OT_OBJ_HS45 = 3, OT_OBJ_GENRAMP = 4 };
 
 /* per-problem status */
 enum {
@@ -131,6 +131,27 @@ void ot_admm_run(const ot_net* net, ot_state* st, const ot_opts* o, int niters, 
                  ot_counters* total);
 /* build the 36-entry branch record of branch k from the current state */
 void ot_admm_branch_record(const ot_net* net, const ot_state* st, int k, double* rec);
+
+/* --------------------------------------- multi-period ADMM (future work of Sec. 7)
+ * T periods of one network (nets[t] differ only in their loads); the generator
+ * component spans the periods: its T active-power outputs are one NLP of kind
+ * OT_OBJ_GENRAMP with the ramp penalty rho_ramp/2 max(0, |p_t - p_{t-1}| - ramp[g])^2,
+ * solved by TRON warm started from the previous iteration; everything else is the
+ * single-period iteration, period by period.  Residuals combine all periods. */
+typedef struct ot_mp {
+  int32_t T;
+  const ot_net* nets;   /* [T] */
+  ot_state* states;     /* [T] */
+  const double* ramp;   /* [ngen] ramp limit between consecutive periods */
+  double rho_ramp;
+  double* gen_delta;    /* [ngen] trust radius carried between iterations */
+} ot_mp;
+
+void ot_admm_mp_init(ot_mp* mp);
+void ot_admm_mp_run(ot_mp* mp, const ot_opts* o, int niters, int nthreads,
+                    double* hist_primal, double* hist_dual, ot_counters* total);
+/* the (8 + 2T)-entry record of generator g from the current states */
+void ot_genramp_record(const ot_mp* mp, int g, double* rec);
 
 #ifdef __cplusplus
 }

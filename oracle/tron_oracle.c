@@ -531,6 +531,55 @@ static int eval_branch(const double* P, const double* x, double* f, double* g, d
   return 0;
 }
 
+/* Generator of the multi-period ADMM over its n periods (readings R16-R17), record
+ * [c2 c1 rho rho_r R 0 0 0 | lambda[n] | target[n]]:
+ *   f = sum_t c2 p_t^2 + c1 p_t + lambda_t (p_t - target_t) + rho/2 (p_t - target_t)^2
+ *       + rho_r/2 sum_{t >= 1} max(0, |p_t - p_{t-1}| - R)^2
+ * The ramp term's second derivative is rho_r on |d| > R and 0 below (as for the line
+ * limit of the branch objective). */
+static int eval_genramp(int n, const double* P, const double* x, double* f, double* g,
+                        double* H, ot_counters* c, double* fscale) {
+  double c2 = P[0], c1 = P[1], rho = P[2], rr = P[3], R = P[4];
+  const double* lam = P + 8;
+  const double* tgt = P + 8 + n;
+  double val = 0.0, mag = 0.0;
+  if (g)
+    for (int t = 0; t < n; t++) g[t] = 0.0;
+  if (H)
+    for (int e = 0; e < n * n; e++) H[e] = 0.0;
+  for (int t = 0; t < n; t++) {
+    double p = x[t], r = p - tgt[t];
+    val += c2 * p * p + c1 * p + lam[t] * r + 0.5 * rho * r * r;
+    mag += fabs(c2) * p * p + fabs(c1 * p) + fabs(lam[t] * r) + 0.5 * rho * r * r +
+           (fabs(lam[t]) + rho * fabs(r)) * (fabs(p) + fabs(tgt[t]));
+    if (g) g[t] += 2.0 * c2 * p + c1 + lam[t] + rho * r;
+    if (H) H[t * n + t] += 2.0 * c2 + rho;
+  }
+  for (int t = 1; t < n; t++) {
+    double d = x[t] - x[t - 1];
+    double e = fabs(d) - R;
+    if (e > 0.0) {
+      double s = d > 0.0 ? 1.0 : -1.0;
+      val += 0.5 * rr * e * e;
+      mag += 0.5 * rr * e * e + rr * e * (fabs(x[t]) + fabs(x[t - 1]) + R);
+      if (g) {
+        g[t] += rr * e * s;
+        g[t - 1] -= rr * e * s;
+      }
+      if (H) {
+        H[t * n + t] += rr;
+        H[(t - 1) * n + (t - 1)] += rr;
+        H[t * n + (t - 1)] -= rr;
+        H[(t - 1) * n + t] -= rr;
+      }
+    }
+  }
+  *f = val;
+  if (fscale) *fscale = mag;
+  if (c) c->flops += 14.0 * n + 10.0 * (n - 1);
+  return 0;
+}
+
 /* f, gradient, Hessian; *fscale receives the sum of the magnitudes of the terms f is
  * assembled from (including, for the branch, the first-order effect of the terms of
  * each flow), the scale of the rounding error of the computed f */
@@ -542,6 +591,7 @@ static int eval_c(int kind, int n, const double* P, const double* x, double* f, 
     case OT_OBJ_BRANCH:
       if (n != 4) return -1;
       return eval_branch(P, x, f, g, H, c, fscale);
+    case OT_OBJ_GENRAMP: return eval_genramp(n, P, x, f, g, H, c, fscale);
     default: return -1;
   }
 }
@@ -939,16 +989,23 @@ static double pair_tilde(const ot_net* net, const ot_state* st, int k, int a) {
   }
 }
 
-void ot_admm_run(const ot_net* net, ot_state* st, const ot_opts* o, int niters, int nthreads,
-                 double* hist_primal, double* hist_dual, int64_t* status_counts,
-                 ot_counters* total) {
+/* incidence lists and branch-solve buffers of one network (ADMM workspace) */
+typedef struct admm_ws {
+  int *ep, *gp, *el, *gl;
+  int32_t* n4;
+  int64_t *poff, *voff;
+  double *recs, *bl, *bu, *bf, *bpg, *tprev;
+  int32_t *bit, *bst;
+} admm_ws;
+
+static void admm_ws_init(const ot_net* net, admm_ws* w) {
   int nb = net->nbus, nl = net->nbranch, ng = net->ngen;
-  double rho = net->rho;
   /* bus incidence, ends and generators listed in increasing id (end id = 2 k + side) */
-  int* ep = (int*)calloc((size_t)nb + 1, sizeof(int));
-  int* gp = (int*)calloc((size_t)nb + 1, sizeof(int));
-  int* el = (int*)malloc(sizeof(int) * (size_t)(2 * nl + 1));
-  int* gl = (int*)malloc(sizeof(int) * (size_t)(ng + 1));
+  w->ep = (int*)calloc((size_t)nb + 1, sizeof(int));
+  w->gp = (int*)calloc((size_t)nb + 1, sizeof(int));
+  w->el = (int*)malloc(sizeof(int) * (size_t)(2 * nl + 1));
+  w->gl = (int*)malloc(sizeof(int) * (size_t)(ng + 1));
+  int *ep = w->ep, *gp = w->gp, *el = w->el, *gl = w->gl;
   for (int k = 0; k < nl; k++) {
     ep[net->br_from[k] + 1]++;
     ep[net->br_to[k] + 1]++;
@@ -972,154 +1029,275 @@ void ot_admm_run(const ot_net* net, ot_state* st, const ot_opts* o, int niters, 
     }
     free(fill);
   }
-  int32_t* n4 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
-  int64_t* poff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl + 1));
-  int64_t* voff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl + 1));
-  double* recs = (double*)malloc(sizeof(double) * 36 * (size_t)(nl + 1));
-  double* bl = (double*)malloc(sizeof(double) * 4 * (size_t)(nl + 1));
-  double* bu = (double*)malloc(sizeof(double) * 4 * (size_t)(nl + 1));
-  double* bf = (double*)malloc(sizeof(double) * (size_t)(nl + 1));
-  double* bpg = (double*)malloc(sizeof(double) * (size_t)(nl + 1));
-  int32_t* bit = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
-  int32_t* bst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
-  double* tprev = (double*)malloc(sizeof(double) * (size_t)(8 * nl + 2 * ng + 1));
+  w->n4 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
+  w->poff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl + 1));
+  w->voff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl + 1));
+  w->recs = (double*)malloc(sizeof(double) * 36 * (size_t)(nl + 1));
+  w->bl = (double*)malloc(sizeof(double) * 4 * (size_t)(nl + 1));
+  w->bu = (double*)malloc(sizeof(double) * 4 * (size_t)(nl + 1));
+  w->bf = (double*)malloc(sizeof(double) * (size_t)(nl + 1));
+  w->bpg = (double*)malloc(sizeof(double) * (size_t)(nl + 1));
+  w->bit = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
+  w->bst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
+  w->tprev = (double*)malloc(sizeof(double) * (size_t)(8 * nl + 2 * ng + 1));
   const double twopi = 6.283185307179586476925286766559;
   for (int k = 0; k < nl; k++) {
-    n4[k] = 4;
-    poff[k] = 36 * (int64_t)k;
-    voff[k] = 4 * (int64_t)k;
-    bl[4 * k + 0] = net->vmin;
-    bl[4 * k + 1] = net->vmin;
-    bl[4 * k + 2] = -twopi;
-    bl[4 * k + 3] = -twopi;
-    bu[4 * k + 0] = net->vmax;
-    bu[4 * k + 1] = net->vmax;
-    bu[4 * k + 2] = twopi;
-    bu[4 * k + 3] = twopi;
+    w->n4[k] = 4;
+    w->poff[k] = 36 * (int64_t)k;
+    w->voff[k] = 4 * (int64_t)k;
+    w->bl[4 * k + 0] = net->vmin;
+    w->bl[4 * k + 1] = net->vmin;
+    w->bl[4 * k + 2] = -twopi;
+    w->bl[4 * k + 3] = -twopi;
+    w->bu[4 * k + 0] = net->vmax;
+    w->bu[4 * k + 1] = net->vmax;
+    w->bu[4 * k + 2] = twopi;
+    w->bu[4 * k + 3] = twopi;
   }
+}
 
+static void admm_ws_free(admm_ws* w) {
+  free(w->ep);
+  free(w->gp);
+  free(w->el);
+  free(w->gl);
+  free(w->n4);
+  free(w->poff);
+  free(w->voff);
+  free(w->recs);
+  free(w->bl);
+  free(w->bu);
+  free(w->bf);
+  free(w->bpg);
+  free(w->bit);
+  free(w->bst);
+  free(w->tprev);
+}
+
+/* closed-form generator update: minimiser of the box-clipped scalar quadratics; only q
+ * when active_power is 0 (the multi-period update sets p) */
+static void admm_gen_update(const ot_net* net, ot_state* st, int active_power) {
+  double rho = net->rho;
+  for (int g = 0; g < net->ngen; g++) {
+    double pt = st->gen_tilde[2 * g], qt = st->gen_tilde[2 * g + 1];
+    double lp = st->gen_lam[2 * g], lq = st->gen_lam[2 * g + 1];
+    double p = (rho * pt - lp - net->gen_c1[g]) / (2.0 * net->gen_c2[g] + rho);
+    double q = qt - lq / rho;
+    if (active_power) st->gen_pq[2 * g] = proj1(p, net->gen_pmin[g], net->gen_pmax[g]);
+    st->gen_pq[2 * g + 1] = proj1(q, net->gen_qmin[g], net->gen_qmax[g]);
+  }
+}
+
+/* one ADMM iteration after the generator update: branch updates, bus updates,
+ * multipliers; returns the squared primal and (unscaled) dual residual sums */
+static void admm_after_gens(const ot_net* net, ot_state* st, const ot_opts* o, int nthreads,
+                            admm_ws* w, int64_t* status_counts, ot_counters* total,
+                            double* pr2_out, double* du2_out) {
+  int nb = net->nbus, nl = net->nbranch, ng = net->ngen;
+  double rho = net->rho;
+  int *ep = w->ep, *gp = w->gp, *el = w->el, *gl = w->gl;
+  double* tprev = w->tprev;
+  /* branch update: TRON on eq. exp-branch, warm started from the previous x, delta */
+  for (int k = 0; k < nl; k++) ot_admm_branch_record(net, st, k, w->recs + 36 * (size_t)k);
+  ot_tron_batch(OT_OBJ_BRANCH, nl, w->n4, w->poff, w->voff, w->recs, w->bl, w->bu, st->br_x,
+                st->br_delta, o, w->bf, w->bpg, w->bit, w->bst, nthreads, total);
+  if (status_counts)
+    for (int k = 0; k < nl; k++)
+      if (w->bst[k] >= 0 && w->bst[k] < 6) status_counts[w->bst[k]]++;
+  for (int k = 0; k < nl; k++)
+    branch_values_at(net->br_coef + 8 * (size_t)k, st->br_x + 4 * (size_t)k,
+                     st->br_val + 8 * (size_t)k);
+  /* remember the bus-side copies for the dual residual */
+  for (int g = 0; g < ng; g++) {
+    tprev[2 * g] = st->gen_tilde[2 * g];
+    tprev[2 * g + 1] = st->gen_tilde[2 * g + 1];
+  }
+  for (int k = 0; k < nl; k++)
+    for (int a = 0; a < 8; a++) tprev[2 * ng + 8 * k + a] = pair_tilde(net, st, k, a);
+  /* bus update: minimise sum rho/2 (xt - a)^2 with a = x + lambda/rho subject to the
+   * bus balance equations (eqs. PowerBalanceReal/Reactive); x = a - D^-1 A' mu with
+   * (A D^-1 A') mu = A a - (p_d, q_d) */
+  for (int b = 0; b < nb; b++) {
+    double rhsP = -net->bus_pd[b], rhsQ = -net->bus_qd[b];
+    double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
+    for (int t = gp[b]; t < gp[b + 1]; t++) {
+      int g = gl[t];
+      rhsP += st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho;
+      rhsQ += st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho;
+      sinv += 1.0 / rho;
+    }
+    for (int t = ep[b]; t < ep[b + 1]; t++) {
+      int e = el[t], k = e / 2, side = e % 2;
+      const double* val = st->br_val + 8 * (size_t)k;
+      const double* lam = st->br_lam + 8 * (size_t)k;
+      int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
+      rhsP -= val[kp] + lam[kp] / rho;
+      rhsQ -= val[kq] + lam[kq] / rho;
+      sinv += 1.0 / rho;
+      Dw += rho;
+      awn += rho * (val[kw] + lam[kw] / rho);
+      athn += rho * (val[kt] + lam[kt] / rho);
+    }
+    double gsh = net->bus_gsh[b], bsh = net->bus_bsh[b];
+    double aw = Dw > 0.0 ? awn / Dw : st->bus_w[b];
+    rhsP -= gsh * aw;
+    rhsQ += bsh * aw;
+    double M11 = sinv, M22 = sinv, M12 = 0.0;
+    if (Dw > 0.0) {
+      M11 += gsh * gsh / Dw;
+      M22 += bsh * bsh / Dw;
+      M12 = -gsh * bsh / Dw;
+    }
+    double det = M11 * M22 - M12 * M12;
+    double mu1 = 0.0, mu2 = 0.0;
+    if (det != 0.0) {
+      mu1 = (M22 * rhsP - M12 * rhsQ) / det;
+      mu2 = (M11 * rhsQ - M12 * rhsP) / det;
+    }
+    for (int t = gp[b]; t < gp[b + 1]; t++) {
+      int g = gl[t];
+      st->gen_tilde[2 * g] = st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho - mu1 / rho;
+      st->gen_tilde[2 * g + 1] =
+          st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho - mu2 / rho;
+    }
+    for (int t = ep[b]; t < ep[b + 1]; t++) {
+      int e = el[t], k = e / 2, side = e % 2;
+      const double* val = st->br_val + 8 * (size_t)k;
+      const double* lam = st->br_lam + 8 * (size_t)k;
+      int kp = side ? 2 : 0, kq = kp + 1;
+      st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho + mu1 / rho;
+      st->br_tilde[4 * (size_t)k + kq] = val[kq] + lam[kq] / rho + mu2 / rho;
+    }
+    if (Dw > 0.0) {
+      st->bus_w[b] = aw - (-gsh * mu1 + bsh * mu2) / Dw;
+      st->bus_th[b] = athn / Dw;
+    }
+  }
+  /* multipliers lambda += rho (x - xt); primal ||x - xt||, dual rho ||xt - xt_prev|| */
+  double pr2 = 0.0, du2 = 0.0;
+  for (int g = 0; g < ng; g++) {
+    for (int a = 0; a < 2; a++) {
+      double xv = st->gen_pq[2 * g + a], xt = st->gen_tilde[2 * g + a];
+      st->gen_lam[2 * g + a] += rho * (xv - xt);
+      pr2 += (xv - xt) * (xv - xt);
+      double dd = xt - tprev[2 * g + a];
+      du2 += dd * dd;
+    }
+  }
+  for (int k = 0; k < nl; k++) {
+    for (int a = 0; a < 8; a++) {
+      double xv = st->br_val[8 * (size_t)k + a], xt = pair_tilde(net, st, k, a);
+      st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);
+      pr2 += (xv - xt) * (xv - xt);
+      double dd = xt - tprev[2 * ng + 8 * k + a];
+      du2 += dd * dd;
+    }
+  }
+  *pr2_out = pr2;
+  *du2_out = du2;
+}
+
+void ot_admm_run(const ot_net* net, ot_state* st, const ot_opts* o, int niters, int nthreads,
+                 double* hist_primal, double* hist_dual, int64_t* status_counts,
+                 ot_counters* total) {
+  admm_ws w;
+  admm_ws_init(net, &w);
   for (int it = 0; it < niters; it++) {
-    /* generator update: closed-form minimiser of the box-clipped scalar quadratics */
+    admm_gen_update(net, st, 1);
+    double pr2, du2;
+    admm_after_gens(net, st, o, nthreads, &w, status_counts, total, &pr2, &du2);
+    if (hist_primal) hist_primal[it] = sqrt(pr2);
+    if (hist_dual) hist_dual[it] = net->rho * sqrt(du2);
+  }
+  admm_ws_free(&w);
+}
+
+/* ------------------------------------------------- multi-period ADMM (Sec. 7, readings)
+ * The generator component spans the periods: its T active-power outputs are one NLP
+ * (OT_OBJ_GENRAMP) with the ramp penalty, solved by the same TRON; everything else is
+ * the single-period iteration, period by period. */
+void ot_genramp_record(const ot_mp* mp, int g, double* rec) {
+  int T = mp->T;
+  const ot_net* n0 = &mp->nets[0];
+  rec[0] = n0->gen_c2[g];
+  rec[1] = n0->gen_c1[g];
+  rec[2] = n0->rho;
+  rec[3] = mp->rho_ramp;
+  rec[4] = mp->ramp[g];
+  rec[5] = 0.0;
+  rec[6] = 0.0;
+  rec[7] = 0.0;
+  for (int t = 0; t < T; t++) {
+    rec[8 + t] = mp->states[t].gen_lam[2 * g];
+    rec[8 + T + t] = mp->states[t].gen_tilde[2 * g];
+  }
+}
+
+void ot_admm_mp_init(ot_mp* mp) {
+  for (int t = 0; t < mp->T; t++) ot_admm_init(&mp->nets[t], &mp->states[t]);
+  for (int g = 0; g < mp->nets[0].ngen; g++) mp->gen_delta[g] = 1.0;
+}
+
+void ot_admm_mp_run(ot_mp* mp, const ot_opts* o, int niters, int nthreads,
+                    double* hist_primal, double* hist_dual, ot_counters* total) {
+  int T = mp->T, ng = mp->nets[0].ngen;
+  const ot_net* n0 = &mp->nets[0];
+  admm_ws w;
+  admm_ws_init(n0, &w);  /* the periods share the topology */
+  int rs = 8 + 2 * T;
+  int32_t* nT = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ng + 1));
+  int64_t* poff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ng + 1));
+  int64_t* voff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ng + 1));
+  double* recs = (double*)malloc(sizeof(double) * (size_t)rs * (size_t)(ng + 1));
+  double* gl = (double*)malloc(sizeof(double) * (size_t)T * (size_t)(ng + 1));
+  double* gu = (double*)malloc(sizeof(double) * (size_t)T * (size_t)(ng + 1));
+  double* gx = (double*)malloc(sizeof(double) * (size_t)T * (size_t)(ng + 1));
+  double* gf = (double*)malloc(sizeof(double) * (size_t)(ng + 1));
+  double* gpg = (double*)malloc(sizeof(double) * (size_t)(ng + 1));
+  int32_t* git = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ng + 1));
+  int32_t* gst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ng + 1));
+  for (int g = 0; g < ng; g++) {
+    nT[g] = T;
+    poff[g] = (int64_t)rs * g;
+    voff[g] = (int64_t)T * g;
+    for (int t = 0; t < T; t++) {
+      gl[(size_t)T * g + t] = n0->gen_pmin[g];
+      gu[(size_t)T * g + t] = n0->gen_pmax[g];
+    }
+  }
+  for (int it = 0; it < niters; it++) {
+    /* generator update: the T periods' p jointly (warm started), q per period */
     for (int g = 0; g < ng; g++) {
-      double pt = st->gen_tilde[2 * g], qt = st->gen_tilde[2 * g + 1];
-      double lp = st->gen_lam[2 * g], lq = st->gen_lam[2 * g + 1];
-      double p = (rho * pt - lp - net->gen_c1[g]) / (2.0 * net->gen_c2[g] + rho);
-      double q = qt - lq / rho;
-      st->gen_pq[2 * g] = proj1(p, net->gen_pmin[g], net->gen_pmax[g]);
-      st->gen_pq[2 * g + 1] = proj1(q, net->gen_qmin[g], net->gen_qmax[g]);
+      ot_genramp_record(mp, g, recs + (size_t)rs * g);
+      for (int t = 0; t < T; t++) gx[(size_t)T * g + t] = mp->states[t].gen_pq[2 * g];
     }
-    /* branch update: TRON on eq. exp-branch, warm started from the previous x, delta */
-    for (int k = 0; k < nl; k++) ot_admm_branch_record(net, st, k, recs + 36 * (size_t)k);
-    ot_tron_batch(OT_OBJ_BRANCH, nl, n4, poff, voff, recs, bl, bu, st->br_x, st->br_delta, o,
-                  bf, bpg, bit, bst, nthreads, total);
-    if (status_counts)
-      for (int k = 0; k < nl; k++)
-        if (bst[k] >= 0 && bst[k] < 6) status_counts[bst[k]]++;
-    for (int k = 0; k < nl; k++)
-      branch_values_at(net->br_coef + 8 * (size_t)k, st->br_x + 4 * (size_t)k,
-                       st->br_val + 8 * (size_t)k);
-    /* remember the bus-side copies for the dual residual */
-    for (int g = 0; g < ng; g++) {
-      tprev[2 * g] = st->gen_tilde[2 * g];
-      tprev[2 * g + 1] = st->gen_tilde[2 * g + 1];
+    ot_tron_batch(OT_OBJ_GENRAMP, ng, nT, poff, voff, recs, gl, gu, gx, mp->gen_delta, o, gf,
+                  gpg, git, gst, nthreads, total);
+    for (int t = 0; t < T; t++) {
+      for (int g = 0; g < ng; g++) mp->states[t].gen_pq[2 * g] = gx[(size_t)T * g + t];
+      admm_gen_update(&mp->nets[t], &mp->states[t], 0);
     }
-    for (int k = 0; k < nl; k++)
-      for (int a = 0; a < 8; a++) tprev[2 * ng + 8 * k + a] = pair_tilde(net, st, k, a);
-    /* bus update: minimise sum rho/2 (xt - a)^2 with a = x + lambda/rho subject to the
-     * bus balance equations (eqs. PowerBalanceReal/Reactive); x = a - D^-1 A' mu with
-     * (A D^-1 A') mu = A a - (p_d, q_d) */
-    for (int b = 0; b < nb; b++) {
-      double rhsP = -net->bus_pd[b], rhsQ = -net->bus_qd[b];
-      double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
-      for (int t = gp[b]; t < gp[b + 1]; t++) {
-        int g = gl[t];
-        rhsP += st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho;
-        rhsQ += st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho;
-        sinv += 1.0 / rho;
-      }
-      for (int t = ep[b]; t < ep[b + 1]; t++) {
-        int e = el[t], k = e / 2, side = e % 2;
-        const double* val = st->br_val + 8 * (size_t)k;
-        const double* lam = st->br_lam + 8 * (size_t)k;
-        int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
-        rhsP -= val[kp] + lam[kp] / rho;
-        rhsQ -= val[kq] + lam[kq] / rho;
-        sinv += 1.0 / rho;
-        Dw += rho;
-        awn += rho * (val[kw] + lam[kw] / rho);
-        athn += rho * (val[kt] + lam[kt] / rho);
-      }
-      double gsh = net->bus_gsh[b], bsh = net->bus_bsh[b];
-      double aw = Dw > 0.0 ? awn / Dw : st->bus_w[b];
-      rhsP -= gsh * aw;
-      rhsQ += bsh * aw;
-      double M11 = sinv, M22 = sinv, M12 = 0.0;
-      if (Dw > 0.0) {
-        M11 += gsh * gsh / Dw;
-        M22 += bsh * bsh / Dw;
-        M12 = -gsh * bsh / Dw;
-      }
-      double det = M11 * M22 - M12 * M12;
-      double mu1 = 0.0, mu2 = 0.0;
-      if (det != 0.0) {
-        mu1 = (M22 * rhsP - M12 * rhsQ) / det;
-        mu2 = (M11 * rhsQ - M12 * rhsP) / det;
-      }
-      for (int t = gp[b]; t < gp[b + 1]; t++) {
-        int g = gl[t];
-        st->gen_tilde[2 * g] = st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho - mu1 / rho;
-        st->gen_tilde[2 * g + 1] =
-            st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho - mu2 / rho;
-      }
-      for (int t = ep[b]; t < ep[b + 1]; t++) {
-        int e = el[t], k = e / 2, side = e % 2;
-        const double* val = st->br_val + 8 * (size_t)k;
-        const double* lam = st->br_lam + 8 * (size_t)k;
-        int kp = side ? 2 : 0, kq = kp + 1;
-        st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho + mu1 / rho;
-        st->br_tilde[4 * (size_t)k + kq] = val[kq] + lam[kq] / rho + mu2 / rho;
-      }
-      if (Dw > 0.0) {
-        st->bus_w[b] = aw - (-gsh * mu1 + bsh * mu2) / Dw;
-        st->bus_th[b] = athn / Dw;
-      }
-    }
-    /* multipliers lambda += rho (x - xt); primal ||x - xt||, dual rho ||xt - xt_prev|| */
+    /* branches and buses, period by period */
     double pr2 = 0.0, du2 = 0.0;
-    for (int g = 0; g < ng; g++) {
-      for (int a = 0; a < 2; a++) {
-        double xv = st->gen_pq[2 * g + a], xt = st->gen_tilde[2 * g + a];
-        st->gen_lam[2 * g + a] += rho * (xv - xt);
-        pr2 += (xv - xt) * (xv - xt);
-        double dd = xt - tprev[2 * g + a];
-        du2 += dd * dd;
-      }
-    }
-    for (int k = 0; k < nl; k++) {
-      for (int a = 0; a < 8; a++) {
-        double xv = st->br_val[8 * (size_t)k + a], xt = pair_tilde(net, st, k, a);
-        st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);
-        pr2 += (xv - xt) * (xv - xt);
-        double dd = xt - tprev[2 * ng + 8 * k + a];
-        du2 += dd * dd;
-      }
+    for (int t = 0; t < T; t++) {
+      double p2, d2;
+      admm_after_gens(&mp->nets[t], &mp->states[t], o, nthreads, &w, NULL, total, &p2, &d2);
+      pr2 += p2;
+      du2 += d2;
     }
     if (hist_primal) hist_primal[it] = sqrt(pr2);
-    if (hist_dual) hist_dual[it] = rho * sqrt(du2);
+    if (hist_dual) hist_dual[it] = n0->rho * sqrt(du2);
   }
-  free(ep);
-  free(gp);
-  free(el);
-  free(gl);
-  free(n4);
+  admm_ws_free(&w);
+  free(nT);
   free(poff);
   free(voff);
   free(recs);
-  free(bl);
-  free(bu);
-  free(bf);
-  free(bpg);
-  free(bit);
-  free(bst);
-  free(tprev);
+  free(gl);
+  free(gu);
+  free(gx);
+  free(gf);
+  free(gpg);
+  free(git);
+  free(gst);
 }

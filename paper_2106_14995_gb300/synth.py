@@ -207,6 +207,39 @@ def network(nbus: int = 10000, nchord: int = 3000, ngen: int = 3000, seed_index:
         bus_pd=pd, bus_qd=qd, bus_gsh=np.zeros(nbus), bus_bsh=np.zeros(nbus))
 
 
+def load_profile(T: int = 24, swing: float = 0.2) -> np.ndarray:
+    """Per-period load scale of a synthetic day: 1 + swing sin(2 pi (t - 6) / 24), so the
+    load rises through the morning, peaks at hour 12 and falls through the evening."""
+    t = np.arange(T, dtype=np.float64)
+    return 1.0 + swing * np.sin(2.0 * math.pi * (t - 6.0) / 24.0)
+
+
+def genramp_batch(B: int = 3000, T: int = 24, seed_index: int = 8, rho: float = 400.0,
+                  rho_ramp: float = 1.0e4) -> dict:
+    """Multi-period generator problems (record [c2 c1 rho rho_r R 0 0 0 | lambda | target]):
+    c2 ~ U[0.001, 0.05], c1 ~ U[5, 40], p in [0, p_max] with p_max ~ U[0.5, 1.5], ramp
+    R ~ U[0.02, 0.2] p_max, multipliers ~ N(0, 20^2), targets ~ U[0, p_max] per period
+    (so that ramps bind), x0 = the targets."""
+    rng = rng_for(seed_index)
+    c2 = rng.uniform(0.001, 0.05, B)
+    c1 = rng.uniform(5.0, 40.0, B)
+    pmax = rng.uniform(0.5, 1.5, B)
+    ramp = rng.uniform(0.02, 0.2, B) * pmax
+    lam = rng.normal(0.0, 20.0, (B, T))
+    tgt = rng.uniform(0.0, 1.0, (B, T)) * pmax[:, None]
+    rec = np.zeros((B, 8 + 2 * T))
+    rec[:, 0] = c2
+    rec[:, 1] = c1
+    rec[:, 2] = rho
+    rec[:, 3] = rho_ramp
+    rec[:, 4] = ramp
+    rec[:, 8:8 + T] = lam
+    rec[:, 8 + T:] = tgt
+    lo = np.zeros((B, T))
+    hi = np.repeat(pmax[:, None], T, axis=1)
+    return dict(kind=4, n=T, params=rec, l=lo, u=hi, x0=tgt.copy(), delta0=np.ones(B))
+
+
 def serving_stream(duration_s: float = 60.0, rate_hz: float = 200.0, seed_index: int = 4,
                    bus_lo: int = 500, bus_hi: int = 20000):
     """Poisson arrivals of independent ADMM instances: arrival times, bus counts

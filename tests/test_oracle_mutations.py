@@ -65,6 +65,19 @@ MUTATIONS = [
      "st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);",
      "st->br_lam[8 * (size_t)k + a] -= rho * (xv - xt);",
      [pins.test_admm_bus_update_kkt_and_multipliers]),
+    ("generator chain: sign of the ramp gradient",
+     "g[t] += rr * e * s;", "g[t] -= rr * e * s;",
+     [pins.test_genramp_gradient_hessian_finite_differences]),
+    ("generator chain: sign of the Hessian's subdiagonal",
+     "H[t * n + (t - 1)] -= rr;", "H[t * n + (t - 1)] += rr;",
+     [pins.test_genramp_gradient_hessian_finite_differences]),
+    ("generator chain: ramp term dropped from f",
+     "val += 0.5 * rr * e * e;", "val += 0.0 * rr * e * e;",
+     [pins.test_genramp_binding_ramps_vs_lbfgsb]),
+    ("multi-period record: targets from the multipliers",
+     "rec[8 + T + t] = mp->states[t].gen_tilde[2 * g];",
+     "rec[8 + T + t] = mp->states[t].gen_lam[2 * g];",
+     [pins.test_multiperiod_admm_without_binding_ramps_equals_single_period_runs]),
 ]
 
 

@@ -610,3 +610,125 @@ def test_admm_two_bus_by_hand():
     assert abs(st["br_tilde"][0, 2] + net["bus_pd"][1]) < 1e-12
     assert abs(st["br_tilde"][0, 3] + net["bus_qd"][1]) < 1e-12
     assert abs(st["gen_tilde"][0, 0] - st["br_tilde"][0, 0] - net["bus_pd"][0]) < 1e-12
+
+
+# ------------------------------------------------ multi-period generator and ADMM
+
+def _genramp_points(rng, rec, T, k):
+    """points away from the ramp kinks (| |p_t - p_{t-1}| - R | > 1e-3)"""
+    out = []
+    R = rec[4]
+    while len(out) < k:
+        x = rng.uniform(0.0, 1.2, T)
+        d = np.abs(np.diff(x))
+        if np.all(np.abs(d - R) > 1e-3) and np.any(d > R):
+            out.append(x)
+    return out
+
+
+def test_genramp_gradient_hessian_finite_differences():
+    d = synth.genramp_batch(8, 7, seed_index=30)
+    rng = np.random.default_rng(30)
+    for p in range(8):
+        rec = d["params"][p]
+        for x in _genramp_points(rng, rec, 7, 3):
+            f, g, H = oracle.eval_obj(oracle.OBJ_GENRAMP, rec, x)
+            h = 1e-6
+            gfd = np.zeros(7)
+            Hfd = np.zeros((7, 7))
+            for i in range(7):
+                e = np.zeros(7)
+                e[i] = h
+                fp, gp, _ = oracle.eval_obj(oracle.OBJ_GENRAMP, rec, x + e)
+                fm, gm, _ = oracle.eval_obj(oracle.OBJ_GENRAMP, rec, x - e)
+                gfd[i] = (fp - fm) / (2 * h)
+                Hfd[:, i] = (gp - gm) / (2 * h)
+            scale = max(1.0, np.abs(g).max())
+            assert np.abs(g - gfd).max() < 1e-6 * scale
+            hs = max(1.0, np.abs(H).max())
+            assert np.abs(H - Hfd).max() < 1e-5 * hs
+            # tridiagonal
+            assert np.all(np.triu(H, 2) == 0.0) and np.all(np.tril(H, -2) == 0.0)
+
+
+def test_genramp_without_binding_ramps_is_the_per_period_closed_form():
+    # R beyond any possible step: the periods separate and each is the box-clipped
+    # minimiser of c2 p^2 + c1 p + lambda (p - t) + rho/2 (p - t)^2
+    d = synth.genramp_batch(20, 12, seed_index=31)
+    for p in range(20):
+        rec = d["params"][p].copy()
+        rec[4] = 1e6
+        c2, c1, rho = rec[0], rec[1], rec[2]
+        lam, tgt = rec[8:20], rec[20:32]
+        closed = np.clip((rho * tgt - lam - c1) / (2 * c2 + rho), d["l"][p], d["u"][p])
+        r = _solve(oracle.OBJ_GENRAMP, rec, d["l"][p], d["u"][p], d["x0"][p])
+        assert r["status"] == oracle.CONVERGED
+        np.testing.assert_allclose(r["x"], closed, rtol=0, atol=1e-9)
+
+
+def test_genramp_binding_ramps_vs_lbfgsb():
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    T = 9
+    d = synth.genramp_batch(16, T, seed_index=32)
+    for p in range(16):
+        rec = d["params"][p]
+        c2, c1, rho, rr, R = rec[:5]
+        lam, tgt = rec[8:8 + T], rec[8 + T:]
+
+        def fg(x):
+            r = x - tgt
+            f = np.sum(c2 * x * x + c1 * x + lam * r + 0.5 * rho * r * r)
+            g = 2 * c2 * x + c1 + lam + rho * r
+            dd = np.diff(x)
+            e = np.maximum(np.abs(dd) - R, 0.0)
+            f += 0.5 * rr * np.sum(e * e)
+            w = rr * e * np.sign(dd)
+            g[1:] += w
+            g[:-1] -= w
+            return f, g
+
+        res = scipy_opt.minimize(fg, d["x0"][p], jac=True, method="L-BFGS-B",
+                                 bounds=list(zip(d["l"][p], d["u"][p])),
+                                 options=dict(gtol=1e-13, ftol=1e-16, maxiter=20000))
+        r = _solve(oracle.OBJ_GENRAMP, rec, d["l"][p], d["u"][p], d["x0"][p])
+        assert r["status"] == oracle.CONVERGED
+        np.testing.assert_allclose(r["x"], res.x, rtol=0, atol=1e-6)
+        assert abs(r["f"] - res.fun) <= 1e-8 * max(1.0, abs(res.fun))
+
+
+def test_multiperiod_admm_without_binding_ramps_equals_single_period_runs():
+    net = _small_net(30, seed=33)
+    scale = [0.85, 1.0, 1.15]
+    mp = oracle.MultiPeriodAdmm(net, scale, ramp=1e6)
+    hp, hd = mp.run(12)
+    pr2 = np.zeros(12)
+    du2 = np.zeros(12)
+    for t, s in enumerate(scale):
+        nt = dict(net, bus_pd=net["bus_pd"] * s, bus_qd=net["bus_qd"] * s)
+        a = oracle.Admm(nt)
+        p1, d1 = a.run(12)
+        pr2 += p1 ** 2
+        du2 += d1 ** 2
+        for k in ("gen_pq", "gen_lam", "bus_w", "bus_th", "br_x", "br_lam"):
+            np.testing.assert_allclose(mp.state(t)[k], a.arrays[k], rtol=1e-9, atol=1e-9,
+                                       err_msg=k)
+    np.testing.assert_allclose(hp, np.sqrt(pr2), rtol=1e-9)
+    np.testing.assert_allclose(hd, np.sqrt(du2), rtol=1e-9)
+
+
+def test_multiperiod_admm_generator_step_satisfies_chain_kkt():
+    # after an iteration, the chain problem built from the state before it is solved:
+    # the projected gradient of its objective at the new p is below gtol
+    net = _small_net(30, seed=34)
+    mp = oracle.MultiPeriodAdmm(net, synth.load_profile(6), ramp=0.01, rho_ramp=1e4)
+    mp.run(3)
+    recs = [mp.genramp_record(g) for g in range(len(net["gen_bus"]))]
+    p_before = np.array([mp.state(t)["gen_pq"][:, 0] for t in range(6)]).T.copy()
+    mp.run(1)
+    p_after = np.array([mp.state(t)["gen_pq"][:, 0] for t in range(6)]).T
+    assert np.abs(p_after - p_before).max() > 0
+    for g, rec in enumerate(recs):
+        f, gr, _ = oracle.eval_obj(oracle.OBJ_GENRAMP, rec, p_after[g])
+        lo = np.full(6, net["gen_pmin"][g])
+        hi = np.full(6, net["gen_pmax"][g])
+        assert oracle.pgnorm(p_after[g], gr, lo, hi) <= 1e-6
