@@ -72,9 +72,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ADMM, uneven-size and serving workloads")
-    ap.add_argument("--extras", default="admm,uneven,serving",
+    ap.add_argument("--extras", default="admm,uneven,serving,multiperiod",
                     help="comma-separated subset of admm, uneven, serving")
     ap.add_argument("--admm-iters", type=int, default=1000)
+    ap.add_argument("--mp-iters", type=int, default=200)
     ap.add_argument("--serve-seconds", type=float, default=0.25)
     ap.add_argument("--serve-max-iters", type=int, default=200)
     return ap.parse_args()
@@ -278,6 +279,45 @@ def bench_uneven(args, dev):
         tb.close()
     res["workload"] = "100,000 dense problems, n in {4,6,8,16,32,64,128}"
     return res
+
+
+def bench_multiperiod(args, dev):
+    """Multi-period ADMM: 24 periods of a 2,000-bus network (2,600 branches, 600
+    generators), loads on a synthetic daily profile, generators coupled by ramp limits of
+    5 % of p_max (penalty 1e4): iterations/s over args.mp_iters iterations (five launches
+    each), with the oracle on the host cores for two iterations."""
+    import torch
+    import oracle
+    from paper_2106_14995_gb300 import synth
+    from paper_2106_14995_gb300.admm import AdmmMultiPeriod
+    net = synth.network(2000, 600, 600, seed_index=9)
+    T = 24
+    scale = synth.load_profile(T)
+    ramp = 0.05 * net["gen_pmax"]
+    g = AdmmMultiPeriod(net, scale, ramp=ramp, rho_ramp=1e4)
+    g.step(4)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    pr, du = g.step(args.mp_iters)
+    dt = time.perf_counter() - t0
+    counts = g.gen_status_counts().tolist()
+    p = np.array([g.get_state(t)["gen_pq"][:, 0] for t in range(T)])
+    g.close()
+    cores = os.cpu_count() or 1
+    o = oracle.MultiPeriodAdmm(net, scale, ramp=ramp, rho_ramp=1e4)
+    t1 = time.perf_counter()
+    o.run(2, nthreads=cores)
+    cpu = 2 / (time.perf_counter() - t1)
+    return {"value": args.mp_iters / dt, "unit": "ADMM iters/s",
+            "workload": "24 periods x (2,000 buses, 2,600 branches, 600 generators), "
+                        "ramp 5 % of p_max, rho=400, rho_ramp=1e4",
+            "iterations": args.mp_iters, "ms_per_iter": dt * 1e3 / args.mp_iters,
+            "gpu_launches": 5 * args.mp_iters, "final_primal": pr, "final_dual": du,
+            "gen_status_last_iter": counts,
+            "max_ramp_step_over_limit": float(np.max(np.abs(np.diff(p, axis=0)) -
+                                                     ramp[None, :])),
+            "cpu_baseline": {"value": cpu, "unit": "ADMM iters/s", "cores": cores,
+                             "kind": "oracle", "sample": "2 iterations from the start"}}
 
 
 def bench_serving(args, dev):
@@ -492,6 +532,8 @@ def main():
             line["uneven"] = bench_uneven(args, dev)
         if "serving" in extras:
             line["serving"] = bench_serving(args, dev)
+        if "multiperiod" in extras:
+            line["multiperiod"] = bench_multiperiod(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -143,6 +143,35 @@ tron_err_t admm_pool_set_state(admm_pool_t* p, int32_t id, const admm_state_view
 int32_t admm_pool_live(const admm_pool_t* p);
 void admm_pool_destroy(admm_pool_t* p);
 
+/* --------------------------------------- multi-period ADMM (the paper's future work)
+ * Sec. 7 names multi-period optimal power flow as the next use of the ADMM with the
+ * batched solver and gives no formulation; this is one reading of it.  T periods of one
+ * network: period t's loads are h_load_scale[t] times the network's; the periods are
+ * coupled by the generators' ramp limits |p_t - p_{t-1}| <= h_ramp[g], enforced by the
+ * penalty rho_ramp/2 max(0, |p_t - p_{t-1}| - h_ramp[g])^2 in the generator component.
+ * That component spans the periods: every iteration solves each generator's T
+ * active-power outputs as one bound-constrained NLP (TRON_OBJ_GEN_RAMP, one batched
+ * TRON launch over all generators, warm started), its reactive powers in closed form;
+ * branches and buses are the single-period components of each period (the periods
+ * live as instances of one resident pool and share its launches).  Residuals combine
+ * all periods: primal sqrt(sum_t primal_t^2), dual sqrt(sum_t dual_t^2).
+ *
+ * admm_mp_create: copies the network and allocates everything (T <= 32, loads > 0).
+ * admm_mp_step: runs n_iters iterations (five launches each); when h_primal / h_dual
+ *   are not NULL, synchronises and writes the last iteration's combined residuals.
+ * admm_mp_get_state: state of one period, as admm_get_state.
+ * admm_mp_gen_status_counts: tron_status_t counts ([6]) of the last generator solves. */
+typedef struct admm_mp admm_mp_t;
+tron_err_t admm_mp_create(admm_mp_t** out, const admm_network_t* net, int32_t T,
+                          const double* h_load_scale, const double* h_ramp, double rho_ramp,
+                          const tron_options_t* opt, void* stream);
+tron_err_t admm_mp_step(admm_mp_t* mp, int32_t n_iters, double* h_primal, double* h_dual,
+                        void* stream);
+tron_err_t admm_mp_get_state(admm_mp_t* mp, int32_t period, admm_state_view_t* host,
+                             void* stream);
+tron_err_t admm_mp_gen_status_counts(admm_mp_t* mp, int64_t* h_counts6, void* stream);
+void admm_mp_destroy(admm_mp_t* mp);
+
 #ifdef __cplusplus
 }
 #endif

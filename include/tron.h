@@ -55,11 +55,17 @@ typedef enum tron_err {
  *   Record of n*n + 2n doubles: Q (row-major, symmetric), c, d.
  * TRON_OBJ_HS45 (n <= 8): the hs45 variant of Sec. 4.2, f = 120 - prod_i x_i.
  *   No record (d_params may be NULL); bounds are the caller's.
+ * TRON_OBJ_GEN_RAMP (n <= 32): one generator of the multi-period ADMM (the paper's
+ *   future work, Sec. 7) over its n periods,
+ *     f = sum_t c2 p_t^2 + c1 p_t + lambda_t (p_t - target_t) + rho/2 (p_t - target_t)^2
+ *         + rho_r/2 sum_{t>=1} max(0, |p_t - p_{t-1}| - R)^2.
+ *   Record of 8 + 2n doubles: [c2, c1, rho, rho_r, R, 0, 0, 0], lambda[n], target[n].
  */
 typedef enum tron_obj {
   TRON_OBJ_ACOPF_BRANCH = 1,
   TRON_OBJ_DENSE_QUARTIC = 2,
-  TRON_OBJ_HS45 = 3
+  TRON_OBJ_HS45 = 3,
+  TRON_OBJ_GEN_RAMP = 4
 } tron_obj_t;
 
 /* Per-problem outcome written to d_status. */

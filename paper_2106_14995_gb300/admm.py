@@ -1,8 +1,10 @@
-"""Component ADMM on the GPU (Sec. 6.1): thin wrappers over the admm_* / admm_pool_* ABI.
+"""Component ADMM on the GPU (Sec. 6.1): thin wrappers over the admm_* / admm_pool_* /
+admm_mp_* ABI.
 
 ``Admm`` holds one network; ``AdmmPool`` holds many independent instances resident on
-the device and advances them together (continuous batching).  Networks are dicts as
-produced by ``synth.network`` (host numpy arrays); they are copied into the pool.
+the device and advances them together (continuous batching); ``AdmmMultiPeriod`` holds T
+periods of one network coupled by generator ramp limits.  Networks are dicts as produced
+by ``synth.network`` (host numpy arrays); they are copied to the device.
 """
 from __future__ import annotations
 
@@ -204,6 +206,67 @@ class AdmmPool:
     def close(self) -> None:
         if getattr(self, "_h", None):
             self._lib.admm_pool_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class AdmmMultiPeriod:
+    """T periods of one network (loads scaled by ``load_scale[t]``) coupled by generator
+    ramp limits ``ramp`` (scalar or [ngen]) through the penalty ``rho_ramp``; see
+    admm_mp_create in include/admm.h."""
+
+    def __init__(self, net: dict, load_scale, ramp, rho_ramp: float = 400.0,
+                 rho: float = 400.0, rho_line: float | None = None, vmin: float = 0.9,
+                 vmax: float = 1.1, opts: nt.TronOptions | None = None, stream=None):
+        self._lib = nt.load()
+        self._net = _NetHolder(net, rho, rho_line, vmin, vmax)
+        self.sizes = self._net.sizes
+        self.T = len(load_scale)
+        self._scale = np.ascontiguousarray(load_scale, dtype=np.float64)
+        self._ramp = np.ascontiguousarray(
+            np.broadcast_to(np.asarray(ramp, dtype=np.float64), (self.sizes["ngen"],)))
+        h = C.c_void_p()
+        nt.check(self._lib.admm_mp_create(C.byref(h), C.byref(self._net.s), int(self.T),
+                                          self._scale.ctypes.data, self._ramp.ctypes.data,
+                                          float(rho_ramp),
+                                          C.byref(opts) if opts is not None else None,
+                                          nt.stream_handle(stream)), "admm_mp_create")
+        self._h = h
+        self.stream = stream
+
+    def step(self, n_iters: int, residuals: bool = True):
+        pr = C.c_double()
+        du = C.c_double()
+        nt.check(self._lib.admm_mp_step(self._h, int(n_iters),
+                                        C.byref(pr) if residuals else None,
+                                        C.byref(du) if residuals else None,
+                                        nt.stream_handle(self.stream)), "admm_mp_step")
+        return (pr.value, du.value) if residuals else None
+
+    def get_state(self, period: int) -> dict:
+        bufs = _state_buffers(self.sizes)
+        v = _view(bufs)
+        nt.check(self._lib.admm_mp_get_state(self._h, int(period), C.byref(v),
+                                             nt.stream_handle(self.stream)),
+                 "admm_mp_get_state")
+        bufs["iteration"] = v.iteration
+        return bufs
+
+    def gen_status_counts(self) -> np.ndarray:
+        c = np.zeros(6, dtype=np.int64)
+        nt.check(self._lib.admm_mp_gen_status_counts(self._h, c.ctypes.data,
+                                                     nt.stream_handle(self.stream)),
+                 "admm_mp_gen_status_counts")
+        return c
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.admm_mp_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -76,6 +76,7 @@ struct PoolDev {
   // instances
   double* inst_param;  // [cap_inst][4] rho, rho_line, vmin, vmax
   int32_t* inst_active;
+  int32_t* inst_flags; // bit 0: the generators are updated outside the pool's launches
   int32_t* inst_blk;   // [cap_inst][2] bus-block range
   int64_t* inst_iter;
   double* hist;        // [cap_inst][H][2] primal, dual
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
     const int g = ((int)blockIdx.x - a.nbb) * (int)blockDim.x + (int)threadIdx.x;
     if (g >= d.cap_gen) return;
     const int inst = d.gen_inst[g];
-    if (inst < 0 || !d.inst_active[inst]) return;
+    if (inst < 0 || !d.inst_active[inst] || (d.inst_flags[inst] & 1)) return;
     const double rho = d.inst_param[4 * inst];
     const double pt = d.gen_tilde[2 * g], qt = d.gen_tilde[2 * g + 1];
     const double lp = d.gen_lam[2 * g], lq = d.gen_lam[2 * g + 1];
@@ -415,6 +416,35 @@ __global__ void k_admm_latest(const PoolDev d) {
   d.lat_res[2 * i + 1] = d.hist[slot + 1];
 }
 
+// ---- multi-period ADMM: the generator component spanning the periods.  Period t of
+// generator g sits in pool slot g0[t] + g.  Gather: the chain records (multipliers and
+// bus-side copies of p over the periods) and the warm start; reactive power per period
+// in closed form (minimiser of lq (q - qt) + rho/2 (q - qt)^2 on [qmin, qmax]).
+__global__ void k_mp_gather(const PoolDev d, const int32_t* __restrict__ g0, int T, int ngen,
+                            double* __restrict__ rec, double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ngen * T) return;
+  const int g = i / T, t = i - g * T;
+  const int s = g0[t] + g;
+  const size_t rs = 8 + 2 * (size_t)T;
+  rec[(size_t)g * rs + 8 + t] = d.gen_lam[2 * s];
+  rec[(size_t)g * rs + 8 + T + t] = d.gen_tilde[2 * s];
+  x[i] = d.gen_pq[2 * s];
+  const double rho = d.inst_param[4 * d.gen_inst[s]];
+  double q = d.gen_tilde[2 * s + 1] - d.gen_lam[2 * s + 1] / rho;
+  q = q < d.gen_qmin[s] ? d.gen_qmin[s] : (q > d.gen_qmax[s] ? d.gen_qmax[s] : q);
+  d.gen_pq[2 * s + 1] = q;
+}
+
+// the solved active powers back into the periods' generator slots
+__global__ void k_mp_scatter(const PoolDev d, const int32_t* __restrict__ g0, int T, int ngen,
+                             const double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ngen * T) return;
+  const int g = i / T, t = i - g * T;
+  d.gen_pq[2 * (g0[t] + g)] = x[i];
+}
+
 // first-fit allocator of aligned slot ranges
 struct RangeAlloc {
   std::vector<std::pair<int, int>> free_;  // sorted, disjoint [start, end)
@@ -605,6 +635,7 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
   PA(gen_list, cg);
   PA(inst_param, 4 * (size_t)cap_instances);
   PA(inst_active, cap_instances);
+  PA(inst_flags, cap_instances);
   PA(inst_blk, 2 * (size_t)cap_instances);
   PA(inst_iter, cap_instances);
   PA(hist, 2 * (size_t)cap_instances * history_len);
@@ -626,6 +657,7 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
       cudaMemsetAsync(p->d.bus_eoff, 0, sizeof(int32_t) * cb, st) ||
       cudaMemsetAsync(p->d.bus_goff, 0, sizeof(int32_t) * cb, st) ||
       cudaMemsetAsync(p->d.inst_active, 0, sizeof(int32_t) * cap_instances, st) ||
+      cudaMemsetAsync(p->d.inst_flags, 0, sizeof(int32_t) * cap_instances, st) ||
       cudaMemsetAsync(p->d.inst_blk, 0, sizeof(int32_t) * 2 * cap_instances, st) ||
       cudaMemsetAsync(p->d.inst_iter, 0, sizeof(int64_t) * cap_instances, st) ||
       cudaMemsetAsync(p->d.inst_param, 0, sizeof(double) * 4 * cap_instances, st) ||
@@ -786,6 +818,8 @@ tron_err_t admm_pool_add(admm_pool_t* p, const admm_network_t* net, int32_t* id,
   ok = ok && up(p->d.inst_param + 4 * (size_t)slot, param, sizeof(param));
   ok = ok && up(p->d.inst_blk + 2 * (size_t)slot, blk, sizeof(blk));
   ok = ok && up(p->d.inst_iter + slot, &zero64, sizeof(zero64));
+  const int32_t zero32 = 0;
+  ok = ok && up(p->d.inst_flags + slot, &zero32, sizeof(zero32));
   if (ok) {
     AdmmArgs a = make_args(p);
     const int m = std::max(anl, std::max(ang, anb));
@@ -979,6 +1013,205 @@ tron_err_t admm_get_state(admm_t* a, admm_state_view_t* host, void* stream) {
 
 tron_err_t admm_set_state(admm_t* a, const admm_state_view_t* host, void* stream) {
   return admm_pool_set_state(a, 0, host, stream);
+}
+
+// ---------------------------------------------------------------- multi-period
+}  // extern "C"
+
+struct admm_mp {
+  admm_pool* pool;
+  int T, ngen;
+  std::vector<int32_t> inst;   // pool instance of each period
+  int32_t* d_g0;               // [T] first generator slot of each period
+  tron_batch_t* tb;            // the generator chains: ngen problems of T periods
+  double *d_rec, *d_lo, *d_hi, *d_x, *d_delta, *d_f, *d_pg;
+  int32_t *d_iters, *d_status;
+  std::vector<void*> allocs;
+};
+
+extern "C" {
+
+void admm_mp_destroy(admm_mp_t* mp) {
+  if (!mp) return;
+  if (mp->tb) tron_batch_destroy(mp->tb);
+  if (mp->pool) admm_pool_destroy(mp->pool);
+  for (void* a : mp->allocs) cudaFree(a);
+  delete mp;
+}
+
+tron_err_t admm_mp_create(admm_mp_t** out, const admm_network_t* net, int32_t T,
+                          const double* h_load_scale, const double* h_ramp, double rho_ramp,
+                          const tron_options_t* opt, void* stream) {
+  clear_error();
+  XT_REQUIRE(out && net && h_load_scale && h_ramp, TRON_EINVAL, "admm_mp_create: null argument");
+  *out = nullptr;
+  XT_REQUIRE(T >= 1 && T <= 32, TRON_EINVAL, "admm_mp_create: T = %d not in [1, 32]", (int)T);
+  XT_REQUIRE(rho_ramp >= 0.0, TRON_EINVAL, "admm_mp_create: rho_ramp < 0");
+  for (int t = 0; t < T; ++t)
+    XT_REQUIRE(h_load_scale[t] > 0.0 && isfinite(h_load_scale[t]), TRON_EINVAL,
+               "admm_mp_create: load scale %d must be positive", t);
+  const int ng = net->ngen;
+  for (int g = 0; g < ng; ++g)
+    XT_REQUIRE(h_ramp[g] >= 0.0, TRON_EINVAL, "admm_mp_create: ramp of generator %d < 0", g);
+  cudaStream_t st = (cudaStream_t)stream;
+  admm_mp* mp = new admm_mp();
+  mp->pool = nullptr;
+  mp->tb = nullptr;
+  mp->T = T;
+  mp->ngen = ng;
+  auto fail = [&](tron_err_t e) {
+    admm_mp_destroy(mp);
+    return e;
+  };
+  tron_err_t e = admm_pool_create(&mp->pool, T * align_up(net->nbus), T * align_up(net->nbranch),
+                                  T * align_up(ng), T, 1 << 12, opt, stream);
+  if (e != TRON_OK) return fail(e);
+  std::vector<double> pd(net->nbus), qd(net->nbus);
+  std::vector<int32_t> g0(T);
+  for (int t = 0; t < T; ++t) {
+    for (int b = 0; b < net->nbus; ++b) {
+      pd[b] = net->bus_pd[b] * h_load_scale[t];
+      qd[b] = net->bus_qd[b] * h_load_scale[t];
+    }
+    admm_network_t nt = *net;
+    nt.bus_pd = pd.data();
+    nt.bus_qd = qd.data();
+    int32_t id = -1;
+    e = admm_pool_add(mp->pool, &nt, &id, stream);
+    if (e != TRON_OK) return fail(e);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {  // pd, qd are reused
+      set_error("admm_mp_create: synchronisation failed");
+      return fail(TRON_ECUDA);
+    }
+    mp->inst.push_back(id);
+    g0[t] = mp->pool->inst[id].g0;
+    const int32_t flag = 1;  // this period's generators are the chains' business
+    if (cudaMemcpy(mp->pool->d.inst_flags + id, &flag, sizeof(flag), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      set_error("admm_mp_create: upload failed");
+      return fail(TRON_ECUDA);
+    }
+  }
+  // the chains' arrays: records with their constant header, bounds, warm radius 1
+  const size_t rs = 8 + 2 * (size_t)T, ngs = (size_t)std::max(ng, 1);
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) return false;
+    mp->allocs.push_back(*ptr);
+    return true;
+  };
+  if (!alloc((void**)&mp->d_g0, 4 * (size_t)T) || !alloc((void**)&mp->d_rec, 8 * rs * ngs) ||
+      !alloc((void**)&mp->d_lo, 8 * (size_t)T * ngs) || !alloc((void**)&mp->d_hi, 8 * (size_t)T * ngs) ||
+      !alloc((void**)&mp->d_x, 8 * (size_t)T * ngs) || !alloc((void**)&mp->d_delta, 8 * ngs) ||
+      !alloc((void**)&mp->d_f, 8 * ngs) || !alloc((void**)&mp->d_pg, 8 * ngs) ||
+      !alloc((void**)&mp->d_iters, 4 * ngs) || !alloc((void**)&mp->d_status, 4 * ngs)) {
+    set_error("admm_mp_create: cudaMalloc failed");
+    return fail(TRON_ENOMEM);
+  }
+  std::vector<double> rec(rs * ngs, 0.0), lo((size_t)T * ngs), hi((size_t)T * ngs), dl(ngs, 1.0);
+  for (int g = 0; g < ng; ++g) {
+    double* r = rec.data() + rs * g;
+    r[0] = net->gen_c2[g];
+    r[1] = net->gen_c1[g];
+    r[2] = net->rho;
+    r[3] = rho_ramp;
+    r[4] = h_ramp[g];
+    for (int t = 0; t < T; ++t) {
+      lo[(size_t)T * g + t] = net->gen_pmin[g];
+      hi[(size_t)T * g + t] = net->gen_pmax[g];
+    }
+  }
+  std::vector<int32_t> status0(ngs, 0);
+  if (cudaMemcpy(mp->d_g0, g0.data(), 4 * (size_t)T, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(mp->d_rec, rec.data(), 8 * rs * ngs, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(mp->d_lo, lo.data(), 8 * (size_t)T * ngs, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(mp->d_hi, hi.data(), 8 * (size_t)T * ngs, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(mp->d_delta, dl.data(), 8 * ngs, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(mp->d_status, status0.data(), 4 * ngs, cudaMemcpyHostToDevice)) {
+    set_error("admm_mp_create: upload failed");
+    return fail(TRON_ECUDA);
+  }
+  tron_options_t o;
+  if (opt) o = *opt;
+  else tron_options_default(&o);
+  o.group = 0;
+  o.layout = 0;
+  o.schedule = TRON_SCHED_PERSISTENT;
+  if (ng > 0) {
+    e = tron_batch_create(&mp->tb, TRON_OBJ_GEN_RAMP, ng, nullptr, T, &o, stream);
+    if (e != TRON_OK) return fail(e);
+  }
+  *out = mp;
+  return TRON_OK;
+}
+
+tron_err_t admm_mp_step(admm_mp_t* mp, int32_t n_iters, double* h_primal, double* h_dual,
+                        void* stream) {
+  clear_error();
+  XT_REQUIRE(mp && n_iters >= 0, TRON_EINVAL, "admm_mp_step: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  admm_pool* p = mp->pool;
+  AdmmArgs a = make_args(p);
+  void* args[] = {&a};
+  const size_t smem = (size_t)p->bw * BranchSolver::WARP_DOUBLES * sizeof(double);
+  const int nthr = mp->ngen * mp->T;
+  for (int it = 0; it < n_iters; ++it) {
+    // branches (the flagged periods' generators are skipped there) ...
+    XT_CUDA(cudaLaunchKernel((const void*)k_admm_branch_gen, dim3(p->nbb + p->ngb),
+                             dim3(p->bw * 32), args, smem, st));
+    // ... generators over all periods ...
+    if (nthr > 0) {
+      k_mp_gather<<<(nthr + 127) / 128, 128, 0, st>>>(p->d, mp->d_g0, mp->T, mp->ngen,
+                                                      mp->d_rec, mp->d_x);
+      XT_CUDA(cudaGetLastError());
+      tron_err_t e = tron_batch_solve(mp->tb, mp->d_rec, mp->d_lo, mp->d_hi, mp->d_x,
+                                      mp->d_delta, mp->d_f, mp->d_pg, mp->d_iters,
+                                      mp->d_status, stream);
+      if (e != TRON_OK) return e;
+      k_mp_scatter<<<(nthr + 127) / 128, 128, 0, st>>>(p->d, mp->d_g0, mp->T, mp->ngen,
+                                                       mp->d_x);
+      XT_CUDA(cudaGetLastError());
+    }
+    // ... then the buses, multipliers and residuals of every period
+    XT_CUDA(cudaLaunchKernel((const void*)k_admm_bus, dim3(p->nbusb), dim3(kBusThreads), args,
+                             0, st));
+  }
+  if (!h_primal && !h_dual) return TRON_OK;
+  const int ci = p->d.cap_inst;
+  std::vector<int64_t> its(ci);
+  std::vector<double> pr(ci), du(ci);
+  tron_err_t e = admm_pool_residuals(p, its.data(), pr.data(), du.data(), stream);
+  if (e != TRON_OK) return e;
+  double p2 = 0.0, d2 = 0.0;
+  for (int t = 0; t < mp->T; ++t) {
+    p2 += pr[mp->inst[t]] * pr[mp->inst[t]];
+    d2 += du[mp->inst[t]] * du[mp->inst[t]];
+  }
+  if (h_primal) *h_primal = sqrt(p2);
+  if (h_dual) *h_dual = sqrt(d2);
+  return TRON_OK;
+}
+
+tron_err_t admm_mp_get_state(admm_mp_t* mp, int32_t period, admm_state_view_t* host,
+                             void* stream) {
+  clear_error();
+  XT_REQUIRE(mp && period >= 0 && period < mp->T, TRON_EINVAL,
+             "admm_mp_get_state: bad period");
+  return admm_pool_get_state(mp->pool, mp->inst[period], host, stream);
+}
+
+tron_err_t admm_mp_gen_status_counts(admm_mp_t* mp, int64_t* h_counts6, void* stream) {
+  clear_error();
+  XT_REQUIRE(mp && h_counts6, TRON_EINVAL, "admm_mp_gen_status_counts: bad argument");
+  std::vector<int32_t> st((size_t)std::max(mp->ngen, 1));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (mp->ngen > 0)
+    XT_CUDA(cudaMemcpyAsync(st.data(), mp->d_status, 4 * (size_t)mp->ngen,
+                            cudaMemcpyDeviceToHost, s));
+  XT_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < 6; ++k) h_counts6[k] = 0;
+  for (int g = 0; g < mp->ngen; ++g)
+    if (st[g] >= 0 && st[g] < 6) h_counts6[st[g]]++;
+  return TRON_OK;
 }
 
 tron_err_t admm_branch_status_counts(admm_t* a, int64_t* h_counts6, void* stream) {

@@ -108,6 +108,15 @@ struct Grp {
     if (G == 1) return v;
     return __shfl_sync(mask, v, src, G);
   }
+  // value of rank t-1 (rank 0 gets its own) and of rank t+1 (the last rank its own)
+  __device__ __forceinline__ double from_prev(double v) const {
+    if (G == 1) return v;
+    return __shfl_up_sync(mask, v, 1, G);
+  }
+  __device__ __forceinline__ double from_next(double v) const {
+    if (G == 1) return v;
+    return __shfl_down_sync(mask, v, 1, G);
+  }
   __device__ __forceinline__ int bcast(int v, int src) const {
     if (G == 1) return v;
     return __shfl_sync(mask, v, src, G);

@@ -250,6 +250,9 @@ static std::vector<KernelEntry>& table() {
       make_entry<DenseObj<128, 32, kQGlobal>, 128, 32, true>(TRON_OBJ_DENSE_QUARTIC,
                                                         kLayoutPacked | kLayoutQGlobal),
       make_entry<Hs45Obj<8>, 8, 1, false>(TRON_OBJ_HS45, 0),
+      make_entry<GenRampObj<8, 8>, 8, 8, false>(TRON_OBJ_GEN_RAMP, 0),
+      make_entry<GenRampObj<16, 16>, 16, 16, false>(TRON_OBJ_GEN_RAMP, 0),
+      make_entry<GenRampObj<32, 32>, 32, 32, true>(TRON_OBJ_GEN_RAMP, kLayoutPacked),
   };
   return t;
 }
@@ -262,6 +265,7 @@ constexpr int kNumClasses = 6;
 static int size_class(int kind, int n) {
   if (kind == TRON_OBJ_ACOPF_BRANCH) return n == 4 ? 4 : -1;
   if (kind == TRON_OBJ_HS45) return (n >= 1 && n <= 8) ? 8 : -1;
+  if (kind == TRON_OBJ_GEN_RAMP) return n < 1 ? -1 : (n <= 8 ? 8 : (n <= 16 ? 16 : (n <= 32 ? 32 : -1)));
   if (kind == TRON_OBJ_DENSE_QUARTIC) {
     if (n < 1) return -1;
     for (int c : kClasses)
@@ -340,6 +344,7 @@ struct tron_batch {
 static int64_t record_size(int kind, int n) {
   if (kind == TRON_OBJ_ACOPF_BRANCH) return 36;
   if (kind == TRON_OBJ_DENSE_QUARTIC) return (int64_t)n * n + 2 * n;
+  if (kind == TRON_OBJ_GEN_RAMP) return 8 + 2 * (int64_t)n;
   return 0;
 }
 
@@ -400,7 +405,7 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
   XT_REQUIRE(out != nullptr, TRON_EINVAL, "tron_batch_create: out is NULL");
   *out = nullptr;
   XT_REQUIRE(kind == TRON_OBJ_ACOPF_BRANCH || kind == TRON_OBJ_DENSE_QUARTIC ||
-                 kind == TRON_OBJ_HS45,
+                 kind == TRON_OBJ_HS45 || kind == TRON_OBJ_GEN_RAMP,
              TRON_EINVAL, "tron_batch_create: unknown objective kind %d", (int)kind);
   XT_REQUIRE(nprob >= 0 && nprob < (int64_t)1 << 31, TRON_EINVAL,
              "tron_batch_create: nprob %lld out of range", (long long)nprob);
@@ -997,7 +1002,7 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
     void* stream) {
   clear_error();
   XT_REQUIRE(kind == TRON_OBJ_ACOPF_BRANCH || kind == TRON_OBJ_DENSE_QUARTIC ||
-                 kind == TRON_OBJ_HS45,
+                 kind == TRON_OBJ_HS45 || kind == TRON_OBJ_GEN_RAMP,
              TRON_EINVAL, "tron_solve_mixed_noalloc: unknown objective kind %d", (int)kind);
   XT_REQUIRE(nprob >= 0 && nprob <= kNoAllocMaxProblems, TRON_EINVAL,
              "tron_solve_mixed_noalloc: nprob = %lld exceeds the fixed scratch capacity of "

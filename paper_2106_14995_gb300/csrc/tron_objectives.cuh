@@ -404,6 +404,123 @@ struct BranchObj {
   }
 };
 
+// --------------------------------------------- multi-period generator (n <= 32 periods)
+// The generator component of the multi-period ADMM: its active power over the periods,
+// f = sum_t c2 p_t^2 + c1 p_t + lambda_t (p_t - target_t) + rho/2 (p_t - target_t)^2
+//     + rho_r/2 sum_{t>=1} max(0, |p_t - p_{t-1}| - R)^2,
+// record [c2 c1 rho rho_r R 0 0 0 | lambda[n] | target[n]].  One period per lane (G = N):
+// the ramp term of the pair (t-1, t) lives on lane t and reaches its neighbours by
+// shuffles; the Hessian is tridiagonal, kept as its diagonal and subdiagonal.
+template <int N, int G>
+struct GenRampObj {
+  static_assert(G == N && N <= 32, "one period per lane");
+  static constexpr int R = 1;
+  static constexpr int SMEM = 2 * N;  // diagonal, subdiagonal H(t, t-1) at t
+  static constexpr bool kHasHd = false;
+  static constexpr bool kStepEval = false;
+
+  SV<G> dg, sd;
+  double c2, c1, rho, rr, ramp, lam, tgt;
+  double ex, sg;  // ramp excess |d| - R and sign of d of the pair (t-1, t), last eval_f
+  double fsc;
+  int n;
+
+  __device__ __forceinline__ void bind(SV<G> base) {
+    dg = base;
+    sd = base.at(N);
+  }
+
+  template <class GP>
+  __device__ __forceinline__ bool load(const GP& gp, const double* __restrict__ rec, int n_) {
+    n = n_;
+    c2 = __ldg(rec + 0);
+    c1 = __ldg(rec + 1);
+    rho = __ldg(rec + 2);
+    rr = __ldg(rec + 3);
+    ramp = __ldg(rec + 4);
+    const int t = gp.t;
+    lam = t < n ? __ldg(rec + 8 + t) : 0.0;
+    tgt = t < n ? __ldg(rec + 8 + n + t) : 0.0;
+    bool fin = isfinite(c2) && isfinite(c1) && isfinite(rho) && isfinite(rr) &&
+               isfinite(ramp) && isfinite(lam) && isfinite(tgt);
+    dg[t] = 0.0;
+    sd[t] = 0.0;
+    gp.sync();
+    return !gp.any(!fin);
+  }
+
+  template <class GP>
+  __device__ __forceinline__ double eval_f(const GP& gp, const double (&y)[R]) {
+    const int t = gp.t;
+    const double p = y[0];
+    const double pp = gp.from_prev(p);
+    double val = 0.0, mag = 0.0;
+    ex = -1.0;
+    sg = 0.0;
+    if (t < n) {
+      const double r = p - tgt;
+      val = c2 * p * p + c1 * p + lam * r + 0.5 * rho * r * r;
+      mag = fabs(c2) * p * p + fabs(c1 * p) + fabs(lam * r) + 0.5 * rho * r * r +
+            (fabs(lam) + rho * fabs(r)) * (fabs(p) + fabs(tgt));
+      if (t >= 1) {
+        const double d = p - pp;
+        ex = fabs(d) - ramp;
+        sg = d > 0.0 ? 1.0 : -1.0;
+        if (ex > 0.0) {
+          val += 0.5 * rr * ex * ex;
+          mag += 0.5 * rr * ex * ex + rr * ex * (fabs(p) + fabs(pp) + ramp);
+        }
+      }
+    }
+    gp.sum2(val, mag);
+    fsc = mag;
+    return val;
+  }
+
+  // gradient and Hessian at the point of the last eval_f
+  template <class GP>
+  __device__ __forceinline__ void grad_hess(const GP& gp, const double (&x)[R], double (&g)[R]) {
+    const int t = gp.t;
+    const bool act = ex > 0.0;
+    const double w = act ? rr * ex * sg : 0.0;  // d/dp_t of the pair (t-1, t)
+    const double wn = gp.from_next(w);          // the pair (t, t+1), from lane t+1
+    const double an = gp.from_next(act ? 1.0 : 0.0);
+    const bool has_next = t + 1 < n;
+    double gt = 0.0, dt = 0.0;
+    if (t < n) {
+      const double p = x[0], r = p - tgt;
+      gt = 2.0 * c2 * p + c1 + lam + rho * r + w - (has_next ? wn : 0.0);
+      dt = 2.0 * c2 + rho + (act ? rr : 0.0) + (has_next && an != 0.0 ? rr : 0.0);
+    }
+    g[0] = gt;
+    dg[t] = dt;
+    sd[t] = (t < n && act) ? -rr : 0.0;
+    gp.sync();
+  }
+
+  __device__ __forceinline__ double hq(int i, int j) const {
+    if (i == j) return dg[i];
+    if (j == i - 1) return sd[i];
+    if (j == i + 1) return sd[j];
+    return 0.0;
+  }
+  __device__ __forceinline__ double hd(int) const { return 0.0; }
+
+  // row i of the tridiagonal Hessian times v (v staged in shared memory)
+  __device__ __forceinline__ double row_dot(int i, SV<G> v) const {
+    double s = dg[i] * v[i];
+    if (i >= 1) s = fma(sd[i], v[i - 1], s);
+    if (i + 1 < N) s = fma(sd[i + 1], v[i + 1], s);
+    return s;
+  }
+
+  template <class GP>
+  __device__ __forceinline__ bool hess_finite(const GP& gp) const {
+    const bool fin = isfinite(dg[gp.t]) && isfinite(sd[gp.t]);
+    return !gp.any(!fin);
+  }
+};
+
 // ------------------------------------------------------------------ hs45 variant
 // f = 120 - prod_i x_i (Sec. 4.2 footnote), one problem per lane, n <= N.
 template <int N>

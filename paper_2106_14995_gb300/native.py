@@ -16,7 +16,7 @@ from . import _build
 _lock = threading.Lock()
 _lib = None
 
-TRON_OBJ_ACOPF_BRANCH, TRON_OBJ_DENSE_QUARTIC, TRON_OBJ_HS45 = 1, 2, 3
+TRON_OBJ_ACOPF_BRANCH, TRON_OBJ_DENSE_QUARTIC, TRON_OBJ_HS45, TRON_OBJ_GEN_RAMP = 1, 2, 3, 4
 TRON_CONVERGED, TRON_MAX_ITER, TRON_TR_TOO_SMALL, TRON_CHOL_FAIL, TRON_NONFINITE, \
     TRON_BAD_BOUNDS = range(6)
 TRON_SCHED_PLAIN, TRON_SCHED_PERSISTENT = 0, 1
@@ -117,6 +117,12 @@ def load(build_if_missing: bool = True):
             "admm_pool_set_state": (I32, [P, I32, C.POINTER(AdmmStateView), P]),
             "admm_pool_live": (I32, [P]),
             "admm_pool_destroy": (None, [P]),
+            "admm_mp_create": (I32, [C.POINTER(P), C.POINTER(AdmmNetwork), I32, P, P,
+                                     C.c_double, C.POINTER(TronOptions), P]),
+            "admm_mp_step": (I32, [P, I32, P, P, P]),
+            "admm_mp_get_state": (I32, [P, I32, C.POINTER(AdmmStateView), P]),
+            "admm_mp_gen_status_counts": (I32, [P, P, P]),
+            "admm_mp_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
