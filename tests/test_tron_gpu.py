@@ -223,6 +223,16 @@ def test_concurrent_solves_on_two_streams_equal_sequential(mixed):
             np.testing.assert_array_equal(o[k].cpu().numpy(), r[k], err_msg=k)
 
 
+def test_ctas_per_sm_changes_the_schedule_not_the_results():
+    d = synth.dense_batch(900, 32, seed_index=97)
+    a = gpu_solve(d, n=32, schedule=native.TRON_SCHED_PERSISTENT)
+    b = gpu_solve(d, n=32, schedule=native.TRON_SCHED_PERSISTENT, ctas_per_sm=2)
+    for k in ("x", "f", "pg", "iters", "status", "delta"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    with pytest.raises(native.TronError, match="EINVAL"):
+        TronBatch(2, 4, n=8, opts=options(ctas_per_sm=-1))
+
+
 def _host(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).pin_memory()
 
