@@ -594,20 +594,26 @@ struct Solver {
   // Cauchy trial s(alpha) = P[x - alpha g] - x: q(s) <= mu0 g's and ||s|| <= mu1 delta.
   // kap = 0 for the first trial of a search (full product); otherwise alpha is kap times
   // the step length of the trial held in s, Hs, cl (clipped coordinates), and H s is
-  // rescaled from it.
+  // rescaled from it.  inside: alpha is below the largest breakpoint along -g (breakpt of
+  // Figure 2), i.e. some coordinate that -g moves is still strictly inside its box at
+  // x - alpha g: decided on the trial's own integer keys, without the breakpoints'
+  // divisions.
   __device__ __forceinline__ bool cauchy_try(double alpha, const double (&x)[R],
                                              const double (&g)[R], double delta,
                                              double (&s)[R], double (&Hs)[R], bool (&cl)[R],
-                                             double kap) {
+                                             double kap, bool& inside) {
     double sn[R];
     bool cn[R];
+    bool mv = false;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const double v = fma(alpha, -g[r], x[r]);
       const long long k = okey(v);
       cn[r] = (k < kl[r]) || (k > ku[r]);
+      mv = mv || (kl[r] < k && k < ku[r] && okey(g[r]) != 0);
       sn[r] = P(v, r) - x[r];
     }
+    inside = gp.any(mv);
     if (kap != 0.0) {
       bool both[R];
 #pragma unroll
@@ -629,20 +635,6 @@ struct Solver {
     const double q = gts + 0.5 * sHs;
     const double bound = o.mu1 * delta;
     return (q <= o.mu0 * gts) && (ss <= bound * bound);
-  }
-
-  // largest breakpoint along w = -g (breakpt of Figure 2), 0 if nothing can move
-  __device__ __forceinline__ double brptmax(const double (&x)[R], const double (&g)[R]) const {
-    double bmax = -CUDART_INF;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const double w = -g[r];
-      const long long kx = okey(x[r]), kw = okey(w);
-      if (kx < ku[r] && kw > 0) bmax = fmax(bmax, (u[r] - x[r]) / w);
-      else if (kx > kl[r] && kw < 0) bmax = fmax(bmax, (l[r] - x[r]) / w);
-    }
-    bmax = gp.max(bmax);
-    return (bmax == -CUDART_INF) ? 0.0 : bmax;
   }
 
   __device__ __forceinline__ bool all_finite(const double (&v)[R]) const {
@@ -746,8 +738,8 @@ struct Solver {
       double s[R], Hs[R];
       bool cl[R];
       double alpha = alpha_c;
-      if (cauchy_try(alpha, x, g, delta, s, Hs, cl, 0.0)) {
-        const double bmax = brptmax(x, g);
+      bool inside;
+      if (cauchy_try(alpha, x, g, delta, s, Hs, cl, 0.0, inside)) {
         double sb[R], Hsb[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -755,9 +747,9 @@ struct Solver {
           Hsb[r] = Hs[r];
         }
         for (int t = 0; t < o.max_trials; ++t) {
-          if (!(alpha < bmax)) break;
+          if (!inside) break;  // alpha at or beyond the largest breakpoint
           const double a2 = alpha * o.extrapf;
-          if (!cauchy_try(a2, x, g, delta, s, Hs, cl, o.extrapf)) break;
+          if (!cauchy_try(a2, x, g, delta, s, Hs, cl, o.extrapf, inside)) break;
           alpha = a2;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
@@ -773,7 +765,7 @@ struct Solver {
       } else {
         for (int t = 0; t < o.max_trials; ++t) {
           alpha = alpha * o.interpf;
-          if (cauchy_try(alpha, x, g, delta, s, Hs, cl, o.interpf)) break;
+          if (cauchy_try(alpha, x, g, delta, s, Hs, cl, o.interpf, inside)) break;
         }
       }
       alpha_c = alpha;
