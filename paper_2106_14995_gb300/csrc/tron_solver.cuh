@@ -101,6 +101,9 @@ struct Solver {
     if (b == (long long)0x8000000000000000ULL) b = 0;
     return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
   }
+  // a <= b and a < b for non-NaN doubles, on the integer keys (no FP64 instruction)
+  __device__ __forceinline__ static bool le(double a, double b) { return okey(a) <= okey(b); }
+  __device__ __forceinline__ static bool lt(double a, double b) { return okey(a) < okey(b); }
   // |v| > t for t >= 0 (magnitude bits compared as integers)
   __device__ __forceinline__ static bool abs_above(double v, long long tkey) {
     return (__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL) > tkey;
@@ -538,11 +541,12 @@ struct Solver {
     const double dsq = delta * delta;
     if (exact) {
       const double zz = dotv(z, z);
-      const double sg = (zz >= dsq) ? delta / sqrt(zz) : 1.0;
+      const bool bnd = le(dsq, zz);
+      const double sg = bnd ? delta / sqrt(zz) : 1.0;
 #pragma unroll
       for (int r = 0; r < R; ++r) w[r] = sg * z[r];
       wscale = sg;  // A w = -sg rF
-      return (zz >= dsq) ? 2 : 0;
+      return bnd ? 2 : 0;
     }
     double p[R], q[R];
     double rz = dotv(res, z);
@@ -634,7 +638,7 @@ struct Solver {
     gp.sum3(gts, sHs, ss);
     const double q = gts + 0.5 * sHs;
     const double bound = o.mu1 * delta;
-    return (q <= o.mu0 * gts) && (ss <= bound * bound);
+    return le(q, o.mu0 * gts) && le(ss, bound * bound);
   }
 
   __device__ __forceinline__ bool all_finite(const double (&v)[R]) const {
@@ -865,7 +869,7 @@ struct Solver {
             dHd = fma(d[r], Hd[r], dHd);
           }
           gp.sum2(rtd, dHd);
-          if (rtd + 0.5 * dHd <= o.mu0 * rtd) {
+          if (le(fma(0.5, dHd, rtd), o.mu0 * rtd)) {
             found = true;
             break;
           }
@@ -915,11 +919,11 @@ struct Solver {
       // rho = (ared + fl) / (pred + fl) is compared with each eta as
       // ared + fl > eta (pred + fl), the denominator being positive: no division; an
       // invalid ratio (pred <= 0 or f(y) not finite) counts as -infinity
-      const bool valid = (pred > 0.0) && isfinite(fy);
+      const bool valid = (okey(pred) > 0) && isfinite(fy) && isfinite(pred);
       const double num = ared + fl, den = pred + fl;
-      const bool above0 = valid && num > o.eta0 * den;
-      const bool below1 = !valid || num < o.eta1 * den;
-      const bool above2 = valid && num > o.eta2 * den;
+      const bool above0 = valid && lt(o.eta0 * den, num);
+      const bool below1 = !valid || lt(num, o.eta1 * den);
+      const bool above2 = valid && lt(o.eta2 * den, num);
       if (above0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = y[r];
@@ -935,7 +939,7 @@ struct Solver {
       const double d99 = 0.99 * delta;
       if (below1) {
         delta = o.sigma1 * fmin(sqrt(ss2), delta);
-      } else if (above2 && ss2 >= d99 * d99) {
+      } else if (above2 && le(d99 * d99, ss2)) {
         delta = fmin(o.sigma3 * delta, o.delta_max);
       }
       // delta < c (1 + ||x||), decided without a square root:
@@ -943,7 +947,7 @@ struct Solver {
       // box bound xb2 cannot decide
       const double dc = delta - o.delta_min_rel;
       const double c2 = o.delta_min_rel * o.delta_min_rel;
-      if (dc < 0.0 || (dc * dc < c2 * xb2 && dc * dc < c2 * dotv(x, x))) {
+      if (okey(dc) < 0 || (lt(dc * dc, c2 * xb2) && lt(dc * dc, c2 * dotv(x, x)))) {
         status = TRON_TR_TOO_SMALL;
         break;
       }
