@@ -409,7 +409,7 @@ struct Solver {
         const int i = Fi[c];
         double a = obj.hq(i, i);
         if (Obj::kHasHd) a = a + obj.hd(i);
-        nonpos = nonpos || !(a > 0.0);
+        nonpos = nonpos || !(okey(a) > 0);  // finite: a non-finite Hessian stops earlier
       }
     }
     const bool all_pos = !gp.any(nonpos);
@@ -915,7 +915,7 @@ struct Solver {
       // Methods, Sec. 17.4.2), measured on the magnitudes of the terms of f
       const double pred = -qs;
       const double ared = f - fy;
-      const double fl = o.ared_guard * fmax(fs, 1.0);
+      const double fl = o.ared_guard * (le(fs, 1.0) ? 1.0 : fs);  // max(1, S), S >= 0
       // rho = (ared + fl) / (pred + fl) is compared with each eta as
       // ared + fl > eta (pred + fl), the denominator being positive: no division; an
       // invalid ratio (pred <= 0 or f(y) not finite) counts as -infinity
