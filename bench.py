@@ -36,10 +36,10 @@ FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.0
 # From one ncu capture of the timed kernel (profiles/tron_dense32_n10000.md, 2,000
 # problems, scaled per problem to the launch), valid only for the kernel sources it was
 # taken on: DRAM bytes (19.05 MB per 2,000 problems) and the FP64 flops the kernel
-# executes (thread-level DFMA x 2 + DADD + DMUL: 317.5 Mflop per 2,000 problems).
-TRAFFIC_BYTES_PER_PROBLEM = 19.051776e6 / 2000
-EXEC_FLOPS_PER_PROBLEM = 317.48e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "361994aff232ddd33419be12174fe4930325a4f3"
+# executes (thread-level DFMA x 2 + DADD + DMUL: 312.9 Mflop per 2,000 problems).
+TRAFFIC_BYTES_PER_PROBLEM = 19.05152e6 / 2000
+EXEC_FLOPS_PER_PROBLEM = 312.918e6 / 2000
+TRAFFIC_SOURCES_SHA1 = "84f1a145a54934818e603f67851da8ff8bde261c"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
