@@ -165,3 +165,56 @@ def test_serving_loop_admits_waits_retires_and_matches_alone_runs():
     serial = serial_plain(reqs, chunk=4, max_iters=12)
     assert [x["iterations"] for x in sorted(serial, key=lambda x: x["id"])] == \
         [x["iterations"] for x in sorted(recs, key=lambda x: x["id"])]
+
+
+def test_admm_full_size_network_tracks_oracle():
+    # the benchmark's network (10,000 buses, 13,000 branches, 3,000 generators)
+    net = synth.network(10000, 3000, 3000, seed_index=2)
+    o = oracle.Admm(net)
+    hp, hd = o.run(6, nthreads=8)
+    g = Admm(net)
+    res = np.array([g.step(1) for _ in range(6)])
+    np.testing.assert_allclose(res[:, 0], hp, rtol=1e-6)
+    np.testing.assert_allclose(res[:, 1], hd, rtol=1e-6)
+    s = g.get_state()
+    rng = np.random.default_rng(0)
+    ks = rng.choice(13000, 500, replace=False)
+    np.testing.assert_allclose(s["br_x"][ks], o.arrays["br_x"][ks], rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(s["bus_w"], o.arrays["bus_w"], rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(s["gen_pq"], o.arrays["gen_pq"], rtol=1e-6, atol=1e-8)
+    g.close()
+
+
+def _edge_network():
+    # 5 buses: bus 3 has no branch (a generator and a load only), bus 4 carries two
+    # generators, bus 2 has neither generator nor load; branches 0-1, 1-2, 2-4, 4-0
+    rng = np.random.default_rng(60)
+    br_from = np.array([0, 1, 2, 4], dtype=np.int32)
+    br_to = np.array([1, 2, 4, 0], dtype=np.int32)
+    r, x, bc, smax = synth.random_lines(rng, 4)
+    return dict(nbus=5, br_from=br_from, br_to=br_to,
+                br_coef=synth.line_coefficients(r, x, bc), br_smax2=smax * smax,
+                gen_bus=np.array([3, 4, 4, 1], dtype=np.int32),
+                gen_c2=np.array([0.01, 0.02, 0.03, 0.015]),
+                gen_c1=np.array([10.0, 20.0, 15.0, 12.0]),
+                gen_pmin=np.zeros(4), gen_pmax=np.array([1.0, 0.8, 0.6, 1.2]),
+                gen_qmin=np.full(4, -0.5), gen_qmax=np.full(4, 0.5),
+                bus_pd=np.array([0.3, 0.2, 0.0, 0.4, 0.5]),
+                bus_qd=np.array([0.05, 0.1, 0.0, 0.1, 0.0]),
+                bus_gsh=np.zeros(5), bus_bsh=np.zeros(5))
+
+
+def test_admm_edge_network_isolated_and_multi_generator_buses():
+    net = _edge_network()
+    o = oracle.Admm(net)
+    hp, hd = o.run(25)
+    g = Admm(net)
+    res = np.array([g.step(1) for _ in range(25)])
+    np.testing.assert_allclose(res[:, 0], hp, rtol=1e-6)
+    np.testing.assert_allclose(res[:, 1], hd, rtol=1e-6)
+    s = g.get_state()
+    for k in ("gen_pq", "gen_lam", "bus_w", "bus_th", "br_x", "br_lam"):
+        np.testing.assert_allclose(s[k], o.arrays[k], rtol=1e-6, atol=1e-8, err_msg=k)
+    # the isolated bus keeps its voltage (no branch copies to average)
+    assert s["bus_w"][3] == 1.0 and s["bus_th"][3] == 0.0
+    g.close()

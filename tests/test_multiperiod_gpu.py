@@ -107,3 +107,20 @@ def test_multiperiod_rejects_bad_arguments():
         AdmmMultiPeriod(net, np.ones(4), ramp=-0.1)
     with pytest.raises(native.TronError, match="EINVAL"):
         AdmmMultiPeriod(net, [1.0, 0.0], ramp=0.1)
+
+
+def test_multiperiod_benchmark_size_tracks_oracle():
+    # the benchmark's workload: 24 periods x (2,000 buses, 2,600 branches, 600 generators)
+    net = synth.network(2000, 600, 600, seed_index=9)
+    scale = synth.load_profile(24)
+    kw = dict(ramp=0.05 * net["gen_pmax"], rho_ramp=1e4)
+    o = oracle.MultiPeriodAdmm(net, scale, **kw)
+    hp, hd = o.run(3, nthreads=8)
+    g = AdmmMultiPeriod(net, scale, **kw)
+    res = np.array([g.step(1) for _ in range(3)])
+    np.testing.assert_allclose(res[:, 0], hp, rtol=1e-6)
+    np.testing.assert_allclose(res[:, 1], hd, rtol=1e-6)
+    for t in (0, 11, 23):
+        np.testing.assert_allclose(g.get_state(t)["gen_pq"], o.state(t)["gen_pq"], rtol=1e-6,
+                                   atol=1e-8)
+    g.close()
