@@ -650,9 +650,9 @@ struct Solver {
 
   // H d for the projected search's first trial d = P[y + w] - y when nothing is clipped
   // and w came from the exact-preconditioner step: on the free rows H_FF w_F = -sigma rF
-  // (rF is rv there), so only the rows of the bound variables (at most 3, d = 0 on
-  // them) need their dot products, reduced in one fused butterfly.  One variable per
-  // lane only; false, with nothing computed, otherwise.
+  // (rF is rv there), so only the rows of the bound variables (at most 6, d = 0 on
+  // them) need their dot products, reduced three at a time in fused butterflies.  One
+  // variable per lane only; false, with nothing computed, otherwise.
   __device__ __forceinline__ bool first_trial_known(double wscale, const int (&cidx)[R],
                                                     const bool (&cn)[R], const double (&rv)[R],
                                                     const double (&d)[R], double (&Hd)[R]) {
@@ -661,25 +661,26 @@ struct Solver {
     } else {
       if (wscale == 0.0 || gp.any(cn[0])) return false;
       const bool bnd = cidx[0] < 0 && gp.t < n;
-      const unsigned msk = gp.ballot(bnd);
-      if (__popc(msk) > 3) return false;
-      int ib[3] = {-1, -1, -1};
-      unsigned mm = msk;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (mm) {
-          ib[q] = __ffs(mm) - 1;
-          mm &= mm - 1u;
-        }
-      }
-      double p0 = ib[0] >= 0 ? obj.hq(ib[0], gp.t) * d[0] : 0.0;
-      double p1 = ib[1] >= 0 ? obj.hq(ib[1], gp.t) * d[0] : 0.0;
-      double p2 = ib[2] >= 0 ? obj.hq(ib[2], gp.t) * d[0] : 0.0;
-      gp.sum3(p0, p1, p2);
+      unsigned mm = gp.ballot(bnd);
+      if (__popc(mm) > 6) return false;
       double h = (cidx[0] >= 0) ? -wscale * rv[0] : 0.0;
-      if (gp.t == ib[0]) h = p0;
-      if (gp.t == ib[1]) h = p1;
-      if (gp.t == ib[2]) h = p2;
+      while (mm) {  // group-uniform: up to three bound rows per fused reduction
+        int ib[3] = {-1, -1, -1};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (mm) {
+            ib[q] = __ffs(mm) - 1;
+            mm &= mm - 1u;
+          }
+        }
+        double p0 = ib[0] >= 0 ? obj.hq(ib[0], gp.t) * d[0] : 0.0;
+        double p1 = ib[1] >= 0 ? obj.hq(ib[1], gp.t) * d[0] : 0.0;
+        double p2 = ib[2] >= 0 ? obj.hq(ib[2], gp.t) * d[0] : 0.0;
+        gp.sum3(p0, p1, p2);
+        if (gp.t == ib[0]) h = p0;
+        if (gp.t == ib[1]) h = p1;
+        if (gp.t == ib[2]) h = p2;
+      }
       Hd[0] = h;
       return true;
     }
