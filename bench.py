@@ -364,7 +364,10 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    _build.build()
+    if rank == 0:  # one rank compiles (if anything is stale); the others wait for it
+        _build.build()
+    if world > 1:
+        dist.barrier()
     native.load()
 
     # weak scaling: every rank solves its own batch of the same distribution (rank 0
