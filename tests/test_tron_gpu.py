@@ -297,6 +297,27 @@ def test_edge_cases_status_codes():
     assert np.all(g["iters"][[0, 3, 4]] == 1)
 
 
+@pytest.mark.parametrize("n", [6, 32, 64])
+def test_degenerate_boxes_fixed_variables(n):
+    # l = u on some variables (fixed), every variable fixed in one problem, a
+    # zero-width box at the unconstrained minimiser's side, and x0 already optimal
+    d = synth.dense_batch(12, n, seed_index=70 + n)
+    rng = np.random.default_rng(70 + n)
+    for p in range(12):
+        fix = rng.random(n) < 0.3
+        d["l"][p, fix] = d["u"][p, fix] = rng.uniform(-0.5, 0.5, fix.sum())
+    d["l"][3] = d["u"][3] = 0.25                                  # everything fixed
+    r0 = oracle_solve(d)
+    d["x0"][5] = r0["x"][5]                                       # start at the solution
+    g = gpu_solve(d, n=n)
+    r = oracle_solve(d)
+    assert_convex_parity(g, r, d["l"], d["u"])
+    fixed = d["l"] == d["u"]
+    np.testing.assert_array_equal(g["x"][fixed], d["l"][fixed])
+    assert g["iters"][3] == r["iters"][3]
+    assert g["iters"][5] <= 1
+
+
 def test_empty_batch_is_noop():
     tb = TronBatch(native.TRON_OBJ_DENSE_QUARTIC, 0, n=8)
     e = torch.empty(0, dtype=torch.float64, device=DEV)
