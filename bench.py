@@ -38,8 +38,8 @@ FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.0
 # taken on: DRAM bytes (19.05 MB per 2,000 problems) and the FP64 flops the kernel
 # executes (thread-level DFMA x 2 + DADD + DMUL: 312.9 Mflop per 2,000 problems).
 TRAFFIC_BYTES_PER_PROBLEM = 19.05152e6 / 2000
-EXEC_FLOPS_PER_PROBLEM = 312.918e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "84f1a145a54934818e603f67851da8ff8bde261c"
+EXEC_FLOPS_PER_PROBLEM = 309.82e6 / 2000
+TRAFFIC_SOURCES_SHA1 = "e5c63abf3a8ce4fa61a7c470dbd61c8a33ca3eeb"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
