@@ -79,7 +79,12 @@ typedef admm_pool_t admm_t;
 
 /* Create the device state of one network (initial point: v = 1, theta = 0, generators
  * at box midpoints, bus copies equal to the component values, lambda = 0, delta = 1).
- * opt: TRON options of the branch solves (NULL = defaults). */
+ * opt: TRON options of the branch solves (NULL = defaults).  options.group is the number
+ * of lanes per branch problem in the branch launch: 1, 4, or 0 = chosen by the branch
+ * slots per SM sub-partition (4 up to 24 slots per sub-partition: the launch is then as
+ * long as its slowest problem, whose serial chain four lanes shorten; 1 beyond, where
+ * the FP64 issue rate over all problems decides); any other value is TRON_EINVAL.  The
+ * choice is fixed for the life of the handle or pool. */
 tron_err_t admm_create(admm_t** out, const admm_network_t* net, const tron_options_t* opt,
                        void* stream);
 
@@ -141,6 +146,8 @@ tron_err_t admm_pool_get_state(admm_pool_t* p, int32_t id, admm_state_view_t* ho
 tron_err_t admm_pool_set_state(admm_pool_t* p, int32_t id, const admm_state_view_t* host,
                                void* stream);
 int32_t admm_pool_live(const admm_pool_t* p);
+/* Lanes per branch problem the pool's branch launch uses (1 or 4); 0 for NULL. */
+int32_t admm_pool_branch_group(const admm_pool_t* p);
 void admm_pool_destroy(admm_pool_t* p);
 
 /* --------------------------------------- multi-period ADMM (the paper's future work)

@@ -101,6 +101,11 @@ class Admm:
     def iterations(self) -> int:
         return int(self._lib.admm_iterations(self._h))
 
+    @property
+    def branch_group(self) -> int:
+        """Lanes per branch problem in the branch launch (1 or 4)."""
+        return int(self._lib.admm_pool_branch_group(self._h))
+
     def get_state(self) -> dict:
         bufs = _state_buffers(self.sizes)
         v = _view(bufs)
@@ -202,6 +207,11 @@ class AdmmPool:
     @property
     def live(self) -> int:
         return int(self._lib.admm_pool_live(self._h))
+
+    @property
+    def branch_group(self) -> int:
+        """Lanes per branch problem in the branch launch (1 or 4)."""
+        return int(self._lib.admm_pool_branch_group(self._h))
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -31,6 +31,11 @@ namespace xt {
 constexpr int kAlign = 128;      // slot alignment of every instance range
 constexpr int kBusThreads = 128; // = kAlign: one bus block never spans two instances
 constexpr int kGraphChunk = 8;   // iterations per replayed graph
+// lanes per branch problem when options.group is 0: four while the pool holds at most
+// this many branch slots per SM sub-partition (the launch is then as long as its slowest
+// problem's serial chain, which four lanes shorten), one beyond (the FP64 issue rate over
+// all problems decides, and one lane per problem needs the fewest instructions)
+constexpr int kG4BranchesPerSmsp = 24;
 constexpr double kTwoPi = 6.283185307179586;
 
 struct PoolDev {
@@ -95,24 +100,27 @@ struct AdmmArgs {
   int32_t ngb;    // generator CTAs
 };
 
-using BranchSolver = Solver<BranchObj, 4, 1>;
+template <int G>
+using BranchSolver = Solver<BranchObj<G>, 4, G>;
 
-__global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
-  const PoolDev& d = a.d;
-  if ((int)blockIdx.x < a.nbb) {
-    extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = ((int)blockIdx.x * (int)(blockDim.x >> 5) + warp) * 32 + lane;
-    if (k >= d.cap_br) return;
-    const int inst = d.br_inst[k];
-    if (inst < 0 || !d.inst_active[inst]) return;
-    const double rho = d.inst_param[4 * inst + 0];
-    const double rhol = d.inst_param[4 * inst + 1];
-    const double vmin = d.inst_param[4 * inst + 2];
-    const double vmax = d.inst_param[4 * inst + 3];
-    BranchSolver sv(a.opt, smem + (size_t)warp * BranchSolver::WARP_DOUBLES);
-    sv.n = 4;
-    sv.obj.n = 4;
+// the branch update of slot k by a group of G lanes (G = 1: one branch per lane; G = 4:
+// lane t owns variable t, flow t and the pair terms t and t + 4)
+template <int G>
+__device__ __forceinline__ void branch_update(const PoolDev& d, const tron_options_t& opt,
+                                              double* wsm, int k) {
+  using S = BranchSolver<G>;
+  const int inst = d.br_inst[k];
+  if (inst < 0 || !d.inst_active[inst]) return;
+  const double rho = d.inst_param[4 * inst + 0];
+  const double rhol = d.inst_param[4 * inst + 1];
+  const double vmin = d.inst_param[4 * inst + 2];
+  const double vmax = d.inst_param[4 * inst + 3];
+  S sv(opt, wsm);
+  sv.n = 4;
+  sv.obj.n = 4;
+  const int i = d.br_from[k], j = d.br_to[k];
+  bool fin = true;
+  if constexpr (G == 1) {
     sv.l[0] = vmin;
     sv.l[1] = vmin;
     sv.l[2] = -kTwoPi;
@@ -122,8 +130,6 @@ __global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
     sv.u[2] = kTwoPi;
     sv.u[3] = kTwoPi;
     // the branch record: coefficients, multipliers, bus-side copies as targets
-    const int i = d.br_from[k], j = d.br_to[k];
-    bool fin = true;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const double c = d.br_coef[8 * (size_t)k + q];
@@ -167,6 +173,57 @@ __global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
     d.br_status[k] = st;
     d.br_iters[k] = it;
   } else {
+    const int t = sv.gp.t;
+    sv.l[0] = t < 2 ? vmin : -kTwoPi;
+    sv.u[0] = t < 2 ? vmax : kTwoPi;
+    // rank t stages entries t and t + 4 of the coefficients, multipliers and penalties,
+    // and the targets of the pair terms t (flow) and t + 4 (w_i, w_j, theta_i, theta_j)
+#pragma unroll
+    for (int q = t; q < 8; q += 4) {
+      const double c = d.br_coef[8 * (size_t)k + q];
+      const double l = d.br_lam[8 * (size_t)k + q];
+      fin = fin && isfinite(c) && isfinite(l);
+      sv.obj.rec[q] = c;
+      sv.obj.rec[8 + q] = l;
+      sv.obj.rec[24 + q] = rho;
+    }
+    const int bus = (t & 1) ? j : i;
+    const double tg1 = d.br_tilde[4 * (size_t)k + t];
+    const double tg2 = t < 2 ? d.bus_w[bus] : d.bus_th[bus];
+    fin = fin && isfinite(tg1) && isfinite(tg2);
+    sv.obj.rec[16 + t] = tg1;
+    sv.obj.rec[20 + t] = tg2;
+    if (t == 0) sv.obj.rec[32] = d.br_smax2[k];
+    if (t == 1) sv.obj.rec[33] = rhol;
+    sv.gp.sync();
+    sv.obj.prepare(t);
+    fin = !sv.gp.any(!fin);
+    double x[1] = {d.br_x[4 * (size_t)k + t]};
+    double delta = d.br_delta[k];
+    double f, pg;
+    int it;
+    const int st = sv.run(x, delta, f, pg, it, fin);
+    d.br_x[4 * (size_t)k + t] = x[0];
+    d.br_val[8 * (size_t)k + t] = sv.obj.Fx;
+    d.br_val[8 * (size_t)k + 4 + t] = t < 2 ? x[0] * x[0] : x[0];
+    if (t == 0) {
+      d.br_delta[k] = delta;
+      d.br_status[k] = st;
+      d.br_iters[k] = it;
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
+  const PoolDev& d = a.d;
+  if ((int)blockIdx.x < a.nbb) {
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = ((int)blockIdx.x * (int)(blockDim.x >> 5) + warp) * (32 / G) + lane / G;
+    if (k >= d.cap_br) return;
+    branch_update<G>(d, a.opt, smem + (size_t)warp * BranchSolver<G>::WARP_DOUBLES, k);
+  } else {
     const int g = ((int)blockIdx.x - a.nbb) * (int)blockDim.x + (int)threadIdx.x;
     if (g >= d.cap_gen) return;
     const int inst = d.gen_inst[g];
@@ -183,6 +240,15 @@ __global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
     d.gen_pq[2 * g] = p;
     d.gen_pq[2 * g + 1] = q;
   }
+}
+
+// the branch kernel and its shared memory per warp for branch group size G (1 or 4)
+static const void* branch_kernel(int G) {
+  return G == 4 ? (const void*)k_admm_branch_gen<4> : (const void*)k_admm_branch_gen<1>;
+}
+static size_t branch_warp_bytes(int G) {
+  return sizeof(double) * (size_t)(G == 4 ? BranchSolver<4>::WARP_DOUBLES
+                                          : BranchSolver<1>::WARP_DOUBLES);
 }
 
 __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
@@ -487,7 +553,8 @@ struct admm_pool {
   PoolDev d;
   tron_options_t opt;
   int nbb, ngb, nbusb;
-  int bw;  // warps per branch CTA
+  int bw;   // warps per branch CTA
+  int grp;  // lanes per branch problem (1 or 4)
   RangeAlloc ab, al, ag;
   struct Inst {
     bool live;
@@ -532,11 +599,11 @@ static AdmmArgs make_args(const admm_pool* p) {
 
 static tron_err_t launch_iteration(admm_pool* p, cudaStream_t st) {
   AdmmArgs a = make_args(p);
-  const size_t smem = (size_t)p->bw * BranchSolver::WARP_DOUBLES * sizeof(double);
+  const size_t smem = (size_t)p->bw * branch_warp_bytes(p->grp);
   void* args[] = {&a};
-  // every CTA has bw warps: a branch CTA solves 32 branches per warp (each warp owns
-  // its slice of the shared memory), a generator CTA updates one generator per thread
-  XT_CUDA(cudaLaunchKernel((const void*)k_admm_branch_gen, dim3(p->nbb + p->ngb),
+  // every CTA has bw warps: a branch CTA solves 32 / grp branches per warp (each warp
+  // owns its slice of the shared memory), a generator CTA updates one generator per thread
+  XT_CUDA(cudaLaunchKernel(branch_kernel(p->grp), dim3(p->nbb + p->ngb),
                            dim3(p->bw * 32), args, smem, st));
   XT_CUDA(cudaLaunchKernel((const void*)k_admm_bus, dim3(p->nbusb), dim3(kBusThreads), args, 0,
                            st));
@@ -576,6 +643,8 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
   XT_REQUIRE(cap_bus >= 0 && cap_branch >= 0 && cap_gen >= 0 && cap_instances > 0 &&
                  history_len > 0,
              TRON_EINVAL, "admm_pool_create: bad capacities");
+  XT_REQUIRE(!opt || opt->group == 0 || opt->group == 1 || opt->group == 4, TRON_EINVAL,
+             "admm: options.group must be 0, 1 or 4");
   admm_pool* p = new admm_pool();
   memset(&p->d, 0, sizeof(p->d));
   p->cap_stream = nullptr;
@@ -584,17 +653,30 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
   p->live = 0;
   if (opt) p->opt = *opt;
   else tron_options_default(&p->opt);
-  p->opt.group = 1;
   const int cb = align_up(cap_bus), cl = align_up(cap_branch), cg = align_up(cap_gen);
+  // lanes per branch problem: options.group 1 or 4, or (0) chosen by the branch slots
+  // per SM sub-partition; fixed for the pool's life, so an instance's results do not
+  // depend on its co-residents
+  if (p->opt.group == 0) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 0;
+    p->grp = (nsm > 0 && (long long)cl <= (long long)kG4BranchesPerSmsp * 4 * nsm) ? 4 : 1;
+  } else {
+    p->grp = p->opt.group;
+  }
+  p->opt.group = p->grp;
   p->d.cap_bus = cb;
   p->d.cap_br = cl;
   p->d.cap_gen = cg;
   p->d.cap_inst = cap_instances;
   p->d.H = history_len;
   // branch CTA size: options.warps_per_block (default 1: spread the branch warps over
-  // every SM); one 32-branch warp per CTA warp
+  // every SM); 32 / grp branches per CTA warp
   p->bw = p->opt.warps_per_block > 0 ? std::min(p->opt.warps_per_block, 8) : 1;
-  p->nbb = (cl + p->bw * 32 - 1) / (p->bw * 32);
+  const int bpw = 32 / p->grp;
+  p->nbb = (cl + p->bw * bpw - 1) / (p->bw * bpw);
   p->ngb = (cg + p->bw * 32 - 1) / (p->bw * 32);
   p->nbusb = std::max(1, (cb + kBusThreads - 1) / kBusThreads);
   PA(br_from, cl);
@@ -664,8 +746,8 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
       cudaMemsetAsync(p->d.done, 0, sizeof(unsigned int), st) ||
       cudaMemsetAsync(p->d.part, 0, sizeof(double) * 2 * p->nbusb, st))
     return fail("workspace initialisation");
-  const size_t smem = (size_t)p->bw * BranchSolver::WARP_DOUBLES * sizeof(double);
-  if (cudaFuncSetAttribute((const void*)k_admm_branch_gen,
+  const size_t smem = (size_t)p->bw * branch_warp_bytes(p->grp);
+  if (cudaFuncSetAttribute(branch_kernel(p->grp),
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
     return fail("cudaFuncSetAttribute");
   if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking)) return fail("stream");
@@ -960,6 +1042,8 @@ tron_err_t admm_pool_set_state(admm_pool_t* p, int32_t id, const admm_state_view
 
 int32_t admm_pool_live(const admm_pool_t* p) { return p ? p->live : 0; }
 
+int32_t admm_pool_branch_group(const admm_pool_t* p) { return p ? p->grp : 0; }
+
 void admm_pool_destroy(admm_pool_t* p) {
   if (!p) return;
   if (p->g1) cudaGraphExecDestroy(p->g1);
@@ -1152,11 +1236,11 @@ tron_err_t admm_mp_step(admm_mp_t* mp, int32_t n_iters, double* h_primal, double
   admm_pool* p = mp->pool;
   AdmmArgs a = make_args(p);
   void* args[] = {&a};
-  const size_t smem = (size_t)p->bw * BranchSolver::WARP_DOUBLES * sizeof(double);
+  const size_t smem = (size_t)p->bw * branch_warp_bytes(p->grp);
   const int nthr = mp->ngen * mp->T;
   for (int it = 0; it < n_iters; ++it) {
     // branches (the flagged periods' generators are skipped there) ...
-    XT_CUDA(cudaLaunchKernel((const void*)k_admm_branch_gen, dim3(p->nbb + p->ngb),
+    XT_CUDA(cudaLaunchKernel(branch_kernel(p->grp), dim3(p->nbb + p->ngb),
                              dim3(p->bw * 32), args, smem, st));
     // ... generators over all periods ...
     if (nthr > 0) {

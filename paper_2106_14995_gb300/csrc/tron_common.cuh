@@ -121,6 +121,11 @@ struct Grp {
     if (G == 1) return v;
     return __shfl_sync(mask, v, src, G);
   }
+  // value of rank t ^ o (0 < o < G)
+  __device__ __forceinline__ double exch(double v, int o) const {
+    if (G == 1) return v;
+    return __shfl_xor_sync(mask, v, o, G);
+  }
 };
 
 // A group spanning a whole CTA (G = 64 or 128 threads, one problem per CTA) for the

@@ -225,7 +225,8 @@ static KernelEntry make_entry(int kind, int layout) {
 // every compiled variant; the first entry of a (kind, N) pair is its default
 static std::vector<KernelEntry>& table() {
   static std::vector<KernelEntry> t = {
-      make_entry<BranchObj, 4, 1, false>(TRON_OBJ_ACOPF_BRANCH, 0),
+      make_entry<BranchObj<1>, 4, 1, false>(TRON_OBJ_ACOPF_BRANCH, 0),
+      make_entry<BranchObj<4>, 4, 4, false>(TRON_OBJ_ACOPF_BRANCH, 0),
       make_entry<DenseObj<4, 4>, 4, 4, false>(TRON_OBJ_DENSE_QUARTIC, 0),
       make_entry<DenseObj<4, 1>, 4, 1, false>(TRON_OBJ_DENSE_QUARTIC, 0),
       make_entry<DenseObj<8, 8>, 8, 8, false>(TRON_OBJ_DENSE_QUARTIC, 0),

@@ -214,10 +214,22 @@ struct DenseObj {
 };
 
 // -------------------------------------------------------------- ACOPF branch (n = 4)
-// eq. exp-branch of Sec. 6.1 with the flows of eqs. pij-qji and the line-limit penalty.
-// One problem per lane (G = 1): every lane evaluates its own branch, so the FP64 pipe
-// (including the sin/cos of theta_i - theta_j) runs with all 32 lanes busy.
-struct BranchObj {
+// eq. exp-branch of Sec. 6.1 with the flows of eqs. pij-qji and the line-limit penalty,
+// record [coefficients c[8] | lambda[8] | targets[8] | rho[8] | smax^2 | rho_line].
+// Two mappings:
+//   BranchObj<1>: one problem per lane; every lane evaluates its own branch, so the FP64
+//                 pipe (including the sin/cos of theta_i - theta_j) runs with all 32
+//                 lanes busy -- the most problems per FP64 instruction.
+//   BranchObj<4>: one problem per four lanes; lane t owns variable t, flow t and the pair
+//                 terms t and t + 4 and assembles row t of the Hessian.  A warp's
+//                 duration is that of its slowest problem, and with one problem's work
+//                 spread over four lanes that serial chain is much shorter: the mapping
+//                 for launches with few problems per SM (an ADMM iteration's branches).
+template <int G>
+struct BranchObj;
+
+template <>
+struct BranchObj<1> {
   static constexpr int N = 4;
   static constexpr int R = 4;
   static constexpr int SMEM = 36 + 16;  // record, Hessian
@@ -401,6 +413,235 @@ struct BranchObj {
 #pragma unroll
     for (int e = 0; e < 16; ++e) fin = fin && isfinite(H[e]);
     return fin;
+  }
+};
+
+template <>
+struct BranchObj<4> {
+  static constexpr int N = 4;
+  static constexpr int R = 1;
+  static constexpr int SMEM = 36 + 16;  // record, Hessian (row-major)
+  static constexpr bool kHasHd = false;
+  static constexpr bool kStepEval = false;
+
+  SV<4> rec, H;
+  double ca, cR, cI;  // flow t = ca w + cR wR + cI wI (w = w_i for t < 2, else w_j)
+  double a0, a1;      // 2 ca where w is w_i (a0) or w_j (a1), else 0
+  // at the point of the last eval_f; the first six are the same in the four lanes
+  double vi, vj, sn, cs, wR, wI;
+  double Ft, r1, r2;  // flow t, residuals of the pair terms t and t + 4
+  double mx;          // p^2 + q^2 - smax^2 of the direction of flow t
+  double Fx;          // flow t at the point of the last grad_hess
+  double fsc;
+  int n;
+
+  __device__ __forceinline__ void bind(SV<4> base) {
+    rec = base;
+    H = base.at(36);
+  }
+
+  // per-lane coefficients from the staged record (after the group has synchronised):
+  //   F0 = c0 w_i - c2 wR + c3 wI,  F1 = c1 w_i - c3 wR - c2 wI,
+  //   F2 = c4 w_j - c6 wR - c7 wI,  F3 = c5 w_j - c7 wR + c6 wI
+  __device__ __forceinline__ void prepare(int t) {
+    ca = rec[t < 2 ? t : t + 2];
+    cR = -rec[t == 0 ? 2 : (t == 1 ? 3 : (t == 2 ? 6 : 7))];
+    const double c = rec[t == 0 ? 3 : (t == 1 ? 2 : (t == 2 ? 7 : 6))];
+    cI = (t == 0 || t == 3) ? c : -c;
+    a0 = t < 2 ? 2.0 * ca : 0.0;
+    a1 = t < 2 ? 0.0 : 2.0 * ca;
+  }
+
+  template <class GP>
+  __device__ __forceinline__ bool load(const GP& gp, const double* __restrict__ src, int n_) {
+    n = n_;
+    bool fin = true;
+    for (int k = gp.t; k < 34; k += 4) {
+      const double v = __ldg(src + k);
+      fin = fin && isfinite(v);
+      rec[k] = v;
+    }
+    gp.sync();
+    prepare(gp.t);
+    return !gp.any(!fin);
+  }
+
+  template <class GP>
+  __device__ __forceinline__ double eval_f(const GP& gp, const double (&y)[1]) {
+    const int t = gp.t;
+    vi = gp.bcast(y[0], 0);
+    vj = gp.bcast(y[0], 1);
+    const double thi = gp.bcast(y[0], 2), thj = gp.bcast(y[0], 3);
+    sincos(thi - thj, &sn, &cs);
+    const double vv = vi * vj;
+    wR = vv * cs;
+    wI = vv * sn;
+    const double vf = t < 2 ? vi : vj;
+    const double wf = vf * vf;
+    const double yy = y[0] * y[0];
+    Ft = ca * wf + cR * wR + cI * wI;
+    // magnitudes of the terms of each pair quantity (rounding scale of f)
+    const double Mt = fabs(ca) * wf + fabs(cR) * fabs(wR) + fabs(cI) * fabs(wI);
+    // pair term t + 4: w_i, w_j, theta_i, theta_j
+    const double P2 = t < 2 ? yy : y[0];
+    const double M2 = t < 2 ? yy : fabs(y[0]);
+    r1 = Ft - rec[16 + t];
+    r2 = P2 - rec[20 + t];
+    const double l1 = rec[8 + t], l2 = rec[12 + t];
+    const double p1 = rec[24 + t], p2 = rec[28 + t];
+    double val = l1 * r1 + 0.5 * p1 * r1 * r1;
+    double mag = fabs(l1 * r1) + 0.5 * p1 * r1 * r1 + (fabs(l1) + p1 * fabs(r1)) * Mt;
+    val += l2 * r2 + 0.5 * p2 * r2 * r2;
+    mag += fabs(l2 * r2) + 0.5 * p2 * r2 * r2 + (fabs(l2) + p2 * fabs(r2)) * M2;
+    // line limit of the direction of flow t (its flows on ranks 2d, 2d + 1): squares
+    // added unfused, so both ranks of the pair hold the same bits and take the same branch
+    const double sq = __dmul_rn(Ft, Ft);
+    const double p2q2 = __dadd_rn(sq, gp.exch(sq, 1));
+    const double smax2 = rec[32], rhol = rec[33];
+    mx = p2q2 - smax2;
+    if (mx > 0.0 && (t & 1) == 0) {
+      val += 0.5 * rhol * mx * mx;
+      mag += 0.5 * rhol * mx * mx + rhol * mx * (p2q2 + smax2);
+    }
+    gp.sum2(val, mag);
+    fsc = mag;
+    return val;
+  }
+
+  // gradient and Hessian row t at the point of the last eval_f.  The sums over the four
+  // flows -- the scalars (Aw, Bw, CR, CI) multiplying the derivatives of w_i, w_j, wR, wI
+  // (with the weights of the pair terms of w_i, w_j) and the Gauss-Newton entries of
+  // sum_k W_k dF_k dF_k' -- are one reduce-scatter butterfly over the group.
+  template <class GP>
+  __device__ __forceinline__ void grad_hess(const GP& gp, const double (&x)[1], double (&g)[1]) {
+    const int t = gp.t;
+    Fx = Ft;
+    const double p1 = rec[24 + t], rhol = rec[33];
+    double tw = rec[8 + t] + p1 * r1;                   // first-order weight of flow t
+    const double tw2 = rec[12 + t] + rec[28 + t] * r2;  // of the pair term t + 4
+    double W = p1;                                      // Gauss-Newton weight of flow t
+    const bool act = mx > 0.0;
+    if (act) {
+      // (rho_l/2) m^2, m = p^2 + q^2 - smax^2: first-order weight 2 rho_l m F_t, and
+      // 2 rho_l m on dF_t dF_t' (the rest, rho_l grad m grad m', below)
+      tw += rhol * mx * 2.0 * Ft;
+      W += 2.0 * rhol * mx;
+    }
+    // row t of dF = d(flows)/d(v_i, v_j, theta_i, theta_j); the theta_j entry is -d2
+    const double h = cR * cs + cI * sn;
+    const double d0 = fma(a0, vi, vj * h);
+    const double d1 = fma(a1, vj, vi * h);
+    const double d2 = cI * wR - cR * wI;
+    const double twc = tw * ca, tws = twc + tw2;
+    const double u0 = W * d0, u1 = W * d1, u2 = W * d2;
+    double v[10];
+    v[0] = t == 0 ? tws : (t == 1 ? twc : 0.0);  // Aw: flows 0, 1 and the term of w_i
+    v[1] = t == 1 ? tw2 : (t >= 2 ? twc : 0.0);  // Bw: flows 2, 3 and the term of w_j
+    v[2] = tw * cR;
+    v[3] = tw * cI;
+    v[4] = d0 * u0;
+    v[5] = d0 * u1;
+    v[6] = d0 * u2;
+    v[7] = d1 * u1;
+    v[8] = d1 * u2;
+    v[9] = d2 * u2;
+    if (gp.any(act)) {
+      // rho_l grad m grad m' of each exceeded direction, grad m = 2p dF_p + 2q dF_q,
+      // added once per direction (by its even rank)
+      const double f2 = 2.0 * Ft;
+      const double c0 = f2 * d0, c1 = f2 * d1, c2 = f2 * d2;
+      const double m0 = c0 + gp.exch(c0, 1), m1 = c1 + gp.exch(c1, 1), m2 = c2 + gp.exch(c2, 1);
+      if (act && (t & 1) == 0) {
+        const double q0 = rhol * m0, q1 = rhol * m1, q2 = rhol * m2;
+        v[4] = fma(m0, q0, v[4]);
+        v[5] = fma(m0, q1, v[5]);
+        v[6] = fma(m0, q2, v[6]);
+        v[7] = fma(m1, q1, v[7]);
+        v[8] = fma(m1, q2, v[8]);
+        v[9] = fma(m2, q2, v[9]);
+      }
+    }
+    // reduce-scatter: after the exchange across rank bit 1, ranks 0, 1 hold partial sums
+    // of v[0..4] and ranks 2, 3 of v[5..9]; after the one across bit 0 rank 0 holds the
+    // sums of v[0..2], rank 1 of v[3..4], rank 2 of v[5..7], rank 3 of v[8..9]
+    const bool h2 = (t & 2) != 0, h1 = (t & 1) != 0;
+    double k5[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      const double keep = h2 ? v[5 + s] : v[s];
+      const double send = h2 ? v[s] : v[5 + s];
+      k5[s] = keep + gp.exch(send, 2);
+    }
+    double k3[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const double hi = s < 2 ? k5[3 + s] : 0.0;
+      const double keep = h1 ? hi : k5[s];
+      const double send = h1 ? k5[s] : hi;
+      k3[s] = keep + gp.exch(send, 1);
+    }
+    const double Aw = gp.bcast(k3[0], 0), Bw = gp.bcast(k3[1], 0), CR = gp.bcast(k3[2], 0);
+    const double CI = gp.bcast(k3[0], 1), e00 = gp.bcast(k3[1], 1);
+    const double e01 = gp.bcast(k3[0], 2), e02 = gp.bcast(k3[1], 2), e11 = gp.bcast(k3[2], 2);
+    const double e12 = gp.bcast(k3[0], 3), e22 = gp.bcast(k3[1], 3);
+    // g_t = [t=0] 2 v_i Aw + [t=1] 2 v_j Bw + [t>=2] (weight of term t + 4)
+    //       + CR dwR/dx_t + CI dwI/dx_t,
+    // dwR/dx = (v_j cs, v_i cs, -wI, wI), dwI/dx = (v_j sn, v_i sn, wR, -wR)
+    const double vo = t == 0 ? vj : vi;
+    const double dRv = vo * cs, dIv = vo * sn;
+    const double dRt = t < 2 ? dRv : (t == 2 ? -wI : wI);
+    const double dIt = t < 2 ? dIv : (t == 2 ? wR : -wR);
+    const double ab = t == 0 ? Aw : Bw;
+    const double x2 = 2.0 * x[0];
+    const double base = t < 2 ? x2 * ab : tw2;
+    g[0] = base + CR * dRt + CI * dIt;
+    // second derivatives of w_i, w_j, wR, wI times (Aw, Bw, CR, CI):
+    //   (0,0) 2 Aw, (1,1) 2 Bw, (0,1) CR cs + CI sn,
+    //   (0,2) = -(0,3) = v_j gm, (1,2) = -(1,3) = v_i gm with gm = CI cs - CR sn,
+    //   (2,2) = (3,3) = -(2,3) = -(CR wR + CI wI)
+    const double q01 = CR * cs + CI * sn;
+    const double gm = CI * cs - CR * sn;
+    const double aj = vj * gm, ai = vi * gm;
+    const double bb = CR * wR + CI * wI;
+    // diagonal: the Gauss-Newton part of the pair terms t + 4 (rho (2 v)^2 for w_i, w_j;
+    // rho for the angles) plus the second-derivative entry
+    const double dterm = t < 2 ? rec[28 + t] * (x2 * x2) : rec[28 + t];
+    const double sdiag = (t < 2 ? 2.0 * ab : -bb) + dterm;
+    double gn[4], s2[4];
+    if (t == 0) {
+      gn[0] = e00; gn[1] = e01; gn[2] = e02; gn[3] = -e02;
+      s2[0] = sdiag; s2[1] = q01; s2[2] = aj; s2[3] = -aj;
+    } else if (t == 1) {
+      gn[0] = e01; gn[1] = e11; gn[2] = e12; gn[3] = -e12;
+      s2[0] = q01; s2[1] = sdiag; s2[2] = ai; s2[3] = -ai;
+    } else if (t == 2) {
+      gn[0] = e02; gn[1] = e12; gn[2] = e22; gn[3] = -e22;
+      s2[0] = aj; s2[1] = ai; s2[2] = sdiag; s2[3] = bb;
+    } else {
+      gn[0] = -e02; gn[1] = -e12; gn[2] = -e22; gn[3] = e22;
+      s2[0] = -aj; s2[1] = -ai; s2[2] = bb; s2[3] = sdiag;
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) H[4 * t + b] = gn[b] + s2[b];
+    gp.sync();
+  }
+
+  __device__ __forceinline__ double hq(int i, int j) const { return H[4 * i + j]; }
+  __device__ __forceinline__ double hd(int) const { return 0.0; }
+  // row i of H times v (v staged in shared memory)
+  __device__ __forceinline__ double row_dot(int i, SV<4> v) const {
+    double s = H[4 * i] * v[0];
+    s = fma(H[4 * i + 1], v[1], s);
+    s = fma(H[4 * i + 2], v[2], s);
+    return fma(H[4 * i + 3], v[3], s);
+  }
+
+  template <class GP>
+  __device__ __forceinline__ bool hess_finite(const GP& gp) const {
+    const int t = gp.t;
+    const bool fin = isfinite(H[4 * t]) && isfinite(H[4 * t + 1]) && isfinite(H[4 * t + 2]) &&
+                     isfinite(H[4 * t + 3]);
+    return !gp.any(!fin);
   }
 };
 

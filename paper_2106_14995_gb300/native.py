@@ -116,6 +116,7 @@ def load(build_if_missing: bool = True):
             "admm_pool_get_state": (I32, [P, I32, C.POINTER(AdmmStateView), P]),
             "admm_pool_set_state": (I32, [P, I32, C.POINTER(AdmmStateView), P]),
             "admm_pool_live": (I32, [P]),
+            "admm_pool_branch_group": (I32, [P]),
             "admm_pool_destroy": (None, [P]),
             "admm_mp_create": (I32, [C.POINTER(P), C.POINTER(AdmmNetwork), I32, P, P,
                                      C.c_double, C.POINTER(TronOptions), P]),

@@ -7,6 +7,7 @@ import pytest
 import oracle
 from paper_2106_14995_gb300 import synth
 from paper_2106_14995_gb300.admm import Admm, AdmmPool
+from paper_2106_14995_gb300.tron import options
 
 pytestmark = pytest.mark.gpu
 
@@ -16,10 +17,12 @@ def small_net(nb, seed):
                          rng=np.random.default_rng(seed))
 
 
-def test_admm_residual_trajectory_matches_oracle():
+@pytest.mark.parametrize("group", [1, 4])
+def test_admm_residual_trajectory_matches_oracle(group):
+    # group: lanes per branch problem in the branch launch (4 is the default)
     net = small_net(60, 3)
     K = 12
-    g = Admm(net)
+    g = Admm(net, opts=options(group=group))
     g.step(K)
     hp_g, hd_g = g.history(0, K)
     o = oracle.Admm(net)
@@ -33,6 +36,34 @@ def test_admm_residual_trajectory_matches_oracle():
     np.testing.assert_allclose(s["br_lam"], o.arrays["br_lam"], rtol=1e-6, atol=1e-5)
     np.testing.assert_allclose(s["gen_lam"], o.arrays["gen_lam"], rtol=1e-6, atol=1e-5)
     g.close()
+
+
+def test_branch_group_default_follows_branch_slots_per_sm():
+    # four lanes per branch problem while the pool holds <= 24 branch slots per SM
+    # sub-partition, else one; an explicit options.group wins; the default run equals
+    # the explicit run of the same mapping bit for bit
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    net = small_net(60, 3)
+    a = Admm(net)
+    b = Admm(net, opts=options(group=4))
+    assert a.branch_group == 4 and b.branch_group == 4
+    a.step(5)
+    b.step(5)
+    np.testing.assert_array_equal(a.history(0, 5)[0], b.history(0, 5)[0])
+    np.testing.assert_array_equal(a.get_state()["br_x"], b.get_state()["br_x"])
+    a.close()
+    b.close()
+    big = 24 * 4 * nsm + 128
+    p = AdmmPool(1000, big, 1000, 2)
+    assert p.branch_group == 1
+    p.close()
+    p = AdmmPool(1000, big, 1000, 2, opts=options(group=4))
+    assert p.branch_group == 4
+    p.close()
+    p = AdmmPool(1000, 24 * 4 * nsm, 1000, 2)
+    assert p.branch_group == 4
+    p.close()
 
 
 def test_admm_larger_network_tracks_oracle():

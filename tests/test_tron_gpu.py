@@ -118,19 +118,41 @@ def _branch_kkt(rec, x, l, u):
     return oracle.pgnorm(x, gr, l, u)
 
 
-def test_branch_parity_256():
-    d = synth.branch_batch(256, seed_index=0)
-    g = gpu_solve(d, n=4)
+@pytest.mark.parametrize("B,group", [(256, 1), (256, 4), (301, 4)])
+def test_branch_parity(B, group):
+    # group 1: one branch per lane; group 4: one per four lanes (301: a ragged last warp)
+    d = synth.branch_batch(B, seed_index=0)
+    g = gpu_solve(d, n=4, group=group)
     r = oracle_solve(d)
     assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
     assert np.all(r["status"] == oracle.CONVERGED)
     # the GPU result is a KKT point by the oracle's own gradient
-    for p in range(256):
+    for p in range(B):
         assert _branch_kkt(d["params"][p], g["x"][p], d["l"][p], d["u"][p]) <= 1e-6 * 1.01
     same = np.all(np.abs(g["x"] - r["x"]) <= 1e-6, axis=1)
-    assert same.mean() >= 0.98, f"{(~same).sum()} of 256 branch solutions differ"
+    assert same.mean() >= 0.98, f"{(~same).sum()} of {B} branch solutions differ"
     rel = np.abs(g["f"] - r["f"])[same] / np.maximum(1.0, np.abs(r["f"][same]))
     assert rel.max() <= 1e-8
+
+
+def test_branch_groups_agree_with_line_limits_active():
+    # tight line limits so the penalty of eq. exp-branch is active on many branches: the
+    # four-lane evaluator (reduce-scatter of the Gauss-Newton terms) and the one-lane one
+    # reach the same points, and both are KKT points by the oracle's gradient
+    d = synth.branch_batch(200, seed_index=83)
+    d["params"] = d["params"].copy()
+    d["params"][:, 32] *= 0.05
+    a = gpu_solve(d, n=4, group=1)
+    b = gpu_solve(d, n=4, group=4)
+    r = oracle_solve(d)
+    for g in (a, b):
+        assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
+        for p in range(200):
+            assert _branch_kkt(d["params"][p], g["x"][p], d["l"][p], d["u"][p]) <= 1e-6 * 1.01
+    same = np.all(np.abs(a["x"] - b["x"]) <= 1e-6, axis=1)
+    assert same.mean() >= 0.98
+    same_r = np.all(np.abs(b["x"] - r["x"]) <= 1e-6, axis=1)
+    assert same_r.mean() >= 0.98
 
 
 def test_hs45_gpu_matches_printed_solution():
@@ -187,10 +209,11 @@ def test_persistent_equals_plain_bitwise():
     for k in ("x", "f", "pg", "iters", "status", "delta"):
         np.testing.assert_array_equal(a[k], b[k])
     d = synth.branch_batch(300, seed_index=8)
-    a = gpu_solve(d, n=4)
-    b = gpu_solve(d, n=4, schedule=native.TRON_SCHED_PERSISTENT)
-    for k in ("x", "f", "pg", "iters", "status", "delta"):
-        np.testing.assert_array_equal(a[k], b[k])
+    for grp in (1, 4):
+        a = gpu_solve(d, n=4, group=grp)
+        b = gpu_solve(d, n=4, group=grp, schedule=native.TRON_SCHED_PERSISTENT)
+        for k in ("x", "f", "pg", "iters", "status", "delta"):
+            np.testing.assert_array_equal(a[k], b[k])
 
 
 @pytest.mark.parametrize("mixed", [False, True])
