@@ -39,7 +39,7 @@ FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.0
 # executes (thread-level DFMA x 2 + DADD + DMUL: 312.9 Mflop per 2,000 problems).
 TRAFFIC_BYTES_PER_PROBLEM = 19.05152e6 / 2000
 EXEC_FLOPS_PER_PROBLEM = 309.82e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "e5c63abf3a8ce4fa61a7c470dbd61c8a33ca3eeb"
+TRAFFIC_SOURCES_SHA1 = "2a3b8a4ade823fe020768f70675a5cf7452c51b6"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 

@@ -134,7 +134,7 @@ __device__ __forceinline__ void branch_update(const PoolDev& d, const tron_optio
     for (int q = 0; q < 8; ++q) {
       const double c = d.br_coef[8 * (size_t)k + q];
       const double l = d.br_lam[8 * (size_t)k + q];
-      fin = fin && isfinite(c) && isfinite(l);
+      fin = fin && finite_bits(c) && finite_bits(l);
       sv.obj.rec[q] = c;
       sv.obj.rec[8 + q] = l;
       sv.obj.rec[24 + q] = rho;
@@ -148,7 +148,7 @@ __device__ __forceinline__ void branch_update(const PoolDev& d, const tron_optio
     tg[7] = d.bus_th[j];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      fin = fin && isfinite(tg[q]);
+      fin = fin && finite_bits(tg[q]);
       sv.obj.rec[16 + q] = tg[q];
     }
     sv.obj.rec[32] = d.br_smax2[k];
@@ -182,7 +182,7 @@ __device__ __forceinline__ void branch_update(const PoolDev& d, const tron_optio
     for (int q = t; q < 8; q += 4) {
       const double c = d.br_coef[8 * (size_t)k + q];
       const double l = d.br_lam[8 * (size_t)k + q];
-      fin = fin && isfinite(c) && isfinite(l);
+      fin = fin && finite_bits(c) && finite_bits(l);
       sv.obj.rec[q] = c;
       sv.obj.rec[8 + q] = l;
       sv.obj.rec[24 + q] = rho;
@@ -190,7 +190,7 @@ __device__ __forceinline__ void branch_update(const PoolDev& d, const tron_optio
     const int bus = (t & 1) ? j : i;
     const double tg1 = d.br_tilde[4 * (size_t)k + t];
     const double tg2 = t < 2 ? d.bus_w[bus] : d.bus_th[bus];
-    fin = fin && isfinite(tg1) && isfinite(tg2);
+    fin = fin && finite_bits(tg1) && finite_bits(tg2);
     sv.obj.rec[16 + t] = tg1;
     sv.obj.rec[20 + t] = tg2;
     if (t == 0) sv.obj.rec[32] = d.br_smax2[k];

@@ -19,6 +19,17 @@
 
 namespace xt {
 
+// tests on the IEEE bit pattern, so they take no FP64 instruction (the FP64 unit is the
+// bottleneck of the solver): finite (exponent not all ones); nonzero (any bit but the
+// sign); positive (sign clear and nonzero; for a NaN with the sign clear as well)
+__device__ __forceinline__ bool finite_bits(double v) {
+  return (__double_as_longlong(v) & 0x7FF0000000000000LL) != 0x7FF0000000000000LL;
+}
+__device__ __forceinline__ bool nonzero_bits(double v) {
+  return (__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL) != 0;
+}
+__device__ __forceinline__ bool positive_bits(double v) { return __double_as_longlong(v) > 0; }
+
 template <int G>
 struct Grp {
   static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32 || G == 64 ||

@@ -62,10 +62,10 @@ struct DenseObj {
     bool fin = true;
     const int nn = n * n;
     if constexpr (QL == kQGlobal) {
-      for (int e = gp.t; e < nn; e += G) fin = fin && isfinite(__ldg(rec + e));
+      for (int e = gp.t; e < nn; e += G) fin = fin && finite_bits(__ldg(rec + e));
     } else if constexpr (QL == kQDiag) {
       // lane i gathers D_k[i] = Q(i, (i + k) mod n); entries outside n x n are zero
-      for (int e = gp.t; e < nn; e += G) fin = fin && isfinite(__ldg(rec + e));
+      for (int e = gp.t; e < nn; e += G) fin = fin && finite_bits(__ldg(rec + e));
       const int i = gp.t;
 #pragma unroll 4
       for (int k = 0; k <= N / 2; ++k) {
@@ -83,7 +83,7 @@ struct DenseObj {
       gp.sync();
       for (int e = gp.t; e < nn; e += G) {
         double v = __ldg(rec + e);
-        fin = fin && isfinite(v);
+        fin = fin && finite_bits(v);
         int i = e / n, j = e - i * n;
         Q[i * LDQ + j] = v;
       }
@@ -93,7 +93,7 @@ struct DenseObj {
       int i = r * G + gp.t;
       c[r] = (i < n) ? __ldg(rec + nn + i) : 0.0;
       d[r] = (i < n) ? __ldg(rec + nn + n + i) : 0.0;
-      fin = fin && isfinite(c[r]) && isfinite(d[r]);
+      fin = fin && finite_bits(c[r]) && finite_bits(d[r]);
       hdg[i] = 0.0;
     }
     gp.sync();
@@ -208,7 +208,7 @@ struct DenseObj {
   __device__ __forceinline__ bool hess_finite(const GP& gp) const {
     bool fin = true;
 #pragma unroll
-    for (int r = 0; r < R; ++r) fin = fin && isfinite(hdg[r * G + gp.t]);
+    for (int r = 0; r < R; ++r) fin = fin && finite_bits(hdg[r * G + gp.t]);
     return !gp.any(!fin);
   }
 };
@@ -253,7 +253,7 @@ struct BranchObj<1> {
 #pragma unroll
     for (int k = 0; k < 34; ++k) {
       double v = __ldg(src + k);
-      fin = fin && isfinite(v);
+      fin = fin && finite_bits(v);
       rec[k] = v;
     }
     return fin;
@@ -290,7 +290,7 @@ struct BranchObj<1> {
     for (int dir = 0; dir < 2; ++dir) {
       const double p2q2 = F[2 * dir] * F[2 * dir] + F[2 * dir + 1] * F[2 * dir + 1];
       const double m = p2q2 - smax2;
-      if (m > 0.0) {
+      if (positive_bits(m)) {
         val += 0.5 * rhol * m * m;
         mag += 0.5 * rhol * m * m + rhol * m * (p2q2 + smax2);
       }
@@ -346,7 +346,7 @@ struct BranchObj<1> {
       const int kp = 2 * dir, kq = 2 * dir + 1;
       const double p = F[kp], q = F[kq];
       const double m = p * p + q * q - smax2;
-      if (m > 0.0) {
+      if (positive_bits(m)) {
         // (rho_l/2) m^2: first-order weight rho_l m grad m, grad m = 2p dp + 2q dq;
         // second order rho_l (grad m grad m' + m (2 dp dp' + 2p H_p + 2 dq dq' + 2q H_q))
         t[kp] += rhol * m * 2.0 * p;
@@ -411,7 +411,7 @@ struct BranchObj<1> {
   __device__ __forceinline__ bool hess_finite(const Grp<1>&) const {
     bool fin = true;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) fin = fin && isfinite(H[e]);
+    for (int e = 0; e < 16; ++e) fin = fin && finite_bits(H[e]);
     return fin;
   }
 };
@@ -458,7 +458,7 @@ struct BranchObj<4> {
     bool fin = true;
     for (int k = gp.t; k < 34; k += 4) {
       const double v = __ldg(src + k);
-      fin = fin && isfinite(v);
+      fin = fin && finite_bits(v);
       rec[k] = v;
     }
     gp.sync();
@@ -472,7 +472,10 @@ struct BranchObj<4> {
     vi = gp.bcast(y[0], 0);
     vj = gp.bcast(y[0], 1);
     const double thi = gp.bcast(y[0], 2), thj = gp.bcast(y[0], 3);
-    sincos(thi - thj, &sn, &cs);
+    const double dth = thi - thj;
+    const double sc = sin((t & 1) ? dth + 1.5707963267948966 : dth);
+    sn = gp.bcast(sc, 0);
+    cs = gp.bcast(sc, 1);
     const double vv = vi * vj;
     wR = vv * cs;
     wI = vv * sn;
@@ -499,7 +502,7 @@ struct BranchObj<4> {
     const double p2q2 = __dadd_rn(sq, gp.exch(sq, 1));
     const double smax2 = rec[32], rhol = rec[33];
     mx = p2q2 - smax2;
-    if (mx > 0.0 && (t & 1) == 0) {
+    if (positive_bits(mx) && (t & 1) == 0) {
       val += 0.5 * rhol * mx * mx;
       mag += 0.5 * rhol * mx * mx + rhol * mx * (p2q2 + smax2);
     }
@@ -520,7 +523,7 @@ struct BranchObj<4> {
     double tw = rec[8 + t] + p1 * r1;                   // first-order weight of flow t
     const double tw2 = rec[12 + t] + rec[28 + t] * r2;  // of the pair term t + 4
     double W = p1;                                      // Gauss-Newton weight of flow t
-    const bool act = mx > 0.0;
+    const bool act = positive_bits(mx);
     if (act) {
       // (rho_l/2) m^2, m = p^2 + q^2 - smax^2: first-order weight 2 rho_l m F_t, and
       // 2 rho_l m on dF_t dF_t' (the rest, rho_l grad m grad m', below)
@@ -639,8 +642,8 @@ struct BranchObj<4> {
   template <class GP>
   __device__ __forceinline__ bool hess_finite(const GP& gp) const {
     const int t = gp.t;
-    const bool fin = isfinite(H[4 * t]) && isfinite(H[4 * t + 1]) && isfinite(H[4 * t + 2]) &&
-                     isfinite(H[4 * t + 3]);
+    const bool fin = finite_bits(H[4 * t]) && finite_bits(H[4 * t + 1]) && finite_bits(H[4 * t + 2]) &&
+                     finite_bits(H[4 * t + 3]);
     return !gp.any(!fin);
   }
 };
@@ -682,8 +685,8 @@ struct GenRampObj {
     const int t = gp.t;
     lam = t < n ? __ldg(rec + 8 + t) : 0.0;
     tgt = t < n ? __ldg(rec + 8 + n + t) : 0.0;
-    bool fin = isfinite(c2) && isfinite(c1) && isfinite(rho) && isfinite(rr) &&
-               isfinite(ramp) && isfinite(lam) && isfinite(tgt);
+    bool fin = finite_bits(c2) && finite_bits(c1) && finite_bits(rho) && finite_bits(rr) &&
+               finite_bits(ramp) && finite_bits(lam) && finite_bits(tgt);
     dg[t] = 0.0;
     sd[t] = 0.0;
     gp.sync();
@@ -706,8 +709,8 @@ struct GenRampObj {
       if (t >= 1) {
         const double d = p - pp;
         ex = fabs(d) - ramp;
-        sg = d > 0.0 ? 1.0 : -1.0;
-        if (ex > 0.0) {
+        sg = positive_bits(d) ? 1.0 : -1.0;
+        if (positive_bits(ex)) {
           val += 0.5 * rr * ex * ex;
           mag += 0.5 * rr * ex * ex + rr * ex * (fabs(p) + fabs(pp) + ramp);
         }
@@ -722,7 +725,7 @@ struct GenRampObj {
   template <class GP>
   __device__ __forceinline__ void grad_hess(const GP& gp, const double (&x)[R], double (&g)[R]) {
     const int t = gp.t;
-    const bool act = ex > 0.0;
+    const bool act = positive_bits(ex);
     const double w = act ? rr * ex * sg : 0.0;  // d/dp_t of the pair (t-1, t)
     const double wn = gp.from_next(w);          // the pair (t, t+1), from lane t+1
     const double an = gp.from_next(act ? 1.0 : 0.0);
@@ -731,7 +734,7 @@ struct GenRampObj {
     if (t < n) {
       const double p = x[0], r = p - tgt;
       gt = 2.0 * c2 * p + c1 + lam + rho * r + w - (has_next ? wn : 0.0);
-      dt = 2.0 * c2 + rho + (act ? rr : 0.0) + (has_next && an != 0.0 ? rr : 0.0);
+      dt = 2.0 * c2 + rho + (act ? rr : 0.0) + (has_next && nonzero_bits(an) ? rr : 0.0);
     }
     g[0] = gt;
     dg[t] = dt;
@@ -757,7 +760,7 @@ struct GenRampObj {
 
   template <class GP>
   __device__ __forceinline__ bool hess_finite(const GP& gp) const {
-    const bool fin = isfinite(dg[gp.t]) && isfinite(sd[gp.t]);
+    const bool fin = finite_bits(dg[gp.t]) && finite_bits(sd[gp.t]);
     return !gp.any(!fin);
   }
 };
@@ -815,7 +818,7 @@ struct Hs45Obj {
   __device__ __forceinline__ double hd(int) const { return 0.0; }
   __device__ __forceinline__ bool hess_finite(const Grp<1>&) const {
     bool fin = true;
-    for (int e = 0; e < n * N; ++e) fin = fin && isfinite(H[e]);
+    for (int e = 0; e < n * N; ++e) fin = fin && finite_bits(H[e]);
     return fin;
   }
 };

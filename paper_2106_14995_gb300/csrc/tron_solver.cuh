@@ -215,7 +215,7 @@ struct Solver {
       int cnt = 0;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        msk[r] = gp.ballot(v[r] != 0.0);
+        msk[r] = gp.ballot(nonzero_bits(v[r]));
         cnt += __popc(msk[r]);
       }
       if (cnt > N / 4) return false;
@@ -618,7 +618,7 @@ struct Solver {
       sn[r] = P(v, r) - x[r];
     }
     inside = gp.any(mv);
-    if (kap != 0.0) {
+    if (nonzero_bits(kap)) {
       bool both[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) both[r] = cn[r] || cl[r];
@@ -644,7 +644,7 @@ struct Solver {
   __device__ __forceinline__ bool all_finite(const double (&v)[R]) const {
     bool fin = true;
 #pragma unroll
-    for (int r = 0; r < R; ++r) fin = fin && isfinite(v[r]);
+    for (int r = 0; r < R; ++r) fin = fin && finite_bits(v[r]);
     return !gp.any(!fin);
   }
 
@@ -659,7 +659,7 @@ struct Solver {
     if constexpr (R != 1 || G == 1 || G > 32) {
       return false;
     } else {
-      if (wscale == 0.0 || gp.any(cn[0])) return false;
+      if (!nonzero_bits(wscale) || gp.any(cn[0])) return false;
       const bool bnd = cidx[0] < 0 && gp.t < n;
       unsigned mm = gp.ballot(bnd);
       if (__popc(mm) > 6) return false;
@@ -707,8 +707,8 @@ struct Solver {
     f = obj.eval_f(gp, x);
     double fs = obj.fsc;  // rounding scale of f at x
     obj.grad_hess(gp, x, g);
-    if (!params_finite || !isfinite(f) || !all_finite(g) || !obj.hess_finite(gp)) {
-      pg = isfinite(f) ? pgnorm(x, g) : CUDART_NAN;
+    if (!params_finite || !finite_bits(f) || !all_finite(g) || !obj.hess_finite(gp)) {
+      pg = finite_bits(f) ? pgnorm(x, g) : CUDART_NAN;
       return TRON_NONFINITE;
     }
     if (!(delta > 0.0)) {
@@ -920,7 +920,7 @@ struct Solver {
       // rho = (ared + fl) / (pred + fl) is compared with each eta as
       // ared + fl > eta (pred + fl), the denominator being positive: no division; an
       // invalid ratio (pred <= 0 or f(y) not finite) counts as -infinity
-      const bool valid = (okey(pred) > 0) && isfinite(fy) && isfinite(pred);
+      const bool valid = (okey(pred) > 0) && finite_bits(fy) && finite_bits(pred);
       const double num = ared + fl, den = pred + fl;
       const bool above0 = valid && lt(o.eta0 * den, num);
       const bool below1 = !valid || lt(num, o.eta1 * den);
