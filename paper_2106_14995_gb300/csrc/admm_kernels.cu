@@ -332,34 +332,64 @@ __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
       }
       const double dw2 = (w_new - w_old) * (w_new - w_old);
       const double dt2 = (th_new - th_old) * (th_new - th_old);
-#pragma unroll 2
-      for (int t = 0; t < en; ++t) {
-        const int e = d.end_list[e0 + t];
-        const size_t k = (size_t)(e >> 1);
-        const int side = e & 1;
-        const int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
-        double* lam = d.br_lam + 8 * k;
-        const double* val = d.br_val + 8 * k;
-        double* tl = d.br_tilde + 4 * k;
-        const double vp = val[kp], vq = val[kq], vw = val[kw], vt = val[kt];
-        const double lp = lam[kp], lq = lam[kq], lw = lam[kw], lt = lam[kt];
-        const double op = tl[kp], oq = tl[kq];
-        const double xp = fma(lp, irho, vp) + m1r;
-        const double xq = fma(lq, irho, vq) + m2r;
-        tl[kp] = xp;
-        tl[kq] = xq;
-        lam[kp] = fma(rho, vp - xp, lp);
-        lam[kq] = fma(rho, vq - xq, lq);
-        lam[kw] = fma(rho, vw - w_new, lw);
-        lam[kt] = fma(rho, vt - th_new, lt);
-        pr2 = fma(vp - xp, vp - xp, pr2);
-        du2 = fma(xp - op, xp - op, du2);
-        pr2 = fma(vq - xq, vq - xq, pr2);
-        du2 = fma(xq - oq, xq - oq, du2);
-        pr2 = fma(vw - w_new, vw - w_new, pr2);
-        du2 += dw2;
-        pr2 = fma(vt - th_new, vt - th_new, pr2);
-        du2 += dt2;
+      // the branch ends in batches of four: the four copies' loads first, then their
+      // updates and stores (a store may alias the next copy's loads as far as the
+      // compiler knows, so one copy at a time would wait out a memory latency per copy);
+      // the residual sums accumulate in the same order as one at a time
+      constexpr int kEB = 4;
+      for (int t0 = 0; t0 < en; t0 += kEB) {
+        size_t kk[kEB];
+        int kp[kEB];
+        double vp[kEB], vq[kEB], vw[kEB], vt[kEB], lp[kEB], lq[kEB], lw[kEB], lt[kEB];
+        double op[kEB], oq[kEB];
+#pragma unroll
+        for (int u = 0; u < kEB; ++u) {
+          if (t0 + u < en) {
+            const int e = d.end_list[e0 + t0 + u];
+            const size_t k = (size_t)(e >> 1);
+            const int side = e & 1;
+            const int p0 = side ? 2 : 0, kw = side ? 5 : 4, kt = side ? 7 : 6;
+            const double* val = d.br_val + 8 * k;
+            const double* lam = d.br_lam + 8 * k;
+            const double* tl = d.br_tilde + 4 * k;
+            kk[u] = k;
+            kp[u] = p0;
+            vp[u] = val[p0];
+            vq[u] = val[p0 + 1];
+            vw[u] = val[kw];
+            vt[u] = val[kt];
+            lp[u] = lam[p0];
+            lq[u] = lam[p0 + 1];
+            lw[u] = lam[kw];
+            lt[u] = lam[kt];
+            op[u] = tl[p0];
+            oq[u] = tl[p0 + 1];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kEB; ++u) {
+          if (t0 + u < en) {
+            const int p0 = kp[u], kw = p0 ? 5 : 4, kt = p0 ? 7 : 6;
+            double* lam = d.br_lam + 8 * kk[u];
+            double* tl = d.br_tilde + 4 * kk[u];
+            const double xp = fma(lp[u], irho, vp[u]) + m1r;
+            const double xq = fma(lq[u], irho, vq[u]) + m2r;
+            tl[p0] = xp;
+            tl[p0 + 1] = xq;
+            lam[p0] = fma(rho, vp[u] - xp, lp[u]);
+            lam[p0 + 1] = fma(rho, vq[u] - xq, lq[u]);
+            lam[kw] = fma(rho, vw[u] - w_new, lw[u]);
+            lam[kt] = fma(rho, vt[u] - th_new, lt[u]);
+            pr2 = fma(vp[u] - xp, vp[u] - xp, pr2);
+            du2 = fma(xp - op[u], xp - op[u], du2);
+            pr2 = fma(vq[u] - xq, vq[u] - xq, pr2);
+            du2 = fma(xq - oq[u], xq - oq[u], du2);
+            pr2 = fma(vw[u] - w_new, vw[u] - w_new, pr2);
+            du2 += dw2;
+            pr2 = fma(vt[u] - th_new, vt[u] - th_new, pr2);
+            du2 += dt2;
+          }
+        }
       }
       d.bus_w[b] = w_new;
       d.bus_th[b] = th_new;
