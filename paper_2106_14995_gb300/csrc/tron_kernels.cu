@@ -288,7 +288,18 @@ static KernelEntry* find_entry(int kind, int N, int G, int layout_opt = 0) {
       return &e;
   return nullptr;
 }
-static int default_group(int kind, int N) {
+// The default mapping of the branch problems follows the batch: four lanes per problem
+// while the class holds at most this many problems per SM sub-partition (the launch then
+// lasts as long as its slowest problem, whose serial chain four lanes shorten), one lane
+// per problem beyond (fewest FP64 instructions per problem).  Measured crossover of
+// cold-started branch batches: between 16,384 and 32,768 problems on 152 SMs.
+constexpr int64_t kG4BranchProblemsPerSmsp = 40;
+
+static int default_group(int kind, int N, int64_t count) {
+  if (kind == TRON_OBJ_ACOPF_BRANCH && N == 4) {
+    const int sms = device_sm_count();
+    return (sms > 0 && count > 0 && count <= kG4BranchProblemsPerSmsp * 4 * sms) ? 4 : 1;
+  }
   KernelEntry* e = find_entry(kind, N, 0);
   return e ? e->G : 1;
 }
@@ -535,7 +546,7 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
   }
   // resolve the kernels now so that a bad group option fails here
   for (auto& bk : b->buckets) {
-    const int G = o.group ? o.group : default_group(kind, bk.N);
+    const int G = o.group ? o.group : default_group(kind, bk.N, bk.count);
     if (!find_entry(kind, bk.N, G, o.layout)) {
       set_error("tron_batch_create: no kernel for kind %d, size class %d, group %d", (int)kind,
                 bk.N, G);
@@ -552,7 +563,7 @@ tron_err_t tron_batch_set_options(tron_batch_t* b, const tron_options_t* opt) {
   tron_err_t e = check_options(opt);
   if (e != TRON_OK) return e;
   for (auto& bk : b->buckets) {
-    const int G = opt->group ? opt->group : default_group(b->kind, bk.N);
+    const int G = opt->group ? opt->group : default_group(b->kind, bk.N, bk.count);
     XT_REQUIRE(find_entry(b->kind, bk.N, G, opt->layout), TRON_EUNSUPPORTED,
                "no kernel for kind %d, size class %d, group %d", (int)b->kind, bk.N, G);
   }
@@ -589,7 +600,7 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
       ke = bk.tuned;
       if (!b->opt.warps_per_block) wpb = bk.tuned_wpb;
     } else {
-      const int G = b->opt.group ? b->opt.group : default_group(b->kind, bk.N);
+      const int G = b->opt.group ? b->opt.group : default_group(b->kind, bk.N, bk.count);
       ke = find_entry(b->kind, bk.N, G, b->opt.layout);
     }
     XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d", bk.N);
@@ -673,7 +684,8 @@ tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t*
     ke = bk.tuned;
     if (!b->opt.warps_per_block) wpb = bk.tuned_wpb;
   } else {
-    ke = find_entry(b->kind, bk.N, b->opt.group ? b->opt.group : default_group(b->kind, bk.N),
+    ke = find_entry(b->kind, bk.N,
+                    b->opt.group ? b->opt.group : default_group(b->kind, bk.N, bk.count),
                     b->opt.layout);
   }
   XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d", bk.N);
@@ -1078,7 +1090,7 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
   for (int s = kNumClasses - 1; s >= 0; --s) {
     if (count[s] == 0) continue;
     const int N = kClasses[s];
-    const int G = o.group ? o.group : default_group(kind, N);
+    const int G = o.group ? o.group : default_group(kind, N, count[s]);
     KernelEntry* ke = find_entry(kind, N, G, o.layout);
     XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for kind %d, size class %d, group %d",
                (int)kind, N, G);

@@ -135,6 +135,20 @@ def test_branch_parity(B, group):
     assert rel.max() <= 1e-8
 
 
+def test_branch_default_group_follows_batch_size():
+    # the library's mapping of the branch problems: four lanes per problem up to 40
+    # problems per SM sub-partition, one lane beyond; an explicit group wins
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    lim = 40 * 4 * nsm
+    for B, want in ((256, 4), (lim, 4), (lim + 1, 1)):
+        tb = TronBatch(native.TRON_OBJ_ACOPF_BRANCH, B, n=4)
+        assert tb.choices()[0]["group"] == want, (B, tb.choices())
+        tb.close()
+    tb = TronBatch(native.TRON_OBJ_ACOPF_BRANCH, 256, n=4, opts=options(group=1))
+    assert tb.choices()[0]["group"] == 1
+    tb.close()
+
+
 def test_branch_groups_agree_with_line_limits_active():
     # tight line limits so the penalty of eq. exp-branch is active on many branches: the
     # four-lane evaluator (reduce-scatter of the Gauss-Newton terms) and the one-lane one
