@@ -311,21 +311,21 @@ struct BranchObj<1> {
     const double vv = vi * vj;
     const double wR = vv * cs, wI = vv * sn;
     const double wi = vi * vi, wj = vj * vj;
-    // derivatives of wR, wI (order v_i, v_j, th_i, th_j)
-    const double dR[4] = {vj * cs, vi * cs, -wI, wI};
-    const double dI[4] = {vj * sn, vi * sn, wR, -wR};
+    // derivatives of wR, wI along (v_i, v_j, theta_i); along theta_j they are minus the
+    // theta_i ones, and so are those of every flow
+    const double dR[3] = {vj * cs, vi * cs, -wI};
+    const double dI[3] = {vj * sn, vi * sn, wR};
     // coefficients (a, b, cR, cI) of the four flows
     const double co[4][4] = {{rec[0], 0.0, -rec[2], rec[3]},
                              {rec[1], 0.0, -rec[3], -rec[2]},
                              {0.0, rec[4], -rec[6], -rec[7]},
                              {0.0, rec[5], -rec[7], rec[6]}};
-    double dF[4][4];
+    double dF[4][3];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       dF[k][0] = co[k][0] * (2.0 * vi) + co[k][2] * dR[0] + co[k][3] * dI[0];
       dF[k][1] = co[k][1] * (2.0 * vj) + co[k][2] * dR[1] + co[k][3] * dI[1];
       dF[k][2] = co[k][2] * dR[2] + co[k][3] * dI[2];
-      dF[k][3] = co[k][2] * dR[3] + co[k][3] * dI[3];
     }
     double t[8], W[4];
     {
@@ -335,11 +335,9 @@ struct BranchObj<1> {
 #pragma unroll
       for (int k = 0; k < 4; ++k) W[k] = rec[24 + k];
     }
-    double Hm[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) Hm[a][b] = 0.0;
+    // the six distinct entries (0,0) (0,1) (0,2) (1,1) (1,2) (2,2) of the Hessian without
+    // the pair terms of the angles; the theta_j row follows by the sign rule above
+    double E00 = 0.0, E01 = 0.0, E02 = 0.0, E11 = 0.0, E12 = 0.0, E22 = 0.0;
     const double smax2 = rec[32], rhol = rec[33];
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
@@ -353,13 +351,18 @@ struct BranchObj<1> {
         t[kq] += rhol * m * 2.0 * q;
         W[kp] += 2.0 * rhol * m;
         W[kq] += 2.0 * rhol * m;
-        double gm[4];
+        double gm[3], ug[3];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) gm[a] = 2.0 * p * dF[kp][a] + 2.0 * q * dF[kq][a];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = a; b < 4; ++b) Hm[a][b] += rhol * gm[a] * gm[b];
+        for (int a = 0; a < 3; ++a) {
+          gm[a] = 2.0 * p * dF[kp][a] + 2.0 * q * dF[kq][a];
+          ug[a] = rhol * gm[a];
+        }
+        E00 = fma(gm[0], ug[0], E00);
+        E01 = fma(gm[0], ug[1], E01);
+        E02 = fma(gm[0], ug[2], E02);
+        E11 = fma(gm[1], ug[1], E11);
+        E12 = fma(gm[1], ug[2], E12);
+        E22 = fma(gm[2], ug[2], E22);
       }
     }
     // scalars multiplying grad/Hessian of w_i, w_j, wR, wI
@@ -373,37 +376,44 @@ struct BranchObj<1> {
     }
     g[0] = Aw * (2.0 * vi) + CR * dR[0] + CI * dI[0];
     g[1] = Bw * (2.0 * vj) + CR * dR[1] + CI * dI[1];
-    g[2] = CR * dR[2] + CI * dI[2] + t[6];
-    g[3] = CR * dR[3] + CI * dI[3] + t[7];
-    // Gauss-Newton part
+    const double c2 = CR * dR[2] + CI * dI[2];
+    g[2] = c2 + t[6];
+    g[3] = t[7] - c2;
+    // Gauss-Newton part sum_k W_k dF_k dF_k'
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = a; b < 4; ++b) Hm[a][b] += W[k] * dF[k][a] * dF[k][b];
-    Hm[0][0] += rec[28] * (2.0 * vi) * (2.0 * vi);
-    Hm[1][1] += rec[29] * (2.0 * vj) * (2.0 * vj);
-    Hm[2][2] += rec[30];
-    Hm[3][3] += rec[31];
-    // second derivatives of w_i, w_j, wR, wI
-    Hm[0][0] += 2.0 * Aw;
-    Hm[1][1] += 2.0 * Bw;
-    Hm[0][1] += CR * cs + CI * sn;
-    Hm[0][2] += -CR * vj * sn + CI * vj * cs;
-    Hm[0][3] += CR * vj * sn - CI * vj * cs;
-    Hm[1][2] += -CR * vi * sn + CI * vi * cs;
-    Hm[1][3] += CR * vi * sn - CI * vi * cs;
-    Hm[2][2] += -CR * wR - CI * wI;
-    Hm[2][3] += CR * wR + CI * wI;
-    Hm[3][3] += -CR * wR - CI * wI;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a; b < 4; ++b) {
-        H[a * 4 + b] = Hm[a][b];
-        H[b * 4 + a] = Hm[a][b];
-      }
+    for (int k = 0; k < 4; ++k) {
+      const double u0 = W[k] * dF[k][0], u1 = W[k] * dF[k][1], u2 = W[k] * dF[k][2];
+      E00 = fma(dF[k][0], u0, E00);
+      E01 = fma(dF[k][0], u1, E01);
+      E02 = fma(dF[k][0], u2, E02);
+      E11 = fma(dF[k][1], u1, E11);
+      E12 = fma(dF[k][1], u2, E12);
+      E22 = fma(dF[k][2], u2, E22);
+    }
+    // pair terms of w_i, w_j (rho (2 v)^2) and the second derivatives of w_i, w_j, wR, wI
+    E00 += rec[28] * (2.0 * vi) * (2.0 * vi) + 2.0 * Aw;
+    E11 += rec[29] * (2.0 * vj) * (2.0 * vj) + 2.0 * Bw;
+    E01 += CR * cs + CI * sn;
+    const double gmm = CI * cs - CR * sn;
+    E02 += vj * gmm;
+    E12 += vi * gmm;
+    E22 -= CR * wR + CI * wI;
+    H[0] = E00;
+    H[1] = E01;
+    H[2] = E02;
+    H[3] = -E02;
+    H[4] = E01;
+    H[5] = E11;
+    H[6] = E12;
+    H[7] = -E12;
+    H[8] = E02;
+    H[9] = E12;
+    H[10] = E22 + rec[30];  // pair terms of the angles: rho on the diagonal
+    H[11] = -E22;
+    H[12] = -E02;
+    H[13] = -E12;
+    H[14] = -E22;
+    H[15] = E22 + rec[31];
   }
 
   __device__ __forceinline__ double hq(int i, int j) const { return H[i * 4 + j]; }

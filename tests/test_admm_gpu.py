@@ -115,9 +115,9 @@ def test_admm_checkpoint_resume_is_bitwise():
     g2.close()
 
 
-def _alone(net, iters):
+def _alone(net, iters, group=0):
     p = AdmmPool(len(net["bus_pd"]) + 256, len(net["br_from"]) + 256,
-                 len(net["gen_bus"]) + 256, 1)
+                 len(net["gen_bus"]) + 256, 1, opts=options(group=group))
     i = p.add(net)
     p.step(iters)
     st = p.get_state(i)
@@ -126,9 +126,12 @@ def _alone(net, iters):
     return st, hist
 
 
-def test_pool_results_identical_alone_and_in_the_mix():
+@pytest.mark.parametrize("group", [4, 1])
+def test_pool_results_identical_alone_and_in_the_mix(group):
+    # both branch mappings: an instance's results do not depend on its co-residents
     nets = [small_net(40, 11), small_net(130, 12), small_net(25, 13), small_net(70, 14)]
-    pool = AdmmPool(4000, 4000, 2000, 4)
+    pool = AdmmPool(4000, 4000, 2000, 4, opts=options(group=group))
+    assert pool.branch_group == group
     a = pool.add(nets[0])
     pool.step(5)
     b = pool.add(nets[1])          # admitted while a is running
@@ -144,7 +147,7 @@ def test_pool_results_identical_alone_and_in_the_mix():
     sa2, sd = pool.get_state(a), pool.get_state(d)
     for net, st, iters in ((nets[0], sa, 17), (nets[1], sb, 12), (nets[2], sc, 9),
                            (nets[0], sa2, 21), (nets[3], sd, 4)):
-        ref, _ = _alone(net, iters)
+        ref, _ = _alone(net, iters, group)
         for k in ref:
             np.testing.assert_array_equal(st[k], ref[k], err_msg=k)
     assert pool.live == 3
