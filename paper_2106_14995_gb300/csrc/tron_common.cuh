@@ -54,10 +54,10 @@ struct Grp {
   }
   // two and three sums at once: the first butterfly level sends each lane the value
   // its partner does not keep, so both halves of the group reduce a different quantity
-  // and the remaining levels cost one addition for all of them (G = 32 and 16); the
-  // results are read back from the owning lanes, identical in every lane
+  // and the remaining levels cost one addition for all of them; the results are read
+  // back from the owning lanes, identical in every lane
   __device__ __forceinline__ void sum2(double& a, double& b) const {
-    if constexpr (G >= 16) {
+    if constexpr (G >= 2) {
       const bool hi = (t & (G / 2)) != 0;
       double keep = hi ? b : a, send = hi ? a : b;
       keep += __shfl_xor_sync(mask, send, G / 2, G);
@@ -71,22 +71,23 @@ struct Grp {
     }
   }
   __device__ __forceinline__ void sum3(double& a, double& b, double& c) const {
-    if constexpr (G == 32) {
-      // level 16: low half keeps (a, b), high half keeps (c, 0)
-      const bool hi = (t & 16) != 0;
+    if constexpr (G >= 4) {
+      // level G/2: the low half keeps (a, b), the high half (c, 0)
+      const bool hi = (t & (G / 2)) != 0;
       double k0 = hi ? c : a, k1 = hi ? 0.0 : b;
-      double s0 = hi ? a : c, s1 = hi ? b : 0.0;
-      k0 += __shfl_xor_sync(mask, s0, 16);
-      k1 += __shfl_xor_sync(mask, s1, 16);
-      // level 8: in each half, lanes with bit 3 clear keep k0, set keep k1
-      const bool b3 = (t & 8) != 0;
-      double keep = b3 ? k1 : k0, send = b3 ? k0 : k1;
-      keep += __shfl_xor_sync(mask, send, 8);
+      const double s0 = hi ? a : c, s1 = hi ? b : 0.0;
+      k0 += __shfl_xor_sync(mask, s0, G / 2, G);
+      k1 += __shfl_xor_sync(mask, s1, G / 2, G);
+      // level G/4: in each half, lanes with that bit clear keep k0, set keep k1
+      const bool b2 = (t & (G / 4)) != 0;
+      double keep = b2 ? k1 : k0;
+      const double send = b2 ? k0 : k1;
+      keep += __shfl_xor_sync(mask, send, G / 4, G);
 #pragma unroll
-      for (int o = 4; o > 0; o >>= 1) keep += __shfl_xor_sync(mask, keep, o);
-      a = __shfl_sync(mask, keep, 0);
-      b = __shfl_sync(mask, keep, 8);
-      c = __shfl_sync(mask, keep, 16);
+      for (int o = G / 8; o > 0; o >>= 1) keep += __shfl_xor_sync(mask, keep, o, G);
+      a = __shfl_sync(mask, keep, 0, G);
+      b = __shfl_sync(mask, keep, G / 4, G);
+      c = __shfl_sync(mask, keep, G / 2, G);
     } else {
       a = sum(a);
       sum2(b, c);
