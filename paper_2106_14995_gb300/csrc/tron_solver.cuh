@@ -810,7 +810,6 @@ struct Solver {
           rF[r] = (c < m) ? vb[Fi[c]] : 0.0;
         }
         gp.sync();
-        if (pass == 0) rF0 = dotv(rF, rF);  // squared
         const int fac = factor(m);
         if (fac == 0) {
           status = TRON_CHOL_FAIL;
@@ -887,10 +886,21 @@ struct Solver {
           if (cidx[r] >= 0) ss = fma(rv[r], rv[r], ss);
         }
         const bool newly_active = gp.any(na);
-        const double rFn2 = gp.sum(ss);
-        if (info == 2 || info == 3 || newly_active ||
-            rFn2 <= (o.cg_rtol * o.cg_rtol) * rF0)
-          break;
+        if (info == 2 || info == 3 || newly_active) break;
+        // ||rF||^2 after the pass against cg_rtol^2 ||rF||^2 before the first pass (both
+        // squared); the first pass reduces the two together, and neither is formed when
+        // the pass already ended on the boundary, on negative curvature or a new bound
+        double rFn2 = ss;
+        if (pass == 0) {
+          double r0 = 0.0;
+#pragma unroll
+          for (int r = 0; r < R; ++r) r0 = fma(rF[r], rF[r], r0);
+          gp.sum2(rFn2, r0);
+          rF0 = r0;
+        } else {
+          rFn2 = gp.sum(rFn2);
+        }
+        if (rFn2 <= (o.cg_rtol * o.cg_rtol) * rF0) break;
       }
       if (status == TRON_CHOL_FAIL) break;
 
