@@ -36,10 +36,10 @@ FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.0
 # From one ncu capture of the timed kernel (profiles/tron_dense32_n10000.md, 2,000
 # problems, scaled per problem to the launch), valid only for the kernel sources it was
 # taken on: DRAM bytes (19.05 MB per 2,000 problems) and the FP64 flops the kernel
-# executes (thread-level DFMA x 2 + DADD + DMUL: 312.9 Mflop per 2,000 problems).
-TRAFFIC_BYTES_PER_PROBLEM = 19.05152e6 / 2000
-EXEC_FLOPS_PER_PROBLEM = 309.82e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "2a3b8a4ade823fe020768f70675a5cf7452c51b6"
+# executes (thread-level DFMA x 2 + DADD + DMUL: 306.3 Mflop per 2,000 problems).
+TRAFFIC_BYTES_PER_PROBLEM = 19.053568e6 / 2000
+EXEC_FLOPS_PER_PROBLEM = 306.305e6 / 2000
+TRAFFIC_SOURCES_SHA1 = "3f511e3f5361013e9ac9d8684525a92ece0d37fc"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
