@@ -33,6 +33,20 @@ B_DEFAULT = 10000
 N_VARS = 32
 L2_BYTES = 129 * 2 ** 20
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+# algorithmic bytes of one n = 32 problem: record (Q, c, d), l, u, x0, delta in; x,
+# delta, f, pg (FP64) and iterations, status (int32) out
+ALG_BYTES_PER_PROBLEM = (8 * (N_VARS * N_VARS + 2 * N_VARS) + 3 * 8 * N_VARS + 8 +
+                         8 * N_VARS + 3 * 8 + 2 * 4)
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU model (MEASURED_PEAKS.json), else the
+    fallback of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 # From one ncu capture of the timed kernel (profiles/tron_dense32_n10000.md, 2,000
 # problems, scaled per problem to the launch), valid only for the kernel sources it was
 # taken on: DRAM bytes (19.05 MB per 2,000 problems) and the FP64 flops the kernel
@@ -198,8 +212,16 @@ def cpu_baseline(d, budget_s=12.0):
         if time.perf_counter() - t0 >= budget_s or reps >= 50:
             break
     dt = time.perf_counter() - t0
+    # one thread, on the first 2,000 problems
+    b1 = min(B, 2000)
+    t1 = time.perf_counter()
+    oracle.tron_batch(2, d["params"][:b1], d["l"][:b1], d["u"][:b1], d["x0"][:b1],
+                      d["delta0"][:b1], nthreads=1)
+    v1 = b1 / (time.perf_counter() - t1)
     return ({"value": B * reps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-             "sample": f"the full {B}-problem batch solved {reps} time(s) on {cores} threads"},
+             "sample": f"the full {B}-problem batch solved {reps} time(s) on {cores} threads",
+             "one_thread": {"value": v1, "unit": UNIT,
+                            "sample": f"the first {b1} problems on 1 thread"}},
             flops / B, r)
 
 
@@ -273,7 +295,7 @@ def bench_uneven(args, dev):
         if tune:
             tb.autotune(P, L, U, X0, D0, sample=8192)
         ts = []
-        for rep in range(4):
+        for rep in range(6):  # the first untimed, then the median of five
             x, de = X0.clone(), D0.clone()
             torch.cuda.synchronize(dev)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -469,6 +491,9 @@ def main():
     torch.cuda.synchronize(dev)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     ok = ok and bool((outs[0]["status"].cpu().numpy() == 0).all())
+    # share of the variables at a bound in the last solution
+    xa = xs[-1].cpu().numpy()
+    active = float(np.mean((xa <= d["l"]) | (xa >= d["u"])))
     total_ms = xdist.max_over_ranks(total_ms, device=dev)
     value = xdist.weak_scaling_throughput(B, world, args.steps, total_ms)
 
@@ -516,6 +541,7 @@ def main():
                               "last wave overlaps the next one's start); roofline launch "
                               "times are taken with launches one at a time"},
         "all_converged": ok,
+        "active_bound_fraction": active,
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -534,6 +560,10 @@ def main():
             "executed_flops_per_launch": ex,
             "executed_frac": (ex / (lms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS) if ex else None,
             "launch_ms_median": lms,
+            "hbm": {"achieved": ALG_BYTES_PER_PROBLEM * B / (lms * 1e-3) / 1e9,
+                    "peak": hbm_peak_gbs()[0], "peak_source": hbm_peak_gbs()[1],
+                    "unit": "GB/s",
+                    "frac": ALG_BYTES_PER_PROBLEM * B / (lms * 1e-3) / 1e9 / hbm_peak_gbs()[0]},
             "note": "FP64 CUDA-core pipe; peak from 2 DFMA/clk/SM x 152 SMs x 2.07 GHz; "
                     "achieved counts the oracle's algorithmic flops, executed_frac the "
                     "FP64 flops the kernel issues (ncu thread-level counts)"}
