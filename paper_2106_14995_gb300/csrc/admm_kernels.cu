@@ -4,9 +4,10 @@
 // One iteration = two launches, both over the pool's whole capacity:
 //   k_admm_branch_gen : generator updates (closed form) alongside the branch updates
 //                       (the branch NLP of eq. exp-branch solved by the TRON solver of
-//                       tron_solver.cuh, one branch per lane, warm started; the branch
-//                       record is gathered on the fly from the multipliers and the bus
-//                       copies, the pair values at the new point are written back)
+//                       tron_solver.cuh, four lanes or one lane per branch, warm
+//                       started; the branch record is gathered on the fly from the
+//                       multipliers and the bus copies, the pair values at the new
+//                       point are written back)
 //   k_admm_bus        : per bus, the closed-form equality-constrained QP over its copies
 //                       (power balance, eqs. PowerBalanceReal/Reactive), the multiplier
 //                       update of every pair it owns and the residual partial sums; the
@@ -96,7 +97,7 @@ struct PoolDev {
 struct AdmmArgs {
   PoolDev d;
   tron_options_t opt;
-  int32_t nbb;    // branch CTAs (warps_per_block warps of 32 branches each)
+  int32_t nbb;    // branch CTAs (warps_per_block warps of 32 / G branches each)
   int32_t ngb;    // generator CTAs
 };
 

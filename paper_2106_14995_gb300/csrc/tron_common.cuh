@@ -7,8 +7,10 @@
 // leaves the result in every lane and needs no broadcast step (Sec. 5.1, Figure 4).
 //
 // FP64 on this GPU: a warp-wide FP64 instruction costs the same issue slot whether one
-// lane or all 32 are active, so the mapping keeps lanes busy: G = 1 (one problem per
-// lane) for the 4-variable branch problems, G = 32 (one variable per lane) for n = 32.
+// lane or all 32 are active, so the mapping keeps lanes busy: G = 32 (one variable per
+// lane) for n = 32; for the 4-variable branch problems G = 1 (one problem per lane, the
+// fewest instructions) when they are many per SM, G = 4 when they are few (a launch then
+// lasts as long as its slowest problem, whose serial chain four lanes shorten).
 #pragma once
 
 #include <cuda_runtime.h>
