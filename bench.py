@@ -53,7 +53,7 @@ def hbm_peak_gbs():
 # executes (thread-level DFMA x 2 + DADD + DMUL: 306.3 Mflop per 2,000 problems).
 TRAFFIC_BYTES_PER_PROBLEM = 19.053568e6 / 2000
 EXEC_FLOPS_PER_PROBLEM = 306.305e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "0ed9a3dd377e4679918fc82c431777b178999b5c"
+TRAFFIC_SOURCES_SHA1 = "95ab09fc212d2899dc8ad912ec1400fd5d593795"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 

@@ -22,15 +22,19 @@
 namespace xt {
 
 // tests on the IEEE bit pattern, so they take no FP64 instruction (the FP64 unit is the
-// bottleneck of the solver): finite (exponent not all ones); nonzero (any bit but the
-// sign); positive (sign clear and nonzero; for a NaN with the sign clear as well)
+// bottleneck of the solver), each the same predicate as its comparison for every input,
+// NaN included: finite (exponent not all ones); nonzero (v != 0: any bit but the sign);
+// positive (v > 0: sign clear, nonzero, at most +infinity)
 __device__ __forceinline__ bool finite_bits(double v) {
   return (__double_as_longlong(v) & 0x7FF0000000000000LL) != 0x7FF0000000000000LL;
 }
 __device__ __forceinline__ bool nonzero_bits(double v) {
   return (__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL) != 0;
 }
-__device__ __forceinline__ bool positive_bits(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool positive_bits(double v) {
+  const long long b = __double_as_longlong(v);
+  return b > 0 && b <= 0x7FF0000000000000LL;
+}
 
 template <int G>
 struct Grp {

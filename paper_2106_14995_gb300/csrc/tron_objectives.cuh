@@ -3,7 +3,11 @@
 // Interface used by the solver (tron_solver.cuh):
 //   SMEM                doubles of per-problem shared memory the evaluator needs
 //   kHasHd              the Hessian is hq(i,j) + [i==j] hd(i)
-//   load(gp, rec, n)    stage the packed record; returns false if it holds a non-finite
+//   load(gp, rec, n)    stage the packed record; returns false when an entry that enters
+//                       f at every point is not finite (f is then not finite anywhere,
+//                       so the solve stops as TRON_NONFINITE); entries that enter f only
+//                       on part of the box (a penalty's limit and weight) are left to
+//                       the evaluation, as f itself decides there
 //   eval_f(gp, y)       f(y); caches what the gradient needs; sets fsc, the sum of the
 //                       magnitudes of the terms f is assembled from (its rounding scale)
 //   kStepEval           eval_f_step(gp, y, s, Hs) is available: f(y) at y = x + s from
@@ -253,7 +257,7 @@ struct BranchObj<1> {
 #pragma unroll
     for (int k = 0; k < 34; ++k) {
       double v = __ldg(src + k);
-      fin = fin && finite_bits(v);
+      if (k < 32) fin = fin && finite_bits(v);  // smax^2, rho_line: only where a line is over
       rec[k] = v;
     }
     return fin;
@@ -468,7 +472,7 @@ struct BranchObj<4> {
     bool fin = true;
     for (int k = gp.t; k < 34; k += 4) {
       const double v = __ldg(src + k);
-      fin = fin && finite_bits(v);
+      if (k < 32) fin = fin && finite_bits(v);  // smax^2, rho_line: only where a line is over
       rec[k] = v;
     }
     gp.sync();
@@ -695,8 +699,9 @@ struct GenRampObj {
     const int t = gp.t;
     lam = t < n ? __ldg(rec + 8 + t) : 0.0;
     tgt = t < n ? __ldg(rec + 8 + n + t) : 0.0;
-    bool fin = finite_bits(c2) && finite_bits(c1) && finite_bits(rho) && finite_bits(rr) &&
-               finite_bits(ramp) && finite_bits(lam) && finite_bits(tgt);
+    // rho_r and R enter f only where a ramp limit is exceeded
+    const bool fin = finite_bits(c2) && finite_bits(c1) && finite_bits(rho) &&
+                     finite_bits(lam) && finite_bits(tgt);
     dg[t] = 0.0;
     sd[t] = 0.0;
     gp.sync();
