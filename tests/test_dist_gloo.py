@@ -25,6 +25,29 @@ def test_shard_covers_everything_once():
         xdist.shard(10, 2, 2)
 
 
+def test_shard_by_cost_balances_mixed_sizes():
+    rng = np.random.default_rng(7)
+    n = rng.choice([4, 6, 8, 16, 32, 64, 128], size=5000,
+                   p=[0.4, 0.2, 0.15, 0.1, 0.08, 0.05, 0.02])
+    cost = n.astype(np.float64) ** 3
+    for world in (1, 2, 3, 8):
+        ranges = [xdist.shard_by_cost(cost, r, world) for r in range(world)]
+        assert ranges[0][0] == 0 and ranges[-1][1] == len(cost)
+        for (a0, a1), (b0, b1) in zip(ranges, ranges[1:]):
+            assert a1 == b0 and a1 >= a0
+        per = np.array([cost[a:b].sum() for a, b in ranges])
+        assert per.max() <= cost.sum() / world + cost.max()
+        # a count split of the same batch is far less even
+        cnt = np.array([cost[slice(*xdist.shard(len(cost), r, world))].sum()
+                        for r in range(world)])
+        assert per.max() - per.min() <= cnt.max() - cnt.min() + cost.max()
+    # zero or empty costs fall back to the count split
+    assert xdist.shard_by_cost(np.zeros(10), 1, 2) == xdist.shard(10, 1, 2)
+    assert xdist.shard_by_cost([], 0, 3) == (0, 0)
+    with pytest.raises(ValueError):
+        xdist.shard_by_cost([1.0, -1.0], 0, 2)
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
