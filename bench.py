@@ -560,6 +560,13 @@ def main():
             "executed_flops_per_launch": ex,
             "executed_frac": (ex / (lms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS) if ex else None,
             "launch_ms_median": lms,
+            # the timed region's launches back to back (one step's last wave overlapping
+            # the next one's start): the time each adds, not a launch's own duration
+            "overlapped": {"ms_per_launch": total_ms / args.steps,
+                           "achieved": flops_per_problem * B / (total_ms / args.steps * 1e-3)
+                           / 1e9,
+                           "frac": flops_per_problem * B / (total_ms / args.steps * 1e-3)
+                           / 1e9 / FP64_PEAK_GFLOPS},
             "hbm": {"achieved": ALG_BYTES_PER_PROBLEM * B / (lms * 1e-3) / 1e9,
                     "peak": hbm_peak_gbs()[0], "peak_source": hbm_peak_gbs()[1],
                     "unit": "GB/s",

@@ -295,11 +295,9 @@ static KernelEntry* find_entry(int kind, int N, int G, int layout_opt = 0) {
 // cold-started branch batches: between 16,384 and 32,768 problems on 152 SMs.
 constexpr int64_t kG4BranchProblemsPerSmsp = 40;
 
-static int default_group(int kind, int N, int64_t count) {
-  if (kind == TRON_OBJ_ACOPF_BRANCH && N == 4) {
-    const int sms = device_sm_count();
+static int default_group(int kind, int N, int64_t count, int sms) {
+  if (kind == TRON_OBJ_ACOPF_BRANCH && N == 4)
     return (sms > 0 && count > 0 && count <= kG4BranchProblemsPerSmsp * 4 * sms) ? 4 : 1;
-  }
   KernelEntry* e = find_entry(kind, N, 0);
   return e ? e->G : 1;
 }
@@ -546,7 +544,7 @@ tron_err_t tron_batch_create(tron_batch_t** out, tron_obj_t kind, int64_t nprob,
   }
   // resolve the kernels now so that a bad group option fails here
   for (auto& bk : b->buckets) {
-    const int G = o.group ? o.group : default_group(kind, bk.N, bk.count);
+    const int G = o.group ? o.group : default_group(kind, bk.N, bk.count, b->sms);
     if (!find_entry(kind, bk.N, G, o.layout)) {
       set_error("tron_batch_create: no kernel for kind %d, size class %d, group %d", (int)kind,
                 bk.N, G);
@@ -563,7 +561,7 @@ tron_err_t tron_batch_set_options(tron_batch_t* b, const tron_options_t* opt) {
   tron_err_t e = check_options(opt);
   if (e != TRON_OK) return e;
   for (auto& bk : b->buckets) {
-    const int G = opt->group ? opt->group : default_group(b->kind, bk.N, bk.count);
+    const int G = opt->group ? opt->group : default_group(b->kind, bk.N, bk.count, b->sms);
     XT_REQUIRE(find_entry(b->kind, bk.N, G, opt->layout), TRON_EUNSUPPORTED,
                "no kernel for kind %d, size class %d, group %d", (int)b->kind, bk.N, G);
   }
@@ -600,7 +598,8 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
       ke = bk.tuned;
       if (!b->opt.warps_per_block) wpb = bk.tuned_wpb;
     } else {
-      const int G = b->opt.group ? b->opt.group : default_group(b->kind, bk.N, bk.count);
+      const int G =
+          b->opt.group ? b->opt.group : default_group(b->kind, bk.N, bk.count, b->sms);
       ke = find_entry(b->kind, bk.N, G, b->opt.layout);
     }
     XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d", bk.N);
@@ -685,7 +684,8 @@ tron_err_t tron_batch_get_choice(const tron_batch_t* b, int32_t bucket, int32_t*
     if (!b->opt.warps_per_block) wpb = bk.tuned_wpb;
   } else {
     ke = find_entry(b->kind, bk.N,
-                    b->opt.group ? b->opt.group : default_group(b->kind, bk.N, bk.count),
+                    b->opt.group ? b->opt.group
+                                 : default_group(b->kind, bk.N, bk.count, b->sms),
                     b->opt.layout);
   }
   XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for size class %d", bk.N);
@@ -1090,7 +1090,7 @@ extern "C" tron_err_t tron_solve_mixed_noalloc(
   for (int s = kNumClasses - 1; s >= 0; --s) {
     if (count[s] == 0) continue;
     const int N = kClasses[s];
-    const int G = o.group ? o.group : default_group(kind, N, count[s]);
+    const int G = o.group ? o.group : default_group(kind, N, count[s], sms);
     KernelEntry* ke = find_entry(kind, N, G, o.layout);
     XT_REQUIRE(ke, TRON_EUNSUPPORTED, "no kernel for kind %d, size class %d, group %d",
                (int)kind, N, G);
