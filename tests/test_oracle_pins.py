@@ -440,6 +440,31 @@ def test_status_codes_for_bad_input():
     assert r["status"] == oracle.MAX_ITER and r["iters"] == 1
 
 
+def test_branch_entries_that_enter_f_only_past_the_line_limit():
+    # reading R19: an infinite or NaN line limit leaves the penalty off (m > 0 is false),
+    # so the solve is the one with a huge finite limit, bit for bit; an infinite line
+    # weight does not matter while no line is over; an infinite target makes f infinite
+    d = synth.branch_batch(6, seed_index=85)
+    base = d["params"].copy()
+    base[:, 32] = 1e300
+    ref = oracle.tron_batch(d["kind"], base, d["l"], d["u"], d["x0"], d["delta0"])
+    assert np.all(ref["status"] == oracle.CONVERGED)
+    for smax2 in (np.inf, np.nan):
+        p = base.copy()
+        p[:, 32] = smax2
+        r = oracle.tron_batch(d["kind"], p, d["l"], d["u"], d["x0"], d["delta0"])
+        np.testing.assert_array_equal(r["status"], ref["status"])
+        np.testing.assert_array_equal(r["x"], ref["x"])
+    p = base.copy()
+    p[:, 33] = np.inf
+    r = oracle.tron_batch(d["kind"], p, d["l"], d["u"], d["x0"], d["delta0"])
+    np.testing.assert_array_equal(r["x"], ref["x"])
+    p = base.copy()
+    p[0, 20] = np.inf
+    r = oracle.tron_batch(d["kind"], p, d["l"], d["u"], d["x0"], d["delta0"])
+    assert r["status"][0] == oracle.NONFINITE
+
+
 def test_newton_step_solves_an_interior_quadratic_in_one_iteration():
     """Strictly convex quadratic with its minimiser inside the box and a large radius:
     the Cauchy point, the complete factorization (Sec. 4.3: one PCG iteration) and the
