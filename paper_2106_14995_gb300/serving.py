@@ -28,10 +28,15 @@ def percentile(v, q):
 
 
 class AdmmServer:
+    """``pool``: an object with the ``AdmmPool`` calls the loop uses (add, step,
+    residuals, remove, get_state, close); by default a new ``AdmmPool`` of the given
+    capacities."""
+
     def __init__(self, cap_bus: int, cap_branch: int, cap_gen: int, cap_instances: int,
                  chunk: int = 8, tol: float = 1e-4, max_iters: int = 20000,
-                 history_len: int = 256, opts=None):
-        self.pool = AdmmPool(cap_bus, cap_branch, cap_gen, cap_instances, history_len, opts)
+                 history_len: int = 256, opts=None, pool=None):
+        self.pool = pool if pool is not None else AdmmPool(cap_bus, cap_branch, cap_gen,
+                                                           cap_instances, history_len, opts)
         self.chunk = int(chunk)
         self.tol = float(tol)
         self.max_iters = int(max_iters)
