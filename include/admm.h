@@ -115,7 +115,10 @@ void admm_destroy(admm_t* a);
 
 /* ------------------------------------------------- resident pool (continuous batching) */
 
-/* Capacities in slots; instances are placed in contiguous, 128-aligned ranges. */
+/* Capacities in slots; instances are placed in contiguous, 128-aligned ranges.  opt as
+ * for admm_create: with options.group = 0 the branch mapping follows the pool's branch
+ * slots per SM sub-partition (its capacity, not the instances live at a time), fixed for
+ * the pool's life, so an instance's results do not depend on its co-residents. */
 tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_branch,
                             int32_t cap_gen, int32_t cap_instances, int32_t history_len,
                             const tron_options_t* opt, void* stream);
