@@ -50,10 +50,10 @@ def hbm_peak_gbs():
 # From one ncu capture of the timed kernel (profiles/tron_dense32_n10000.md, 2,000
 # problems, scaled per problem to the launch), valid only for the kernel sources it was
 # taken on: DRAM bytes (19.05 MB per 2,000 problems) and the FP64 flops the kernel
-# executes (thread-level DFMA x 2 + DADD + DMUL: 306.3 Mflop per 2,000 problems).
-TRAFFIC_BYTES_PER_PROBLEM = 19.053568e6 / 2000
-EXEC_FLOPS_PER_PROBLEM = 306.305e6 / 2000
-TRAFFIC_SOURCES_SHA1 = "95ab09fc212d2899dc8ad912ec1400fd5d593795"
+# executes (thread-level DFMA x 2 + DADD + DMUL: 306.1 Mflop per 2,000 problems).
+TRAFFIC_BYTES_PER_PROBLEM = 19.057152e6 / 2000
+EXEC_FLOPS_PER_PROBLEM = 306.122e6 / 2000
+TRAFFIC_SOURCES_SHA1 = "d28f12055ee75dad48c2502909f7e882047d5ec3"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 

@@ -118,10 +118,11 @@ typedef struct tron_options {
   int32_t layout;         /* 0      kernel storage variant: 0 = library's choice, else
                                     1 + bits (bit 0: packed factor, bit 1: Q in global,
                                     bit 2: Q as wrapped diagonals, n <= 32 only)         */
-  int32_t cholesky;       /* 0      factorization form: 0 = per size class (right-looking
-                                    up to n = 32, left-looking above), 1 = left-looking
-                                    (Sec. 4.3), 2 = right-looking with the trailing update
-                                    spread over all lanes; both factor the same matrix as
+  int32_t cholesky;       /* 0      factorization form: 0 = the library's choice (right-
+                                    looking, or the autotuner's per size class), 1 = left-
+                                    looking (Sec. 4.3), 2 = right-looking with the trailing
+                                    update spread over all lanes (two columns per pass for
+                                    one problem per CTA); both factor the same matrix as
                                     Lu D Lu^T and agree to rounding                       */
   int32_t ctas_per_sm;    /* 0      persistent schedule: resident CTAs per SM (0 = as many
                                     as fit); fewer shorten each problem's time and so the

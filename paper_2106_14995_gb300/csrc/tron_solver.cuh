@@ -49,7 +49,10 @@ struct Solver {
   static constexpr int OFF_VB = OFF_L + LSZ;
   static constexpr int OFF_DINV = OFF_VB + N;
   static constexpr int OFF_FI = OFF_DINV + N;  // N ints (in N double slots)
-  static constexpr int OFF_OBJ = OFF_FI + N;
+  // a second staging vector for the two-column factorization pass of CTA groups
+  static constexpr int NVB2 = (G > 32) ? N : 0;
+  static constexpr int OFF_VB2 = OFF_FI + N;
+  static constexpr int OFF_OBJ = OFF_VB2 + NVB2;
   static constexpr int S_RAW = OFF_OBJ + Obj::SMEM;
   // problems of one warp start at banks that differ by G doubles (conflict-free when
   // several problems share a warp)
@@ -64,7 +67,7 @@ struct Solver {
   const tron_options_t& o;
   Obj obj;
   int n;
-  SV<G> Lm, vb, dinv;
+  SV<G> Lm, vb, dinv, vb2;
   SV<G, int> Fi;
   double l[R], u[R];
   long long kl[R], ku[R];  // integer keys of the bounds
@@ -76,6 +79,7 @@ struct Solver {
     Lm = sv.at(OFF_L);
     vb = sv.at(OFF_VB);
     dinv = sv.at(OFF_DINV);
+    vb2 = sv.at(OFF_VB2);
     Fi = SV<G, int>{(G == 1) ? reinterpret_cast<int*>(warp_smem + OFF_FI * 32) + gp.lane
                              : reinterpret_cast<int*>(base + OFF_FI)};
     obj.bind(sv.at(OFF_OBJ));
@@ -350,6 +354,13 @@ struct Solver {
     while ((cc0 + 1) * (cc0 + 2) / 2 <= gp.t) ++cc0;
     const int ec0 = gp.t - cc0 * (cc0 + 1) / 2;
     for (int j = 0; j < m; ++j) {
+      if constexpr (G > 32) {
+        if (j + 1 < m) {
+          if (!two_columns(j, m, cc0, ec0)) return false;
+          ++j;
+          continue;
+        }
+      }
       const double piv = lo(j, j);
       if (!positive(piv)) {
         gp.sync();
@@ -391,6 +402,75 @@ struct Solver {
       }
     }
     gp.sync();
+    return true;
+  }
+
+  // columns j and j + 1 of chol_right in one pass, for CTA groups, where each pass costs
+  // two CTA barriers: the owners of the rows below first apply column j to their entry
+  // of column j + 1 (which needs only Lu_{j+1,j} D_j, final when the pass starts), every
+  // lane forms the pivot of column j + 1 the same way, and one sweep over the trailing
+  // triangle applies column j and then column j + 1 to each element -- the operations of
+  // two one-column passes in the same order, so the factor is the same bit for bit
+  __device__ __forceinline__ bool two_columns(int j, int m, int cc0, int ec0) {
+    const double p0 = lo(j, j);
+    if (!positive(p0)) {
+      gp.sync();
+      return false;
+    }
+    const double r0 = pivot_rcp(p0);
+    const double a10 = lo(j + 1, j);
+    const double p1 = fma(-(a10 * r0), a10, lo(j + 1, j + 1));
+    if (!positive(p1)) {
+      gp.sync();
+      return false;
+    }
+    const double r1 = pivot_rcp(p1);
+    double lc0[R], lc1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = r * G + gp.t;
+      lc0[r] = 0.0;
+      lc1[r] = 0.0;
+      if (c > j && c < m) {
+        lc0[r] = lo(c, j) * r0;
+        vb[c] = lc0[r];
+        if (c > j + 1) {
+          const double a1 = fma(-lc0[r], a10, lo(c, j + 1));  // column j + 1 after column j
+          lo(c, j + 1) = a1;
+          lc1[r] = a1 * r1;
+          vb2[c] = lc1[r];
+        }
+      }
+    }
+    if (gp.t == (j & (G - 1))) dinv[j] = r0;
+    if (gp.t == ((j + 1) & (G - 1))) dinv[j + 1] = r1;
+    gp.sync();
+    const int M = m - j - 2;
+    const int T = M * (M + 1) / 2;
+    int cc = cc0, ec = ec0;
+    for (int e = gp.t; e < T; e += G) {
+      const int c = j + 2 + cc, d = j + 2 + ec;
+      lo(c, d) = fma(-vb2[c], lo(d, j + 1), fma(-vb[c], lo(d, j), lo(c, d)));
+      ec += G;
+      while (ec > cc) {
+        ec -= cc + 1;
+        ++cc;
+      }
+    }
+    gp.sync();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = r * G + gp.t;
+      if (c > j && c < m) {
+        lo(c, j) = lc0[r];
+        if (!PK) mt(j, c) = lc0[r];
+      }
+      if (c > j + 1 && c < m) {
+        lo(c, j + 1) = lc1[r];
+        if (!PK) mt(j + 1, c) = lc1[r];
+      }
+      if (c == j + 1) lo(c, c) = p1;
+    }
     return true;
   }
 
@@ -453,7 +533,7 @@ struct Solver {
       }
       gp.sync();
       // options.cholesky: 1 left-looking, 2 right-looking, 0 the size class's default
-      const bool right = (o.cholesky == 2) || (o.cholesky == 0 && N <= 32);
+      const bool right = o.cholesky != 1;
       if (right ? chol_right(m) : chol_left(m)) return alpha == 0.0 ? 1 : 2;
       if (!have_beta) shift_stats();
       alpha = fmax(2.0 * alpha, beta);
