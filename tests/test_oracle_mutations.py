@@ -78,6 +78,16 @@ MUTATIONS = [
      "rec[8 + T + t] = mp->states[t].gen_tilde[2 * g];",
      "rec[8 + T + t] = mp->states[t].gen_lam[2 * g];",
      [pins.test_multiperiod_admm_without_binding_ramps_equals_single_period_runs]),
+    ("line limit: a NaN excess counted as exceeded",
+     "    if (m > 0.0) {", "    if (!(m <= 0.0)) {",
+     [pins.test_branch_entries_that_enter_f_only_past_the_line_limit]),
+    ("acceptance: ratio test reversed",
+     "if (rho > o->eta0) {", "if (rho < o->eta0) {",
+     [pins.test_separable_quadratic_closed_form, pins.test_dense_convex_vs_lbfgsb]),
+    ("dense Hessian: quartic term halved",
+     "H[(size_t)i * n + i] += 12.0 * d[i] * x[i] * x[i];",
+     "H[(size_t)i * n + i] += 6.0 * d[i] * x[i] * x[i];",
+     [pins.test_dense_eval_closed_form]),
 ]
 
 
