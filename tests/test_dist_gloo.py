@@ -41,6 +41,15 @@ def test_shard_by_cost_balances_mixed_sizes():
         cnt = np.array([cost[slice(*xdist.shard(len(cost), r, world))].sum()
                         for r in range(world)])
         assert per.max() - per.min() <= cnt.max() - cnt.min() + cost.max()
+    # more ranks than problems, and one dominant problem: still contiguous and covering,
+    # each rank within one problem's cost of the mean
+    for costs, world in (([1, 1, 1], 8), ([5, 0, 0, 0], 3), ([0, 0, 7], 4),
+                         ([1e9, 1, 1, 1], 2)):
+        c = np.asarray(costs, dtype=float)
+        ranges = [xdist.shard_by_cost(c, r, world) for r in range(world)]
+        assert ranges[0][0] == 0 and ranges[-1][1] == len(c)
+        assert all(a1 == b0 for (_, a1), (b0, _) in zip(ranges, ranges[1:]))
+        assert max(c[a:b].sum() for a, b in ranges) <= c.sum() / world + c.max()
     # zero or empty costs fall back to the count split
     assert xdist.shard_by_cost(np.zeros(10), 1, 2) == xdist.shard(10, 1, 2)
     assert xdist.shard_by_cost([], 0, 3) == (0, 0)
