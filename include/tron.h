@@ -99,7 +99,8 @@ typedef struct tron_options {
   double eta0;            /* 1e-4   accept when rho > eta0                               */
   double eta1;            /* 0.25   shrink when rho < eta1                               */
   double eta2;            /* 0.75   expand when rho > eta2 and the step reached 0.99 delta */
-  double sigma1;          /* 0.25   shrink factor, delta = sigma1 * min(||s||, delta)    */
+  double sigma1;          /* 0.25   shrink factor, delta = sigma1 * min(||s||, delta)
+                                    (||s|| as measured by tr_norm)                       */
   double sigma3;          /* 4.0    expansion factor                                     */
   double delta_max;       /* 1e10   radius cap                                           */
   double delta_min_rel;   /* 1e-12  TR_TOO_SMALL threshold, times (1 + ||x||)            */
@@ -127,7 +128,15 @@ typedef struct tron_options {
   int32_t ctas_per_sm;    /* 0      persistent schedule: resident CTAs per SM (0 = as many
                                     as fit); fewer shorten each problem's time and so the
                                     launch's last-wave tail                                */
-  int32_t reserved[5];    /* must be zero                                                */
+  int32_t tr_norm;        /* 0      trust-region norm of the PCG step (Algorithm 1):
+                                    0 = the CG iterate s of the preconditioned system,
+                                    ||s||_2 = ||L^T w||_2 <= delta, as Algorithm 1 states; the
+                                    radius update then measures each piece of the step in
+                                    the norm that bounded it (the Cauchy step in ||.||_2,
+                                    each subspace search step beta w in ||L^T .||_2);
+                                    1 = the step itself, ||w||_2 <= delta, with the radius
+                                    update on ||x+ - x||_2                                 */
+  int32_t reserved[4];    /* must be zero                                                */
 } tron_options_t;
 
 typedef struct tron_batch tron_batch_t;
@@ -172,19 +181,28 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
                             int32_t* d_status, void* stream);
 
 /* Solve a batch of mixed sizes without allocating device memory.  (The paper has no
- * counterpart: this exists for callers that cannot call cudaMalloc — code running while
- * a CUDA graph is captured, hosts whose device memory all belongs to their own pool
- * allocator, loops that must not pay an allocation's implicit synchronisation.)
+ * counterpart.)  It exists for callers that must not allocate device memory from a
+ * library call: hosts whose device memory is all handed to their own pool allocator (a
+ * framework's caching allocator or a fixed arena), where a cudaMalloc beside the pool
+ * fails or fragments it, and processes run under a device-memory budget that library
+ * allocations would break.
  *
  * Same problem layout and device arrays as tron_batch_solve with per-problem sizes
  * n_host (host array [nprob]); opt may be NULL; the persistent schedule is always used.
  * The library keeps the size/offset tables, per-class problem lists and work counters
  * in one fixed device array of about 24 * TRON_NOALLOC_MAX_PROBLEMS bytes (6 MiB)
  * that every GPU loading the library reserves until the process exits; no call
- * allocates device memory (the tables are staged in host memory and copied in).
+ * allocates device memory.
  *  - nprob > TRON_NOALLOC_MAX_PROBLEMS is rejected with TRON_EINVAL.
  *  - The first call on a device looks up the array's device address once for that
- *    device; make that first call before any stream capture begins.
+ *    device (cudaGetSymbolAddress) and keeps it; make that first call before any stream
+ *    capture begins.  The kept address does not survive cudaDeviceReset of that device.
+ *  - The tables are built in host memory and copied in from pageable memory on
+ *    `stream`: such copies wait for the work already queued on the stream, so the call
+ *    returns only after that work has finished.
+ *  - The size classes are launched one after another on `stream` (tron_batch_solve
+ *    runs them concurrently on forked streams), so a batch of several classes takes
+ *    longer through this entry point.
  *  - Every call uses the same array: the counters are cleared and the tables rewritten
  *    by each call on `stream`, so calls on one stream are ordered, but calls that
  *    overlap on the GPU (other streams, other host threads) race and give wrong
@@ -261,6 +279,14 @@ const char* tron_last_error(void);
 
 /* Library version string. */
 const char* tron_version(void);
+
+/* Test hook of the factorization's pivot reciprocal (Sec. 4.3's factorization, computed
+ * here square-root free as Lu D Lu^T with one reciprocal per pivot): d_out[i] = the
+ * reciprocal of d_a[i] as the factorization forms it -- the hardware estimate refined by
+ * one Newton-Raphson step, IEEE division from 2^1022 up.  d_a, d_out: caller-owned
+ * device arrays of n doubles (n >= 0; positive normal values are the pivots it is made
+ * for).  Enqueued on `stream`; TRON_EINVAL for a null array with n > 0. */
+tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void* stream);
 
 #ifdef __cplusplus
 }

@@ -56,7 +56,7 @@ class Opts(C.Structure):
         ("eta0", C.c_double), ("eta1", C.c_double), ("eta2", C.c_double),
         ("sigma1", C.c_double), ("sigma3", C.c_double), ("delta_max", C.c_double),
         ("delta_min_rel", C.c_double), ("cg_rtol", C.c_double), ("shift_frac", C.c_double),
-        ("max_shift", C.c_int32), ("pad0", C.c_int32), ("ared_guard", C.c_double),
+        ("max_shift", C.c_int32), ("tr_norm", C.c_int32), ("ared_guard", C.c_double),
     ]
 
 
@@ -129,6 +129,8 @@ def _load(path: str):
                                         C.POINTER(Counters)]
             L.ot_eval.argtypes = [C.c_int, C.c_int, P, P, P, P, P]
             L.ot_eval.restype = C.c_int
+            L.ot_fscale.argtypes = [C.c_int, C.c_int, P, P]
+            L.ot_fscale.restype = C.c_double
             L.ot_chol_left.argtypes = [C.c_int, P, C.c_int]
             L.ot_chol_left.restype = C.c_int
             L.ot_chol_shifted.argtypes = [C.c_int, P, P, C.c_double, C.c_int, P]
@@ -138,7 +140,7 @@ def _load(path: str):
             L.ot_pgnorm.argtypes = [C.c_int, P, P, P, P]
             L.ot_pgnorm.restype = C.c_double
             L.ot_breakpt.argtypes = [C.c_int, P, P, P, P, P, P, P]
-            L.ot_steihaug.argtypes = [C.c_int, P, P, P, C.c_double, C.c_double, P, P]
+            L.ot_steihaug.argtypes = [C.c_int, P, P, P, C.c_double, C.c_double, C.c_int, P, P, P]
             L.ot_steihaug.restype = C.c_int
             L.ot_admm_init.argtypes = [C.POINTER(Net), C.POINTER(State)]
             L.ot_admm_run.argtypes = [C.POINTER(Net), C.POINTER(State), C.POINTER(Opts),
@@ -250,6 +252,14 @@ def eval_obj(kind: int, params, x):
     return float(f[0]), g, H
 
 
+def fscale(kind: int, params, x) -> float:
+    """The rounding scale S of f at x that guards the reduction ratio: the sum of the
+    magnitudes of the terms f is assembled from."""
+    x = _f64(x)
+    params = _f64(np.zeros(1) if params is None else params)
+    return float(lib().ot_fscale(kind, x.size, _p(params), _p(x)))
+
+
 def chol(A):
     """Left-looking Cholesky; returns the lower factor or None if not positive definite."""
     A = _f64(A).copy()
@@ -287,12 +297,18 @@ def breakpt(x, w, l, u):
     return int(nb[0]), float(bmin[0]), float(bmax[0])
 
 
-def steihaug(A, L, bhat, delta, rtol=0.1):
+def steihaug(A, L, bhat, delta, rtol=0.1, norm=0, with_len=False):
+    """Steihaug PCG; returns (w, info, iterations) or, with ``with_len``, also the
+    step's length in the bounded norm (||s|| for norm 0, ||w|| for norm 1)."""
     A, L, bhat = _f64(A), _f64(L), _f64(bhat)
     m = bhat.size
     s = np.zeros(m)
     it = np.zeros(1, dtype=np.int32)
-    info = lib().ot_steihaug(m, _p(A), _p(L), _p(bhat), float(delta), float(rtol), _p(s), _p(it))
+    tl = np.zeros(1)
+    info = lib().ot_steihaug(m, _p(A), _p(L), _p(bhat), float(delta), float(rtol), int(norm),
+                             _p(s), _p(it), _p(tl))
+    if with_len:
+        return s, int(info), int(it[0]), float(tl[0])
     return s, int(info), int(it[0])
 
 

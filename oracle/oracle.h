@@ -46,7 +46,9 @@ typedef struct ot_opts {
   double cg_rtol;               /* CG relative residual tolerance (footnote of Sec. 4.3) */
   double shift_frac;            /* Cholesky shift base, times max |A_ii| */
   int32_t max_shift;            /* Cholesky shift retries */
-  int32_t pad0;
+  int32_t tr_norm;              /* trust-region norm of the PCG step: 0 = the CG iterate s
+                                   of the preconditioned system, ||s|| = ||L^T w|| (Algorithm 1),
+                                   1 = the step itself, ||w|| */
   double ared_guard;            /* rounding guard of the ratio, times max(1, magnitude of the terms of f) */
 } ot_opts;
 
@@ -83,6 +85,10 @@ void ot_tron_batch(int kind, int64_t nprob, const int32_t* n, const int64_t* pof
 int ot_eval(int kind, int n, const double* params, const double* x, double* f, double* g,
             double* H);
 
+/* the rounding scale S of f at x used by the ratio's guard (reading R6): the sum of the
+ * magnitudes of the terms f is assembled from */
+double ot_fscale(int kind, int n, const double* params, const double* x);
+
 /* core operations exposed for unit tests */
 int ot_chol_left(int m, double* A, int lda);           /* in place, lower; 0 = ok */
 int ot_chol_shifted(int m, const double* A, double* L, double shift_frac, int max_shift,
@@ -92,7 +98,8 @@ double ot_pgnorm(int n, const double* x, const double* g, const double* l, const
 void ot_breakpt(int n, const double* x, const double* w, const double* l, const double* u,
                 int* nbrpt, double* brptmin, double* brptmax);
 int ot_steihaug(int m, const double* A, const double* L, const double* bhat, double delta,
-                double rtol, double* w, int* iters);  /* w = L^-T s */
+                double rtol, int norm, double* w, int* iters,
+                double* tr_len);  /* w = L^-T s; tr_len = ||s|| (norm 0) or ||w|| (1) */
 
 /* ---------------------------------------------------------------- ADMM (Sec. 6.1) */
 typedef struct ot_net {

@@ -50,7 +50,7 @@ void ot_default_opts(ot_opts* o) {
   o->cg_rtol = 0.1;
   o->shift_frac = 1e-3;
   o->max_shift = 30;
-  o->pad0 = 0;
+  o->tr_norm = 0;
   o->ared_guard = 1e-13;
 }
 
@@ -242,23 +242,31 @@ double ot_pgnorm(int n, const double* x, const double* g, const double* l, const
   return m;
 }
 
-/* Steihaug-Toint truncated CG on the preconditioned system (Alg. 1 lines 8-9, Sec. 3):
- * minimise 0.5 s'Ahat s + bhat's with Ahat = L^-1 A L^-T.  The trust region bounds the
- * step in the original variables, w = L^-T s, by ||w||_2 <= delta (trqsol of Figure 2
- * measures ||x + sigma w||_2); w is accumulated along the iterations as
+/* Steihaug-Toint truncated CG on the preconditioned system (Algorithm 1, Sec. 3):
+ * minimise 0.5 s'Ahat s + bhat's with Ahat = L^-1 A L^-T over the CG iterate s, whose
+ * back transform w = L^-T s is accumulated along the iterations as
  * w += alpha L^-T p, the L^-T p being the backward solve that Ahat p needs anyway.
+ * The trust region (norm == 0, the default) bounds the CG iterate itself, ||s||_2 <=
+ * delta, as Algorithm 1 states; since s = L^T w this is ||L^T w||_2 <= delta on the step.
+ * norm == 1 selects the other reading, ||w||_2 <= delta on the step in the original
+ * variables.  trqsol (Figure 2) is applied to the vectors the bound is stated on.
  * Stops after m iterations, at the boundary, on negative curvature, or when the residual
  * norm drops to rtol*||bhat||.  Returns 0 converged, 1 iteration cap, 2 boundary,
- * 3 negative curvature; w receives the step L^-T s. */
+ * 3 negative curvature; w receives the step L^-T s and *tr_len the length of the step
+ * in the bounded norm (||s||_2 or ||w||_2). */
 static int steihaug_c(int m, const double* A, const double* L, const double* bhat,
-                      double delta, double rtol, double* w, int* iters, ot_counters* c) {
-  double* res = (double*)malloc(sizeof(double) * (size_t)(5 * m + 8));
+                      double delta, double rtol, int norm, double* w, int* iters,
+                      double* tr_len, ot_counters* c) {
+  double* res = (double*)malloc(sizeof(double) * (size_t)(7 * m + 8));
   double* p = res + m;
   double* q = p + m;
   double* z = q + m;
   double* wn = z + m;
+  double* sv = wn + m;
+  double* sn = sv + m;
   for (int i = 0; i < m; i++) {
     w[i] = 0.0;
+    sv[i] = 0.0;
     res[i] = -bhat[i];
     p[i] = res[i];
   }
@@ -279,37 +287,48 @@ static int steihaug_c(int m, const double* A, const double* L, const double* bha
     if (c) c->cg_iters++;
     double kappa = dot(m, p, q, c);
     if (kappa <= 0.0) {
-      double sigma = trqsol_c(m, w, z, delta, c);
-      for (int i = 0; i < m; i++) w[i] += sigma * z[i];
+      double sigma = norm == 0 ? trqsol_c(m, sv, p, delta, c) : trqsol_c(m, w, z, delta, c);
+      for (int i = 0; i < m; i++) {
+        w[i] += sigma * z[i];
+        sv[i] += sigma * p[i];
+      }
       info = 3;
       break;
     }
     double alpha = rr / kappa;
-    for (int i = 0; i < m; i++) wn[i] = w[i] + alpha * z[i];
-    if (nrm2(m, wn, c) >= delta) {
-      double sigma = trqsol_c(m, w, z, delta, c);
-      for (int i = 0; i < m; i++) w[i] += sigma * z[i];
+    for (int i = 0; i < m; i++) {
+      wn[i] = w[i] + alpha * z[i];
+      sn[i] = sv[i] + alpha * p[i];
+    }
+    if (nrm2(m, norm == 0 ? sn : wn, c) >= delta) {
+      double sigma = norm == 0 ? trqsol_c(m, sv, p, delta, c) : trqsol_c(m, w, z, delta, c);
+      for (int i = 0; i < m; i++) {
+        w[i] += sigma * z[i];
+        sv[i] += sigma * p[i];
+      }
       info = 2;
       break;
     }
     for (int i = 0; i < m; i++) {
       w[i] = wn[i];
+      sv[i] = sn[i];
       res[i] -= alpha * q[i];
     }
     double rrn = dot(m, res, res, c);
     double beta = rrn / rr;
     rr = rrn;
     for (int i = 0; i < m; i++) p[i] = res[i] + beta * p[i];
-    if (c) c->flops += 6.0 * m + 2.0;
+    if (c) c->flops += (norm == 0 ? 8.0 : 6.0) * m + 2.0;
   }
   if (iters) *iters = it;
+  if (tr_len) *tr_len = nrm2(m, norm == 0 ? sv : w, c);
   free(res);
   return info;
 }
 
 int ot_steihaug(int m, const double* A, const double* L, const double* bhat, double delta,
-                double rtol, double* w, int* iters) {
-  return steihaug_c(m, A, L, bhat, delta, rtol, w, iters, NULL);
+                double rtol, int norm, double* w, int* iters, double* tr_len) {
+  return steihaug_c(m, A, L, bhat, delta, rtol, norm, w, iters, tr_len, NULL);
 }
 
 /* ------------------------------------------------------------------------ objectives */
@@ -601,6 +620,12 @@ int ot_eval(int kind, int n, const double* params, const double* x, double* f, d
   return eval_c(kind, n, params, x, f, g, H, NULL, NULL);
 }
 
+double ot_fscale(int kind, int n, const double* params, const double* x) {
+  double f, S = NAN;
+  if (eval_c(kind, n, params, x, &f, NULL, NULL, NULL, &S) != 0) return NAN;
+  return S;
+}
+
 static int all_finite(int n, const double* v) {
   for (int i = 0; i < n; i++)
     if (!isfinite(v[i])) return 0;
@@ -667,7 +692,7 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
   double alpha_c = 1.0;
 
   for (;;) {
-    /* Alg. 1 lines 1 and 11: convergence at x^k (Sec. 5.1) */
+    /* Algorithm 1: convergence at x^k (Sec. 5.1) */
     double pg = ot_pgnorm(n, x, g, l, u);
     if (pg <= o->gtol) {
       status = OT_CONVERGED;
@@ -680,7 +705,7 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
     k++;
     c->outer++;
 
-    /* ---- Alg. 1 line 4: Cauchy point x_c = P[x - alpha g] with a sufficient-decrease
+    /* ---- Algorithm 1, Cauchy point: x_c = P[x - alpha g] with a sufficient-decrease
      * search on q(s) = g's + 1/2 s'Hs: q(s) <= mu0 g's and ||s|| <= mu1 delta. */
     for (int i = 0; i < n; i++) mg[i] = -g[i];
     double alpha = alpha_c;
@@ -723,8 +748,16 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
     alpha_c = alpha;
     for (int i = 0; i < n; i++) y[i] = proj1(x[i] - alpha * g[i], l[i], u[i]);
     c->flops += 2.0 * n;
+    /* length of the step in the norms of the trust regions that bound its pieces: the
+     * Cauchy step in ||.||_2 here, each subspace pass's search step beta*w below in the
+     * PCG's norm (used by the radius update when tr_norm == 0) */
+    double nu = 0.0;
+    if (o->tr_norm == 0) {
+      for (int i = 0; i < n; i++) d[i] = y[i] - x[i];
+      nu = nrm2(n, d, c);
+    }
 
-    /* ---- Alg. 1 lines 5-10, repeated on the current face: free set, shifted complete
+    /* ---- Algorithm 1's subspace step, repeated on the current face: free set, shifted complete
      * Cholesky, Steihaug PCG, back transform, projected search.  r is the model gradient
      * g + H (y - x) at the current point y. */
     for (int i = 0; i < n; i++) s[i] = y[i] - x[i];
@@ -752,11 +785,12 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
       for (int a = 0; a < m; a++) bh[a] = rF[a];
       trsv_lower(m, L, bh, c);
       int cgit;
-      /* Alg. 1 lines 8-9: sh receives w_F = L^-T s */
-      int info = steihaug_c(m, A, L, bh, delta, o->cg_rtol, sh, &cgit, c);
+      /* Algorithm 1, PCG and back transform: sh receives w_F = L^-T s */
+      double trlen;
+      int info = steihaug_c(m, A, L, bh, delta, o->cg_rtol, o->tr_norm == 1 ? 1 : 0, sh, &cgit, &trlen, c);
       for (int i = 0; i < n; i++) w[i] = 0.0;
       for (int a = 0; a < m; a++) w[F[a]] = sh[a];
-      /* Alg. 1 line 10: projected search y+ = P[y + beta w], sufficient decrease of the
+      /* Algorithm 1, projected search: y+ = P[y + beta w], sufficient decrease of the
        * model: r'd + 1/2 d'Hd <= mu0 r'd with d = y+ - y, beta halved on failure */
       double beta = 1.0;
       int found = 0;
@@ -775,6 +809,7 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
         beta = beta * o->proj_shrink;
       }
       if (!found) break;
+      if (beta * trlen > nu) nu = beta * trlen;
       int newly_active = 0;
       for (int a = 0; a < m; a++) {
         int i = F[a];
@@ -806,7 +841,7 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
     double ared = f - fy;
     double fl = o->ared_guard * (fs > 1.0 ? fs : 1.0);
     double rho = (pred > 0.0 && isfinite(fy)) ? (ared + fl) / (pred + fl) : -INFINITY;
-    double snorm = nrm2(n, s, c);
+    double snorm = o->tr_norm == 0 ? nu : nrm2(n, s, c);
     c->flops += 5.0 + n;
     if (rho > o->eta0) {
       for (int i = 0; i < n; i++) x[i] = y[i];

@@ -358,6 +358,13 @@ static int64_t record_size(int kind, int n) {
   return 0;
 }
 
+namespace xt {
+__global__ void k_pivot_rcp(const double* a, double* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = pivot_rcp(a[i]);
+}
+}  // namespace xt
+
 static tron_err_t check_options(const tron_options_t* o) {
   XT_REQUIRE(o->max_outer >= 0 && o->max_trials >= 0 && o->max_shift >= 0, TRON_EINVAL,
              "negative iteration cap in options");
@@ -372,6 +379,7 @@ static tron_err_t check_options(const tron_options_t* o) {
   XT_REQUIRE(o->cholesky >= 0 && o->cholesky <= 2, TRON_EINVAL,
              "options.cholesky must be 0, 1 or 2");
   XT_REQUIRE(o->ctas_per_sm >= 0, TRON_EINVAL, "options.ctas_per_sm must be >= 0");
+  XT_REQUIRE(o->tr_norm == 0 || o->tr_norm == 1, TRON_EINVAL, "options.tr_norm must be 0 or 1");
   return TRON_OK;
 }
 
@@ -379,6 +387,18 @@ extern "C" {
 
 const char* tron_last_error(void) { return g_err.c_str(); }
 const char* tron_version(void) { return "exatron-gb300 0.1 (sm_103a, FP64)"; }
+
+tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void* stream) {
+  clear_error();
+  XT_REQUIRE(n >= 0, TRON_EINVAL, "tron_test_pivot_rcp: n < 0");
+  if (n == 0) return TRON_OK;
+  XT_REQUIRE(d_a && d_out, TRON_EINVAL, "tron_test_pivot_rcp: null device array");
+  const int64_t blocks = (n + 255) / 256;
+  XT_REQUIRE(blocks < (1ll << 31), TRON_EINVAL, "tron_test_pivot_rcp: n too large");
+  xt::k_pivot_rcp<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d_a, d_out, n);
+  XT_CUDA(cudaGetLastError());
+  return TRON_OK;
+}
 
 tron_err_t tron_options_default(tron_options_t* o) {
   XT_REQUIRE(o != nullptr, TRON_EINVAL, "tron_options_default: null pointer");
@@ -967,14 +987,15 @@ tron_err_t tron_batch_host_sync(tron_batch_t* b) {
 // --------------------------------------------------------------------------------------
 // Entry point that allocates nothing on the device.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being
-// captured, hosts whose device memory is all handed to their own pool allocator, and
-// real-time loops that must not hit the implicit synchronisation of an allocation.
+// Some callers must not allocate device memory from a library call: hosts whose device
+// memory is all handed to their own pool allocator (a cudaMalloc beside the pool fails
+// or fragments it) and processes run under a fixed device-memory budget.
 // tron_solve_mixed_noalloc serves them: it solves a batch of mixed sizes with the
 // persistent kernel, keeping the per-problem size/offset tables, the per-class problem
 // lists and the work counters in the fixed array below instead of in memory it would
 // otherwise allocate.  The array is reserved on every GPU that loads this library and
-// stays there until the process exits.
+// stays there until the process exits.  The size classes run one after another on the
+// caller's stream.
 // --------------------------------------------------------------------------------------
 namespace xt {
 
@@ -991,7 +1012,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 static std::mutex g_na_mu;
 static void* g_na_addr[256];  // device address of the array, per device ordinal
 
-// Device address of the array for the current device, looked up once per device.
+// Device address of the array for the current device, looked up once per device (a
+// cudaDeviceReset of that device invalidates the kept address).
 static tron_err_t noalloc_scratch(unsigned char** out) {
   int dev = 0;
   XT_CUDA(cudaGetDevice(&dev));

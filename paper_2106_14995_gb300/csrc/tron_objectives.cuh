@@ -1,4 +1,4 @@
-// tron_objectives.cuh -- device evaluators of f, grad f and the Hessian (Alg. 1 line 3).
+// tron_objectives.cuh -- device evaluators of f, grad f and the Hessian (Algorithm 1).
 //
 // Interface used by the solver (tron_solver.cuh):
 //   SMEM                doubles of per-problem shared memory the evaluator needs

@@ -2,12 +2,12 @@
 //
 // Per outer iteration, all on the device (Sec. 4.1: single kernel, no host traffic):
 //   projected-gradient max-norm test (Sec. 5.1) -> Cauchy point with the
-//   interpolation/extrapolation search (line 4) -> free set of the current point and
-//   gather of H_FF (line 5, Sec. 5.3) -> shifted complete factorization, left- or
-//   right-looking, with the factor mirrored into the upper triangle (lines 6-7,
-//   Sec. 4.3, 4.4) -> Steihaug PCG with the step kept inside ||w||_2 <= delta
-//   (lines 8-9) -> projected search (line 10) -> reduction ratio, acceptance and
-//   radius update.
+//   interpolation/extrapolation search -> free set of the current point and
+//   gather of H_FF (Sec. 5.3) -> shifted complete factorization, left- or
+//   right-looking, with the factor mirrored into the upper triangle (Sec. 4.3,
+//   4.4) -> Steihaug PCG with the CG iterate s = L^T w of the
+//   preconditioned system kept inside ||s||_2 <= delta -> back transform -> projected
+//   search -> reduction ratio, acceptance and radius update.
 //
 // Storage: the vectors of a problem are register arrays spread over the group (slot r
 // of lane t holds variable r*G + t); the factor (with its transpose mirrored) and the
@@ -275,15 +275,7 @@ struct Solver {
     return b >= 0x0010000000000000LL && b < 0x7FF0000000000000LL;
   }
 
-  // 1/d of a pivot: the hardware reciprocal approximation refined by one Newton-Raphson
-  // step y <- y + y (1 - d y), which squares its relative error; two FP64 instructions.
-  // Pivots from 2^1022 up (whose reciprocal the approximation flushes to zero) divide.
-  __device__ __forceinline__ static double pivot_rcp(double a) {
-    if (__double_as_longlong(a) >= 0x7FD0000000000000LL) return 1.0 / a;
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-    return fma(y, fma(-a, y, 1.0), y);
-  }
+  __device__ __forceinline__ static double pivot_rcp(double a) { return xt::pivot_rcp(a); }
 
   // ------------------------------------------------ LDL^T factorization (Sec. 4.3)
   // A = Lu D Lu^T with Lu unit lower triangular: the strictly lower part of the factor
@@ -579,6 +571,17 @@ struct Solver {
     }
   }
 
+  // trqsol (Figure 2) from the three inner products of x and p in the trust-region
+  // norm: sigma >= 0 with xx + 2 sigma xp + sigma^2 pp = delta^2 (the positive root,
+  // in the form without cancellation)
+  __device__ __forceinline__ static double trqsol3(double xp, double pp, double xx,
+                                                   double delta) {
+    const double dsq = delta * delta;
+    double rad = xp * xp + pp * (dsq - xx);
+    if (rad < 0.0) rad = 0.0;
+    rad = sqrt(rad);
+    return (xp >= 0.0) ? (dsq - xx) / (xp + rad) : (rad - xp) / pp;
+  }
   // trqsol (Figure 2): sigma >= 0 with ||x + sigma p||_2 = delta
   __device__ __forceinline__ double trqsol(const double (&x)[R], const double (&p)[R],
                                            double delta) const {
@@ -590,26 +593,34 @@ struct Solver {
       xtx = fma(x[r], x[r], xtx);
     }
     gp.sum3(ptx, ptp, xtx);
-    const double dsq = delta * delta;
-    double rad = ptx * ptx + ptp * (dsq - xtx);
-    if (rad < 0.0) rad = 0.0;
-    rad = sqrt(rad);
-    return (ptx >= 0.0) ? (dsq - xtx) / (ptx + rad) : (rad - ptx) / ptp;
+    return trqsol3(ptx, ptp, xtx, delta);
   }
 
-  // Steihaug PCG (lines 8-9) for min rF'w + 1/2 w'Aw, ||w||_2 <= delta, run in the step
-  // w itself with the preconditioner M = A + alpha I = L L^T.  With phat = L^T p and
-  // rhat = L^-1 res this is CG on Ahat = L^-1 A L^-T in s = L^T w step for step: the
-  // same step lengths (rhat'rhat = res'M^-1 res, phat'Ahat phat = p'Ap), the same exits
-  // and the same w, which the trust region bounds directly.  When alpha = 0, M = A and
-  // Ahat = I: the first step, of length 1 along M^-1 res, is the minimiser and leaves a
-  // zero residual, so it is taken without forming A p.
+  // Steihaug PCG of Algorithm 1 for min rF'w + 1/2 w'Aw inside the trust region, run in
+  // the step w itself with the preconditioner M = A + alpha I = L L^T.  With
+  // phat = L^T p and rhat = L^-1 res this is CG on Ahat = L^-1 A L^-T in s = L^T w step
+  // for step: the same step lengths (rhat'rhat = res'M^-1 res, phat'Ahat phat = p'Ap)
+  // and the same exits.  Algorithm 1's trust region bounds the CG iterate,
+  // ||s||_2 = ||w||_M <= delta (options.tr_norm 0); its M-inner products come from the
+  // recurrences of preconditioned CG, with no product by M:
+  //   ||w + alpha p||_M^2 = ww + 2 alpha wp + alpha^2 pp,
+  //   <w', p'>_M = beta (wp + alpha pp),   ||p'||_M^2 = res''M^-1 res' + beta^2 pp,
+  // which hold because res' is orthogonal to every earlier direction (w' lies in their
+  // span and M p' = res' + beta M p).  tr_norm 1 bounds ||w||_2 instead.  When alpha = 0,
+  // M = A and Ahat = I: the first step, of length 1 along M^-1 res, is the minimiser and
+  // leaves a zero residual, so it is taken without forming A p; its length is
+  // ||M^-1 res||_M^2 = res'M^-1 res.
   // Returns 0 converged, 1 iteration cap, 2 boundary, 3 negative curvature; wscale is
-  // sigma > 0 when w was taken that way (then A w = -sigma rF), else 0.
+  // sigma > 0 when w was taken that way (then A w = -sigma rF), else 0; tl2 is the
+  // squared length of w in the bounded norm (tr_norm 0; 0 with tr_norm 1).  With
+  // tr_norm 1 the three inner products are formed from w and p before each step, and
+  // the boundary test and trqsol use them as with tr_norm 0.
   __device__ __forceinline__ int steihaug(int m, double delta, bool exact,
                                           const double (&rF)[R], double (&w)[R],
-                                          double& wscale) {
+                                          double& wscale, double& tl2) {
     wscale = 0.0;
+    tl2 = 0.0;
+    const bool pre = (o.tr_norm == 0);
     double res[R], z[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -620,12 +631,13 @@ struct Solver {
     precond(m, z);
     const double dsq = delta * delta;
     if (exact) {
-      const double zz = dotv(z, z);
+      const double zz = pre ? dotv(res, z) : dotv(z, z);
       const bool bnd = le(dsq, zz);
       const double sg = bnd ? delta / sqrt(zz) : 1.0;
 #pragma unroll
       for (int r = 0; r < R; ++r) w[r] = sg * z[r];
       wscale = sg;  // A w = -sg rF
+      if (pre) tl2 = bnd ? dsq : zz;
       return bnd ? 2 : 0;
     }
     double p[R], q[R];
@@ -633,35 +645,42 @@ struct Solver {
     const double tol2 = (o.cg_rtol * o.cg_rtol) * rz;  // ||rhat|| <= cg_rtol ||rhat_0||, squared
 #pragma unroll
     for (int r = 0; r < R; ++r) p[r] = z[r];
+    // inner products of w and p in the bounded norm: by the recurrences (tr_norm 0), or
+    // formed from the vectors before each step (tr_norm 1)
+    double ww = 0.0, wp = 0.0, pp = rz;
     int info = 1;
     for (int it = 0; it < m; ++it) {
       if (rz <= tol2) {
         info = 0;
         break;
       }
+      if (!pre) {
+        ww = 0.0;
+        wp = 0.0;
+        pp = 0.0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          ww = fma(w[r], w[r], ww);
+          wp = fma(w[r], p[r], wp);
+          pp = fma(p[r], p[r], pp);
+        }
+        gp.sum3(ww, wp, pp);
+      }
       hv_free(m, p, q);
       const double kappa = dotv(p, q);
-      if (kappa <= 0.0) {
-        const double sg = trqsol(w, p, delta);
-#pragma unroll
-        for (int r = 0; r < R; ++r) w[r] = fma(sg, p[r], w[r]);
-        info = 3;
-        break;
-      }
       const double alpha = rz / kappa;
-      double wn[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) wn[r] = fma(alpha, p[r], w[r]);
-      if (dotv(wn, wn) >= dsq) {
-        const double sg = trqsol(w, p, delta);
+      // negative curvature, or the step leaves the region: to the boundary along p
+      if (kappa <= 0.0 || le(dsq, fma(alpha, fma(alpha, pp, 2.0 * wp), ww))) {
+        const double sg = trqsol3(wp, pp, ww, delta);
 #pragma unroll
         for (int r = 0; r < R; ++r) w[r] = fma(sg, p[r], w[r]);
-        info = 2;
+        info = (kappa <= 0.0) ? 3 : 2;
         break;
       }
+      ww = fma(alpha, fma(alpha, pp, 2.0 * wp), ww);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        w[r] = wn[r];
+        w[r] = fma(alpha, p[r], w[r]);
         res[r] = fma(-alpha, q[r], res[r]);
         z[r] = res[r];
       }
@@ -669,9 +688,12 @@ struct Solver {
       const double rzn = dotv(res, z);
       const double beta = rzn / rz;
       rz = rzn;
+      wp = beta * fma(alpha, pp, wp);
+      pp = fma(beta * beta, pp, rz);
 #pragma unroll
       for (int r = 0; r < R; ++r) p[r] = fma(beta, p[r], z[r]);
     }
+    if (pre) tl2 = (info >= 2) ? dsq : ww;
     return info;
   }
 
@@ -685,7 +707,7 @@ struct Solver {
   __device__ __forceinline__ bool cauchy_try(double alpha, const double (&x)[R],
                                              const double (&g)[R], double delta,
                                              double (&s)[R], double (&Hs)[R], bool (&cl)[R],
-                                             double kap, bool& inside) {
+                                             double kap, bool& inside, double& ssq) {
     double sn[R];
     bool cn[R];
     bool mv = false;
@@ -716,6 +738,7 @@ struct Solver {
       ss = fma(s[r], s[r], ss);
     }
     gp.sum3(gts, sHs, ss);
+    ssq = ss;
     const double q = gts + 0.5 * sHs;
     const double bound = o.mu1 * delta;
     return le(q, o.mu0 * gts) && le(ss, bound * bound);
@@ -819,23 +842,26 @@ struct Solver {
       }
       ++k;
 
-      // ---- Cauchy point (line 4)
+      // ---- Cauchy point
       double s[R], Hs[R];
       bool cl[R];
       double alpha = alpha_c;
       bool inside;
-      if (cauchy_try(alpha, x, g, delta, s, Hs, cl, 0.0, inside)) {
+      double ssc;  // squared length of the accepted Cauchy step
+      if (cauchy_try(alpha, x, g, delta, s, Hs, cl, 0.0, inside, ssc)) {
         double sb[R], Hsb[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           sb[r] = s[r];
           Hsb[r] = Hs[r];
         }
+        double ssb = ssc;
         for (int t = 0; t < o.max_trials; ++t) {
           if (!inside) break;  // alpha at or beyond the largest breakpoint
           const double a2 = alpha * o.extrapf;
-          if (!cauchy_try(a2, x, g, delta, s, Hs, cl, o.extrapf, inside)) break;
+          if (!cauchy_try(a2, x, g, delta, s, Hs, cl, o.extrapf, inside, ssc)) break;
           alpha = a2;
+          ssb = ssc;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             sb[r] = s[r];
@@ -847,12 +873,17 @@ struct Solver {
           s[r] = sb[r];
           Hs[r] = Hsb[r];
         }
+        ssc = ssb;
       } else {
         for (int t = 0; t < o.max_trials; ++t) {
           alpha = alpha * o.interpf;
-          if (cauchy_try(alpha, x, g, delta, s, Hs, cl, o.interpf, inside)) break;
+          if (cauchy_try(alpha, x, g, delta, s, Hs, cl, o.interpf, inside, ssc)) break;
         }
       }
+      // squared length of the step in the norms of the trust regions that bounded its
+      // pieces (tr_norm 0): the Cauchy step in ||.||_2, each subspace pass's search step
+      // beta w in the PCG's norm; the radius update measures the step by it
+      double nu2 = ssc;
       alpha_c = alpha;
       double y[R], rv[R];
 #pragma unroll
@@ -863,7 +894,7 @@ struct Solver {
         rv[r] = g[r] + Hs[r];
       }
 
-      // ---- subspace passes (lines 5-10)
+      // ---- subspace passes: free set, factorization, PCG, back transform, search
       double rF0 = 0.0;
       for (int pass = 0; pass < n; ++pass) {
         int cidx[R];
@@ -895,8 +926,8 @@ struct Solver {
           status = TRON_CHOL_FAIL;
           break;
         }
-        double wF[R], wscale;
-        const int info = steihaug(m, delta, fac == 1, rF, wF, wscale);
+        double wF[R], wscale, tl2;
+        const int info = steihaug(m, delta, fac == 1, rF, wF, wscale, tl2);
         // scatter w_F to the full direction w
 #pragma unroll
         for (int r = 0; r < R; ++r) vb[r * G + gp.t] = 0.0;
@@ -911,7 +942,7 @@ struct Solver {
 #pragma unroll
         for (int r = 0; r < R; ++r) w[r] = vb[r * G + gp.t];
         gp.sync();
-        // projected search from y along w (line 10)
+        // projected search from y along w
         double beta = 1.0;
         bool found = false;
         double yt[R], d[R], Hd[R];
@@ -956,6 +987,7 @@ struct Solver {
           beta = beta * o.proj_shrink;
         }
         if (!found) break;
+        nu2 = fmax(nu2, (beta * beta) * tl2);
         bool na = false;
         double ss = 0.0;
 #pragma unroll
@@ -1026,11 +1058,14 @@ struct Solver {
           break;
         }
       }
-      // (||s|| >= 0.99 delta compared squared; the norm itself only when it sets delta)
+      // the step's length: in the norms that bounded its pieces (tr_norm 0), or
+      // ||y - x||_2 (tr_norm 1); ||s|| >= 0.99 delta compared squared, the norm itself
+      // formed only when it sets delta
+      const double sl2 = (o.tr_norm == 0) ? nu2 : ss2;
       const double d99 = 0.99 * delta;
       if (below1) {
-        delta = o.sigma1 * fmin(sqrt(ss2), delta);
-      } else if (above2 && le(d99 * d99, ss2)) {
+        delta = o.sigma1 * fmin(sqrt(sl2), delta);
+      } else if (above2 && le(d99 * d99, sl2)) {
         delta = fmin(o.sigma3 * delta, o.delta_max);
       }
       // delta < c (1 + ||x||), decided without a square root:

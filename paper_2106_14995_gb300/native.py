@@ -34,7 +34,7 @@ class TronOptions(C.Structure):
         ("cg_rtol", C.c_double), ("shift_frac", C.c_double), ("max_shift", C.c_int32),
         ("group", C.c_int32), ("ared_guard", C.c_double), ("schedule", C.c_int32),
         ("warps_per_block", C.c_int32), ("layout", C.c_int32), ("cholesky", C.c_int32),
-        ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 5),
+        ("ctas_per_sm", C.c_int32), ("tr_norm", C.c_int32), ("reserved", C.c_int32 * 4),
     ]
 
 
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
             "tron_batch_destroy": (None, [P]),
             "tron_last_error": (C.c_char_p, []),
             "tron_version": (C.c_char_p, []),
+            "tron_test_pivot_rcp": (I32, [P, P, I64, P]),
             "admm_create": (I32, [C.POINTER(P), C.POINTER(AdmmNetwork), C.POINTER(TronOptions),
                                   P]),
             "admm_step": (I32, [P, I32, P, P, P]),

@@ -38,6 +38,45 @@ def test_admm_residual_trajectory_matches_oracle(group):
     g.close()
 
 
+@pytest.mark.parametrize("group", [1, 4])
+@pytest.mark.parametrize("nb,seed,K", [(120, 11, 600), (200, 12, 400)])
+def test_admm_long_trajectory_matches_oracle(group, nb, seed, K):
+    # past the start-up: the branch solves that need the most TRON iterations (and the
+    # Cholesky shifts and boundary steps of the PCG) come after the first hundred ADMM
+    # iterations; the residual histories must stay within 1e-6 relative of the
+    # oracle's at every iteration, not only at the first few
+    net = small_net(nb, seed)
+    g = Admm(net, opts=options(group=group))
+    g.step(K)
+    hp_g, hd_g = g.history(0, K)
+    o = oracle.Admm(net)
+    hp_o, hd_o = o.run(K, nthreads=8)
+    np.testing.assert_allclose(hp_g, hp_o, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(hd_g, hd_o, rtol=1e-6, atol=0)
+    s = g.get_state()
+    for k in ("br_x", "br_val", "br_tilde", "bus_w", "bus_th", "gen_pq", "gen_tilde"):
+        np.testing.assert_allclose(s[k], o.arrays[k], rtol=1e-6, atol=1e-8, err_msg=k)
+    g.close()
+
+
+def test_admm_2000_bus_trajectory_matches_oracle():
+    net = small_net(2000, 13)
+    K = 150
+    for group in (1, 4):
+        g = Admm(net, opts=options(group=group))
+        g.step(K)
+        hp_g, hd_g = g.history(0, K)
+        if group == 1:
+            o = oracle.Admm(net)
+            hp_o, hd_o = o.run(K, nthreads=8)
+        np.testing.assert_allclose(hp_g, hp_o, rtol=1e-6, atol=0)
+        np.testing.assert_allclose(hd_g, hd_o, rtol=1e-6, atol=0)
+        s = g.get_state()
+        np.testing.assert_allclose(s["br_x"], o.arrays["br_x"], rtol=1e-6, atol=1e-8)
+        np.testing.assert_allclose(s["bus_w"], o.arrays["bus_w"], rtol=1e-6, atol=1e-8)
+        g.close()
+
+
 def test_branch_group_default_follows_branch_slots_per_sm():
     # four lanes per branch problem while the pool holds <= 24 branch slots per SM
     # sub-partition, else one; an explicit options.group wins; the default run equals

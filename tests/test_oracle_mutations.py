@@ -88,6 +88,54 @@ MUTATIONS = [
      "H[(size_t)i * n + i] += 12.0 * d[i] * x[i] * x[i];",
      "H[(size_t)i * n + i] += 6.0 * d[i] * x[i] * x[i];",
      [pins.test_dense_eval_closed_form]),
+    ("radius update: expansion factor 2 instead of 4",
+     "o->sigma3 = 4.0;", "o->sigma3 = 2.0;",
+     [pins.test_cauchy_interpolation_preconditioned_boundary_and_expansion,
+      pins.radius_update_all_cases]),
+    ("radius update: shrink factor 0.5 instead of 0.25",
+     "o->sigma1 = 0.25;", "o->sigma1 = 0.5;",
+     [pins.test_radius_shrinks_to_a_quarter_of_the_shorter_of_step_and_radius]),
+    ("radius update: shrink ignores the step length",
+     "delta = o->sigma1 * (snorm < delta ? snorm : delta);", "delta = o->sigma1 * delta;",
+     [pins.test_radius_shrinks_to_a_quarter_of_the_shorter_of_step_and_radius]),
+    ("radius update: eta2 test on the wrong side",
+     "} else if (rho > o->eta2 && snorm >= 0.99 * delta) {",
+     "} else if (rho < o->eta2 && snorm >= 0.99 * delta) {",
+     [pins.radius_update_all_cases]),
+    ("radius update: expansion needs the full radius",
+     "} else if (rho > o->eta2 && snorm >= 0.99 * delta) {",
+     "} else if (rho > o->eta2 && snorm >= 1.0 * delta) {",
+     [pins.radius_update_all_cases]),
+    ("radius update: step measured in the Euclidean norm under the PCG's norm",
+     "double snorm = o->tr_norm == 0 ? nu : nrm2(n, s, c);", "double snorm = nrm2(n, s, c);",
+     [pins.test_cauchy_interpolation_preconditioned_boundary_and_expansion]),
+    ("Cauchy search: extrapolation factor 5 instead of 10",
+     "o->extrapf = 10.0;", "o->extrapf = 5.0;",
+     [pins.test_cauchy_extrapolation_stops_at_the_largest_breakpoint]),
+    ("Cauchy search: interpolation factor 0.2 instead of 0.1",
+     "o->interpf = 0.1;", "o->interpf = 0.2;",
+     [pins.test_cauchy_interpolation_preconditioned_boundary_and_expansion]),
+    ("Cauchy search: extrapolation does not stop at the largest breakpoint",
+     "if (!(alpha < bmax)) break;", "if (!(alpha < 1e300)) break;",
+     [pins.test_cauchy_extrapolation_stops_at_the_largest_breakpoint]),
+    ("Cauchy search: alpha restarts at 1 every iteration",
+     "    alpha_c = alpha;\n", "    alpha_c = 1.0;\n",
+     [pins.test_cauchy_alpha_persists_between_iterations]),
+    ("projected search: step quartered instead of halved",
+     "o->proj_shrink = 0.5;", "o->proj_shrink = 0.25;",
+     [pins.test_projected_search_halves_the_step_until_the_model_decreases]),
+    ("PCG: boundary tested on w instead of the CG iterate",
+     "if (nrm2(m, norm == 0 ? sn : wn, c) >= delta) {", "if (nrm2(m, wn, c) >= delta) {",
+     [pins.test_steihaug_one_iteration_on_pd,
+      pins.test_cauchy_interpolation_preconditioned_boundary_and_expansion]),
+    ("ratio guard: scaled by |f| instead of the magnitude of the terms",
+     "double fl = o->ared_guard * (fs > 1.0 ? fs : 1.0);",
+     "double fl = o->ared_guard * (fabs(f) > 1.0 ? fabs(f) : 1.0);",
+     [pins.test_branch_solves_at_an_admm_state_all_converge]),
+    ("guard scale: the branch flows' own terms left out",
+     "mag += fabs(lam[k] * r) + 0.5 * rh[k] * r * r + (fabs(lam[k]) + rh[k] * fabs(r)) * M[k];",
+     "mag += fabs(lam[k] * r) + 0.5 * rh[k] * r * r;",
+     [pins.test_guard_scale_is_the_magnitude_of_the_terms_of_f]),
 ]
 
 

@@ -116,17 +116,62 @@ def test_steihaug_one_iteration_on_pd():
     assert alpha == 0.0
     r = rng.standard_normal(m)
     bhat = np.linalg.solve(np.tril(L), r)
-    w, info, it = oracle.steihaug(A, L, bhat, delta=1e6)
-    assert it == 1 and info in (0, 1)
-    np.testing.assert_allclose(w, -np.linalg.solve(A, r), rtol=1e-9, atol=1e-12)
-    # boundary: the step is the Newton direction cut at ||w|| = delta
     newton = -np.linalg.solve(A, r)
-    delta = 0.3 * np.linalg.norm(newton)
-    w2, info2, _ = oracle.steihaug(A, L, bhat, delta=delta)
+    for norm in (0, 1):
+        w, info, it = oracle.steihaug(A, L, bhat, delta=1e6, norm=norm)
+        assert it == 1 and info in (0, 1)
+        np.testing.assert_allclose(w, newton, rtol=1e-9, atol=1e-12)
+    # boundary, as Algorithm 1 prints it (norm 0): the CG iterate s = L^T w is bounded,
+    # ||s||^2 = w'(L L^T)w = w'Aw = delta^2; the step is the Newton direction cut there
+    delta = 0.3 * np.sqrt(newton @ A @ newton)
+    w2, info2, _, tl = oracle.steihaug(A, L, bhat, delta=delta, norm=0, with_len=True)
     assert info2 == 2
-    assert abs(np.linalg.norm(w2) - delta) < 1e-12 * delta
+    assert abs(np.sqrt(w2 @ A @ w2) - delta) < 1e-12 * delta
+    assert abs(tl - delta) < 1e-12 * delta
     np.testing.assert_allclose(w2 / np.linalg.norm(w2), newton / np.linalg.norm(newton),
                                rtol=1e-9, atol=1e-12)
+    # a radius between the two lengths of the Newton step, ||w||_2 < delta < ||L^T w||
+    # (A's eigenvalues are >= 1, so ||L^T w|| >= ||w||): inside for one norm, outside
+    # for the other
+    wl, sl = np.linalg.norm(newton), np.sqrt(newton @ A @ newton)
+    assert wl < 0.9 * sl
+    delta = np.sqrt(wl * sl)
+    w4, info4, _ = oracle.steihaug(A, L, bhat, delta=delta, norm=0)
+    assert info4 == 2 and abs(np.sqrt(w4 @ A @ w4) - delta) < 1e-12 * delta
+    w5, info5, _ = oracle.steihaug(A, L, bhat, delta=delta, norm=1)
+    assert info5 in (0, 1)
+    np.testing.assert_allclose(w5, newton, rtol=1e-9, atol=1e-12)
+    # the other reading (norm 1): the step itself is bounded, ||w||_2 = delta
+    delta = 0.3 * np.linalg.norm(newton)
+    w3, info3, _, tl = oracle.steihaug(A, L, bhat, delta=delta, norm=1, with_len=True)
+    assert info3 == 2
+    assert abs(np.linalg.norm(w3) - delta) < 1e-12 * delta
+    assert abs(tl - delta) < 1e-12 * delta
+    np.testing.assert_allclose(w3 / np.linalg.norm(w3), newton / np.linalg.norm(newton),
+                               rtol=1e-9, atol=1e-12)
+
+
+def test_steihaug_preconditioned_norm_with_a_shift():
+    # an indefinite A factored with a shift: the bound of Algorithm 1 is ||L^T w||_2 with
+    # L L^T = A + alpha I, i.e. w'(A + alpha I)w = delta^2 at the boundary, not w'Aw
+    rng = np.random.default_rng(11)
+    m = 6
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    A = Q @ np.diag([5.0, 3.0, 2.0, 1.0, 0.5, -0.2]) @ Q.T
+    L, alpha = oracle.chol_shifted(A)
+    assert alpha > 0.0
+    M = A + alpha * np.eye(m)
+    np.testing.assert_allclose(np.tril(L) @ np.tril(L).T, M, rtol=1e-12, atol=1e-12)
+    r = rng.standard_normal(m)
+    bhat = np.linalg.solve(np.tril(L), r)
+    for delta in (0.05, 0.3, 2.0):
+        w, info, it, tl = oracle.steihaug(A, L, bhat, delta=delta, norm=0, with_len=True)
+        assert np.sqrt(w @ M @ w) <= delta * (1 + 1e-12)
+        assert abs(tl - np.sqrt(w @ M @ w)) < 1e-12 * max(1.0, tl)
+        if info in (2, 3):
+            assert abs(np.sqrt(w @ M @ w) - delta) < 1e-11 * delta
+        # a descent step of the model r'w + 1/2 w'Aw
+        assert r @ w + 0.5 * w @ A @ w < 0.0
 
 
 def test_steihaug_negative_curvature_goes_to_boundary():
@@ -757,3 +802,168 @@ def test_multiperiod_admm_generator_step_satisfies_chain_kkt():
         lo = np.full(6, net["gen_pmin"][g])
         hi = np.full(6, net["gen_pmax"][g])
         assert oracle.pgnorm(p_after[g], gr, lo, hi) <= 1e-6
+
+
+# ------------------------------------------- step rules, one iteration computed by hand
+# Readings R2 (Cauchy search), R5 (PCG norm), R7 (radius update) and the projected
+# search of Algorithm 1, each pinned by a case small enough to follow on paper: a dense
+# problem f = 1/2 x'Qx + c'x + sum d x^4 stopped after max_outer iterations, with the
+# returned x, radius, status and trial counters compared with the values derived in the
+# comments.  mu0 = 0.01, interpolation x0.1, extrapolation x10, eta = (1e-4, .25, .75),
+# sigma1 = 0.25, sigma3 = 4, projected-search factor 0.5.
+
+def _dense1(Q, c, d, x0, delta, max_outer=1, l=-10.0, u=10.0, **opt):
+    Q = np.atleast_2d(np.asarray(Q, dtype=float))
+    n = Q.shape[0]
+    rec = np.concatenate([Q.ravel(), np.asarray(c, float).ravel(), np.asarray(d, float).ravel()])
+    return oracle.tron_solve(oracle.OBJ_DENSE, rec, np.broadcast_to(l, (n,)),
+                             np.broadcast_to(u, (n,)), x0, delta,
+                             opts=oracle.default_opts(max_outer=max_outer, **opt))
+
+
+def test_cauchy_interpolation_preconditioned_boundary_and_expansion():
+    # f = 5 x^2 - x, x0 = 0, delta = 0.015: g = -1, H = 10.
+    # Cauchy: alpha = 1 (s = 1: q = -1 + 5 > 0.01 g's) and alpha = 0.1 (||s|| = 0.1 >
+    # delta) fail, alpha = 0.01 holds (s = 0.01, q = -0.0095): three trials, x_c = 0.01.
+    # Subspace: r = g + H s = -0.9, L = sqrt(10); the CG iterate s_hat = -bhat has
+    # ||s_hat|| = 0.9/sqrt(10) > delta, so CG stops on the boundary ||s_hat|| = delta and
+    # w = L^-T s_hat = 0.015/sqrt(10); the full step passes the projected search.
+    # The model is exact (rho = 1 > eta2) and the subspace step reached its bound
+    # (beta ||s_hat|| = delta), so delta = 4 * 0.015.
+    r = _dense1([10.0], [-1.0], [0.0], [0.0], 0.015)
+    assert r["status"] == oracle.MAX_ITER and r["iters"] == 1
+    assert r["counters"]["cauchy_trials"] == 3 and r["counters"]["proj_trials"] == 1
+    assert abs(r["x"][0] - (0.01 + 0.015 / math.sqrt(10.0))) < 1e-15
+    assert r["delta"] == 0.06
+    # the other norm reading bounds w itself: w = 0.015, x = 0.025; the radius update
+    # then measures ||x+ - x|| = 0.025 >= 0.99 delta and expands as well
+    r = _dense1([10.0], [-1.0], [0.0], [0.0], 0.015, tr_norm=1)
+    assert abs(r["x"][0] - 0.025) < 1e-15 and r["delta"] == 0.06
+
+
+def test_cauchy_alpha_persists_between_iterations():
+    # the case above for two iterations: x1 = 0.01 + 0.015/sqrt(10), g1 = 10 x1 - 1,
+    # delta = 0.06.  The second search starts from the stored alpha = 0.01: it holds
+    # (s = 0.01 |g1| = 0.0085, within delta), the extrapolated 0.1 does not (||s|| =
+    # 0.085 > 0.06): two trials (restarting at 1 would take three).  x_c = x1 - 0.01 g1,
+    # r = 0.9 g1, CG stops on the boundary again: w = 0.06/sqrt(10), delta = 0.24.
+    r = _dense1([10.0], [-1.0], [0.0], [0.0], 0.015, max_outer=2)
+    x1 = 0.01 + 0.015 / math.sqrt(10.0)
+    g1 = 10.0 * x1 - 1.0
+    assert r["status"] == oracle.MAX_ITER and r["iters"] == 2
+    assert r["counters"]["cauchy_trials"] == 3 + 2
+    assert abs(r["x"][0] - (x1 - 0.01 * g1 + 0.06 / math.sqrt(10.0))) < 1e-14
+    assert abs(r["delta"] - 0.24) < 1e-15
+
+
+def test_cauchy_extrapolation_stops_at_the_largest_breakpoint():
+    # f = 0.0005 x^2 - x on [-10, 10], x0 = 0, delta = 100: alpha = 1 holds (q = -0.9995),
+    # the only breakpoint along -g is 10, alpha = 10 holds (s = 10, q = -9.95) and the
+    # search stops there (alpha is no longer below the breakpoint): two trials.  x_c = 10
+    # is on the bound, the free set is empty, the step is accepted (rho = 1) but is far
+    # inside the radius (10 < 0.99 * 100): delta stays 100.  At x = 10 the gradient
+    # -0.99 pushes against the bound: converged after one iteration.
+    r = _dense1([0.001], [-1.0], [0.0], [0.0], 100.0)
+    assert r["status"] == oracle.CONVERGED and r["iters"] == 1
+    assert r["counters"]["cauchy_trials"] == 2 and r["counters"]["proj_trials"] == 0
+    assert r["x"][0] == 10.0 and r["delta"] == 100.0
+
+
+def test_radius_shrinks_to_a_quarter_of_the_shorter_of_step_and_radius():
+    # f = 1/2 x^2 - x + x^4, x0 = 0, delta = 2: the model 1/2 s^2 - s is minimised by
+    # the Cauchy point alpha = 1 (x_c = 1, alpha = 10 exceeds the radius), the subspace
+    # step is zero (r = 0).  f(1) = 0.5 > f(0) = 0: rho ~ -1, the step is rejected and
+    # delta = 0.25 * min(||s|| = 1, 2) = 0.25.
+    r = _dense1([1.0], [-1.0], [1.0], [0.0], 2.0)
+    assert r["status"] == oracle.MAX_ITER and r["iters"] == 1
+    assert r["x"][0] == 0.0 and r["delta"] == 0.25
+    assert r["counters"]["cauchy_trials"] == 2
+
+
+# f = 1/2 x^2 - x + d x^4, x0 = 0: the step is s = 1 (Cauchy point alpha = 1, the
+# model's minimiser), pred = 0.5, ared = 0.5 - d, rho = 1 - 2d (> eta0: accepted)
+RADIUS_CASES = [
+    (0.25, 1.0, 1.0, 1.0),      # rho = 0.5: accepted, radius kept
+    (0.05, 1.0, 1.0, 4.0),      # rho = 0.9 > eta2 and ||s|| = delta: expanded x4
+    (0.05, 1.005, 1.0, 4.02),   # ||s|| = 1 >= 0.99 * 1.005: expanded
+    (0.05, 1.02, 1.0, 1.02),    # ||s|| = 1 < 0.99 * 1.02: kept
+    (0.40, 1.0, 1.0, 0.25),     # rho = 0.2 < eta1: accepted, and shrunk to 0.25 * 1
+]
+
+
+def _radius_case(d, delta0, x1, delta1):
+    r = _dense1([1.0], [-1.0], [d], [0.0], delta0)
+    assert r["iters"] == 1 and r["x"][0] == x1
+    assert abs(r["delta"] - delta1) < 1e-15
+
+
+@pytest.mark.parametrize("d,delta0,x1,delta1", RADIUS_CASES)
+def test_radius_update_by_ratio_and_step_length(d, delta0, x1, delta1):
+    _radius_case(d, delta0, x1, delta1)
+
+
+def radius_update_all_cases():
+    for case in RADIUS_CASES:
+        _radius_case(*case)
+
+
+def test_projected_search_halves_the_step_until_the_model_decreases():
+    # Q = [[1, .8], [.8, 1]], c = (-1, 1), box [-10, 2] x [-10, 10], x0 = 0, delta = 100.
+    # Cauchy: alpha = 1 holds (s = (1, -1), q = -2 + 0.2); alpha = 10 (s = (2, -10),
+    # q = -12 + 36) fails: x_c = (1, -1), model gradient r = c + Q s = (-0.8, 0.8).
+    # Newton step w = -Q^-1 r = (4, -4) (||s_hat||^2 = r'Q^-1 r = 6.4, inside).
+    # beta = 1: P[x_c + w] = (2, -5), d = (1, -4): r'd = -4, d'Qd = 10.6, the model change
+    # -4 + 5.3 > 0.01 r'd -- fails.  beta = 1/2: P[x_c + w/2] = (2, -3), d = (1, -2):
+    # r'd = -2.4, d'Qd = 1.8, -2.4 + 0.9 <= -0.024 -- holds.  x1 = (2, -3) (variable 1 now
+    # active, which ends the pass), accepted (quadratic: rho = 1), delta kept (the
+    # step's pieces are ||s_c|| = sqrt 2 and ||s_hat|| / 2, far inside 100).
+    r = _dense1([[1.0, 0.8], [0.8, 1.0]], [-1.0, 1.0], [0.0, 0.0], [0.0, 0.0], 100.0,
+                l=np.array([-10.0, -10.0]), u=np.array([2.0, 10.0]))
+    assert r["status"] == oracle.MAX_ITER and r["iters"] == 1
+    assert r["counters"]["cauchy_trials"] == 2 and r["counters"]["proj_trials"] == 2
+    np.testing.assert_allclose(r["x"], [2.0, -3.0], rtol=0, atol=1e-14)
+    assert r["delta"] == 100.0
+
+
+def test_guard_scale_is_the_magnitude_of_the_terms_of_f():
+    # R6: the ratio's rounding guard is 1e-13 max(1, S), S the sum of the magnitudes of
+    # the terms f is assembled from, not |f|.  Dense: x = 10, Q = 20, c = -99.9 gives
+    # f = 1000 - 999 = 1 with S = 1000 + 999 = 1999.
+    rec = np.array([20.0, -99.9, 0.0])
+    f, _, _ = oracle.eval_obj(oracle.OBJ_DENSE, rec, np.array([10.0]))
+    assert abs(f - 1.0) < 1e-12
+    assert abs(oracle.fscale(oracle.OBJ_DENSE, rec, np.array([10.0])) - 1999.0) < 1e-9
+    # quartic term: d x^4 with d = -2 at x = 10 counts |d| x^4 = 2e4
+    rec = np.array([20.0, -99.9, -2.0])
+    assert abs(oracle.fscale(oracle.OBJ_DENSE, rec, np.array([10.0])) - 21999.0) < 1e-8
+    # branch at v = (1, 1), theta = (0, 0): w_i = w_j = wR = 1, wI = 0.  Only the pair
+    # p_ij carries a multiplier (200) and a penalty (400): p_ij = gc_ij - g_ij = 20 - 20
+    # = 0 is its target, so f = 0; each flow term counts (|lambda| + rho |p - t|) times
+    # the magnitudes of its terms, |gc_ij w_i| + |g_ij wR| + |b_ij wI| = 40: S = 8000.
+    rec = np.zeros(36)
+    rec[0], rec[2], rec[3] = 20.0, 20.0, 5.0
+    rec[8], rec[24] = 200.0, 400.0
+    rec[32], rec[33] = 100.0, 400.0  # line limit 10: inactive
+    x = np.array([1.0, 1.0, 0.0, 0.0])
+    f, _, _ = oracle.eval_obj(oracle.OBJ_BRANCH, rec, x)
+    assert f == 0.0
+    assert abs(oracle.fscale(oracle.OBJ_BRANCH, rec, x) - 8000.0) < 1e-9
+
+
+def test_branch_solves_at_an_admm_state_all_converge():
+    # branch subproblems as the ADMM poses them after 20 iterations on a 200-bus network:
+    # f ~ 1..100 is a difference of terms ~ 1e3 (multipliers ~ 1e2 times flows with
+    # coefficients ~ 20).  TRON reaches a KKT point on every one; a guard scaled by |f|
+    # instead of S lets rounding noise of f decide the ratio and collapses the radius on
+    # some of them (TR_TOO_SMALL).
+    net = synth.network(200, 60, 60, rng=np.random.default_rng(7))
+    a = oracle.Admm(net)
+    a.run(20, nthreads=4)
+    nl = len(net["br_from"])
+    recs = np.array([a.branch_record(k) for k in range(nl)])
+    lo = np.tile([0.9, 0.9, -2 * np.pi, -2 * np.pi], (nl, 1))
+    hi = np.tile([1.1, 1.1, 2 * np.pi, 2 * np.pi], (nl, 1))
+    r = oracle.tron_batch(oracle.OBJ_BRANCH, recs, lo, hi, a.arrays["br_x"], np.ones(nl),
+                          nthreads=4)
+    assert np.all(r["status"] == oracle.CONVERGED), np.bincount(r["status"])
+    assert np.all(r["pg"] <= 1e-6)

@@ -135,6 +135,29 @@ def test_branch_parity(B, group):
     assert rel.max() <= 1e-8
 
 
+@pytest.mark.parametrize("tr_norm", [0, 1])
+def test_trust_region_norm_readings_match_oracle(tr_norm):
+    # options.tr_norm 0: the CG iterate of the preconditioned system is bounded,
+    # ||L^T w|| <= delta (as Algorithm 1 prints it; the default); 1: ||w||_2 <= delta.  The GPU
+    # forms the first from CG recurrences, the oracle from the iterate itself.
+    d = synth.dense_batch(160, 32, seed_index=7)
+    g = gpu_solve(d, n=32, tr_norm=tr_norm)
+    r = oracle_solve(d, tr_norm=tr_norm)
+    assert_convex_parity(g, r, d["l"], d["u"])
+    same_path = g["iters"] == r["iters"]
+    assert same_path.mean() >= 0.95
+    # the final radius, on the problems that took the same path
+    np.testing.assert_allclose(g["delta"][same_path], r["delta"][same_path], rtol=1e-6)
+    br = synth.branch_batch(160, seed_index=9)
+    for group in (1, 4):
+        g = gpu_solve(br, n=4, group=group, tr_norm=tr_norm)
+        r = oracle_solve(br, tr_norm=tr_norm)
+        assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
+        same = np.all(np.abs(g["x"] - r["x"]) <= 1e-6, axis=1)
+        assert same.mean() >= 0.98
+        assert np.mean(g["iters"] == r["iters"]) >= 0.95
+
+
 def test_branch_default_group_follows_batch_size():
     # the library's mapping of the branch problems: four lanes per problem up to 40
     # problems per SM sub-partition, one lane beyond; an explicit group wins
@@ -413,3 +436,30 @@ def test_full_size_dense_workload_sampled():
     np.testing.assert_allclose(g["x"][idx], r["x"], rtol=0, atol=1e-6)
     rel = np.abs(g["f"][idx] - r["f"]) / np.maximum(1.0, np.abs(r["f"]))
     assert rel.max() <= 1e-8
+
+
+def test_pivot_reciprocal_against_ieee_division():
+    # the factorization's 1/d: hardware estimate + one Newton step (division from
+    # 2^1022 up); relative error against the correctly rounded 1/d <= 2^-38 over the
+    # positive normal range, powers of two and their neighbours included
+    rng = np.random.default_rng(5)
+    e = rng.uniform(-1022.0, 1023.99, 1 << 20)
+    a = np.ldexp(1.0, 0) * np.exp2(e)
+    p2 = np.ldexp(1.0, np.arange(-1022, 1024))
+    a = np.concatenate([a, p2, np.nextafter(p2, 0.0), np.nextafter(p2, np.inf),
+                        [np.finfo(float).tiny, np.finfo(float).max, 1.0, 3.0, 1e-300, 1e300]])
+    a = a[np.isfinite(a) & (a >= np.finfo(float).tiny)]
+    d_a = _t(a)
+    d_out = torch.empty_like(d_a)
+    lib = native.load()
+    assert lib.tron_test_pivot_rcp(d_a.data_ptr(), d_out.data_ptr(), a.size,
+                                   torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy()
+    ref = 1.0 / a
+    rel = np.abs(got - ref) / ref
+    assert np.all(np.isfinite(got))
+    assert rel.max() <= 2.0 ** -38, (rel.max(), a[np.argmax(rel)])
+    # from 2^1022 up the hook divides: exact
+    big = a >= 2.0 ** 1022
+    np.testing.assert_array_equal(got[big], ref[big])

@@ -1,11 +1,13 @@
 """The entry point that allocates no device memory (tron_solve_mixed_noalloc).
 
-It exists for callers that cannot call cudaMalloc (graph capture in progress, device
-memory owned by the caller's pool allocator, loops that must not synchronise on an
-allocation).  Here it is called through the C ABI twice in a row on two different
-mixed-size batches, and each result is compared with the regular handle-based entry
-point (tron_batch_create + tron_batch_solve) on the same inputs, within the tolerances
-of the other GPU tests.  This file is collected last on purpose.
+It exists for callers that must not allocate device memory from a library call: hosts
+whose device memory all belongs to their own pool allocator, where a cudaMalloc beside
+the pool fails or fragments it, and processes held to a fixed device-memory budget.
+Here it is called through the C ABI twice in a row on two different mixed-size batches
+that between them cover every size class (4 to 128), and each result is compared with
+the regular handle-based entry point (tron_batch_create + tron_batch_solve) on the same
+inputs, and the first batch also with the CPU oracle, within the tolerances of the other
+GPU tests.  This file is collected last on purpose.
 """
 import ctypes as C
 
@@ -63,12 +65,15 @@ def _via_noalloc(lib, d, stream):
 
 
 def test_noalloc_matches_handle_path_on_two_calls_in_a_row():
+    import oracle
     lib = native.load()
     stream = torch.cuda.Stream()
-    sizes, probs = (4, 6, 8, 16, 32), (0.3, 0.2, 0.2, 0.2, 0.1)
-    batches = [synth.uneven_batch(700, seed_index=11, sizes=sizes, probs=probs),
+    sizes = (4, 6, 8, 16, 32, 64, 128)
+    probs = (0.3, 0.2, 0.15, 0.15, 0.1, 0.06, 0.04)
+    batches = [synth.uneven_batch(300, seed_index=11, sizes=sizes, probs=probs),
                synth.uneven_batch(450, seed_index=12, sizes=sizes, probs=probs)]
-    for d in batches:  # two calls in a row; the second reuses the same scratch
+    for k, d in enumerate(batches):  # two calls in a row; the second reuses the scratch
+        assert set(np.unique(d["nvec"])) == set(sizes)  # every size class is present
         a = _via_noalloc(lib, d, stream)
         b = _via_handle(d)
         np.testing.assert_array_equal(a["status"], b["status"])
@@ -77,6 +82,13 @@ def test_noalloc_matches_handle_path_on_two_calls_in_a_row():
         np.testing.assert_allclose(a["x"], b["x"], rtol=0, atol=1e-6)
         rel = np.abs(a["f"] - b["f"]) / np.maximum(1.0, np.abs(b["f"]))
         assert rel.max() <= 1e-8
+        if k == 0:  # and against the CPU oracle
+            r = oracle.tron_batch(2, d["params"], d["l"], d["u"], d["x0"], d["delta0"],
+                                  n=d["nvec"], nthreads=8)
+            assert np.all(r["status"] == oracle.CONVERGED)
+            np.testing.assert_allclose(a["x"], r["x"], rtol=0, atol=1e-6)
+            rel = np.abs(a["f"] - r["f"]) / np.maximum(1.0, np.abs(r["f"]))
+            assert rel.max() <= 1e-8
 
 
 def test_noalloc_rejects_batches_beyond_its_capacity():
