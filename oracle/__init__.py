@@ -146,6 +146,10 @@ def _load(path: str):
             L.ot_admm_run.argtypes = [C.POINTER(Net), C.POINTER(State), C.POINTER(Opts),
                                       C.c_int, C.c_int, P, P, P, C.POINTER(Counters)]
             L.ot_admm_branch_record.argtypes = [C.POINTER(Net), C.POINTER(State), C.c_int, P]
+            L.ot_admm_phase_components.argtypes = [C.POINTER(Net), C.POINTER(State),
+                                                   C.POINTER(Opts), C.c_int, P, P,
+                                                   C.POINTER(Counters)]
+            L.ot_admm_phase_buses.argtypes = [C.POINTER(Net), C.POINTER(State), P, P, P]
             L.ot_admm_mp_init.argtypes = [C.POINTER(MP)]
             L.ot_admm_mp_run.argtypes = [C.POINTER(MP), C.POINTER(Opts), C.c_int, C.c_int, P, P,
                                          C.POINTER(Counters)]
@@ -362,6 +366,26 @@ class Admm:
                           int(nthreads), _p(hp), _p(hd), _p(self.status_counts),
                           C.byref(self.counters))
         return hp, hd
+
+    def phase_components(self, gen_mask, br_mask, opts: Opts | None = None,
+                         nthreads: int = 1) -> None:
+        """Generator and branch updates of the masked components (one phase of the
+        iteration, as a partitioned run performs it)."""
+        o = opts or default_opts()
+        gm = np.ascontiguousarray(gen_mask, dtype=np.uint8)
+        bm = np.ascontiguousarray(br_mask, dtype=np.uint8)
+        lib().ot_admm_phase_components(C.byref(self.net), C.byref(self.state), C.byref(o),
+                                       int(nthreads), _p(gm), _p(bm), C.byref(self.counters))
+
+    def phase_buses(self, bus_mask):
+        """Bus updates of the masked buses with the multipliers of their pairs; returns
+        the squared primal and (unscaled) dual residual sums of those pairs."""
+        bm = np.ascontiguousarray(bus_mask, dtype=np.uint8)
+        pr2 = np.zeros(1)
+        du2 = np.zeros(1)
+        lib().ot_admm_phase_buses(C.byref(self.net), C.byref(self.state), _p(bm), _p(pr2),
+                                  _p(du2))
+        return float(pr2[0]), float(du2[0])
 
     def branch_record(self, k: int) -> np.ndarray:
         rec = np.zeros(36)

@@ -139,6 +139,16 @@ void ot_admm_run(const ot_net* net, ot_state* st, const ot_opts* o, int niters, 
 /* build the 36-entry branch record of branch k from the current state */
 void ot_admm_branch_record(const ot_net* net, const ot_state* st, int k, double* rec);
 
+/* The same iteration in phases on subsets (for partitioned runs, Sec. 6.3): generators
+ * and branches of the masks; then buses of the mask, each followed by the multiplier
+ * updates and squared residual terms of the pairs whose bus-side copies it holds
+ * (their sums are returned in *pr2_out and, unscaled by rho, *du2_out). */
+void ot_admm_phase_components(const ot_net* net, ot_state* st, const ot_opts* o,
+                              int nthreads, const uint8_t* gen_mask,
+                              const uint8_t* br_mask, ot_counters* total);
+void ot_admm_phase_buses(const ot_net* net, ot_state* st, const uint8_t* bus_mask,
+                         double* pr2_out, double* du2_out);
+
 /* --------------------------------------- multi-period ADMM (future work of Sec. 7)
  * T periods of one network (nets[t] differ only in their loads); the generator
  * component spans the periods: its T active-power outputs are one NLP of kind

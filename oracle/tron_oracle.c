@@ -1247,6 +1247,192 @@ void ot_admm_run(const ot_net* net, ot_state* st, const ot_opts* o, int niters, 
   admm_ws_free(&w);
 }
 
+/* ------------------------------------------ the same iteration in phases, on a subset
+ * A partitioned run (buses split between ranks, Sec. 6.3) performs the iteration above in
+ * three phases, each on the components a rank owns, with exchanges in between:
+ *   1. components: generators (closed form) and branches (TRON) of the masks;
+ *   2. buses of the mask: the bus QP, then the multipliers and the residual terms of
+ *      every pair whose bus-side copy the bus holds (its generators and incident branch
+ *      ends).  A pair's multiplier is used only by its own bus and, in the next
+ *      iteration, by its component, so updating it right after its bus gives the values
+ *      of the undivided iteration; only the order of the residual sums differs. */
+void ot_admm_phase_components(const ot_net* net, ot_state* st, const ot_opts* o,
+                              int nthreads, const uint8_t* gen_mask,
+                              const uint8_t* br_mask, ot_counters* total) {
+  double rho = net->rho;
+  for (int g = 0; g < net->ngen; g++) {
+    if (!gen_mask[g]) continue;
+    double pt = st->gen_tilde[2 * g], qt = st->gen_tilde[2 * g + 1];
+    double lp = st->gen_lam[2 * g], lq = st->gen_lam[2 * g + 1];
+    double p = (rho * pt - lp - net->gen_c1[g]) / (2.0 * net->gen_c2[g] + rho);
+    double q = qt - lq / rho;
+    st->gen_pq[2 * g] = proj1(p, net->gen_pmin[g], net->gen_pmax[g]);
+    st->gen_pq[2 * g + 1] = proj1(q, net->gen_qmin[g], net->gen_qmax[g]);
+  }
+  int nl = net->nbranch, m = 0;
+  int* ids = (int*)malloc(sizeof(int) * (size_t)(nl + 1));
+  for (int k = 0; k < nl; k++)
+    if (br_mask[k]) ids[m++] = k;
+  int32_t* n4 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+  int64_t* poff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m + 1));
+  int64_t* voff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m + 1));
+  double* recs = (double*)malloc(sizeof(double) * 36 * (size_t)(m + 1));
+  double* bx = (double*)malloc(sizeof(double) * 4 * (size_t)(m + 1));
+  double* bl = (double*)malloc(sizeof(double) * 4 * (size_t)(m + 1));
+  double* bu = (double*)malloc(sizeof(double) * 4 * (size_t)(m + 1));
+  double* bd = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  double* bf = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  double* bpg = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  int32_t* bit = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+  int32_t* bst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+  const double twopi = 6.283185307179586476925286766559;
+  for (int t = 0; t < m; t++) {
+    int k = ids[t];
+    n4[t] = 4;
+    poff[t] = 36 * (int64_t)t;
+    voff[t] = 4 * (int64_t)t;
+    ot_admm_branch_record(net, st, k, recs + 36 * (size_t)t);
+    for (int a = 0; a < 4; a++) bx[4 * t + a] = st->br_x[4 * (size_t)k + a];
+    bd[t] = st->br_delta[k];
+    bl[4 * t + 0] = net->vmin;
+    bl[4 * t + 1] = net->vmin;
+    bl[4 * t + 2] = -twopi;
+    bl[4 * t + 3] = -twopi;
+    bu[4 * t + 0] = net->vmax;
+    bu[4 * t + 1] = net->vmax;
+    bu[4 * t + 2] = twopi;
+    bu[4 * t + 3] = twopi;
+  }
+  if (m > 0)
+    ot_tron_batch(OT_OBJ_BRANCH, m, n4, poff, voff, recs, bl, bu, bx, bd, o, bf, bpg, bit,
+                  bst, nthreads, total);
+  for (int t = 0; t < m; t++) {
+    int k = ids[t];
+    for (int a = 0; a < 4; a++) st->br_x[4 * (size_t)k + a] = bx[4 * t + a];
+    st->br_delta[k] = bd[t];
+    branch_values_at(net->br_coef + 8 * (size_t)k, st->br_x + 4 * (size_t)k,
+                     st->br_val + 8 * (size_t)k);
+  }
+  free(ids);
+  free(n4);
+  free(poff);
+  free(voff);
+  free(recs);
+  free(bx);
+  free(bl);
+  free(bu);
+  free(bd);
+  free(bf);
+  free(bpg);
+  free(bit);
+  free(bst);
+}
+
+void ot_admm_phase_buses(const ot_net* net, ot_state* st, const uint8_t* bus_mask,
+                         double* pr2_out, double* du2_out) {
+  admm_ws w;
+  admm_ws_init(net, &w);
+  double rho = net->rho;
+  double pr2 = 0.0, du2 = 0.0;
+  for (int b = 0; b < net->nbus; b++) {
+    if (!bus_mask[b]) continue;
+    /* the bus-side copies before the update (dual residual) */
+    double prev_w = st->bus_w[b], prev_th = st->bus_th[b];
+    for (int t = w.gp[b]; t < w.gp[b + 1]; t++) {
+      int g = w.gl[t];
+      w.tprev[2 * g] = st->gen_tilde[2 * g];
+      w.tprev[2 * g + 1] = st->gen_tilde[2 * g + 1];
+    }
+    for (int t = w.ep[b]; t < w.ep[b + 1]; t++) {
+      int e = w.el[t], k = e / 2, kp = (e % 2) ? 2 : 0;
+      w.tprev[2 * net->ngen + 8 * k + kp] = st->br_tilde[4 * (size_t)k + kp];
+      w.tprev[2 * net->ngen + 8 * k + kp + 1] = st->br_tilde[4 * (size_t)k + kp + 1];
+    }
+    double rhsP = -net->bus_pd[b], rhsQ = -net->bus_qd[b];
+    double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
+    for (int t = w.gp[b]; t < w.gp[b + 1]; t++) {
+      int g = w.gl[t];
+      rhsP += st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho;
+      rhsQ += st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho;
+      sinv += 1.0 / rho;
+    }
+    for (int t = w.ep[b]; t < w.ep[b + 1]; t++) {
+      int e = w.el[t], k = e / 2, side = e % 2;
+      const double* val = st->br_val + 8 * (size_t)k;
+      const double* lam = st->br_lam + 8 * (size_t)k;
+      int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
+      rhsP -= val[kp] + lam[kp] / rho;
+      rhsQ -= val[kq] + lam[kq] / rho;
+      sinv += 1.0 / rho;
+      Dw += rho;
+      awn += rho * (val[kw] + lam[kw] / rho);
+      athn += rho * (val[kt] + lam[kt] / rho);
+    }
+    double gsh = net->bus_gsh[b], bsh = net->bus_bsh[b];
+    double aw = Dw > 0.0 ? awn / Dw : st->bus_w[b];
+    rhsP -= gsh * aw;
+    rhsQ += bsh * aw;
+    double M11 = sinv, M22 = sinv, M12 = 0.0;
+    if (Dw > 0.0) {
+      M11 += gsh * gsh / Dw;
+      M22 += bsh * bsh / Dw;
+      M12 = -gsh * bsh / Dw;
+    }
+    double det = M11 * M22 - M12 * M12;
+    double mu1 = 0.0, mu2 = 0.0;
+    if (det != 0.0) {
+      mu1 = (M22 * rhsP - M12 * rhsQ) / det;
+      mu2 = (M11 * rhsQ - M12 * rhsP) / det;
+    }
+    for (int t = w.gp[b]; t < w.gp[b + 1]; t++) {
+      int g = w.gl[t];
+      st->gen_tilde[2 * g] = st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho - mu1 / rho;
+      st->gen_tilde[2 * g + 1] =
+          st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho - mu2 / rho;
+    }
+    for (int t = w.ep[b]; t < w.ep[b + 1]; t++) {
+      int e = w.el[t], k = e / 2, side = e % 2;
+      const double* val = st->br_val + 8 * (size_t)k;
+      const double* lam = st->br_lam + 8 * (size_t)k;
+      int kp = side ? 2 : 0, kq = kp + 1;
+      st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho + mu1 / rho;
+      st->br_tilde[4 * (size_t)k + kq] = val[kq] + lam[kq] / rho + mu2 / rho;
+    }
+    if (Dw > 0.0) {
+      st->bus_w[b] = aw - (-gsh * mu1 + bsh * mu2) / Dw;
+      st->bus_th[b] = athn / Dw;
+    }
+    /* multipliers and residual terms of the pairs whose copies this bus holds */
+    for (int t = w.gp[b]; t < w.gp[b + 1]; t++) {
+      int g = w.gl[t];
+      for (int a = 0; a < 2; a++) {
+        double xv = st->gen_pq[2 * g + a], xt = st->gen_tilde[2 * g + a];
+        st->gen_lam[2 * g + a] += rho * (xv - xt);
+        pr2 += (xv - xt) * (xv - xt);
+        double dd = xt - w.tprev[2 * g + a];
+        du2 += dd * dd;
+      }
+    }
+    for (int t = w.ep[b]; t < w.ep[b + 1]; t++) {
+      int e = w.el[t], k = e / 2, side = e % 2;
+      int kp = side ? 2 : 0;
+      int as[4] = {kp, kp + 1, side ? 5 : 4, side ? 7 : 6};
+      for (int q = 0; q < 4; q++) {
+        int a = as[q];
+        double xv = st->br_val[8 * (size_t)k + a], xt = pair_tilde(net, st, k, a);
+        double prev = q < 2 ? w.tprev[2 * net->ngen + 8 * k + a] : (q == 2 ? prev_w : prev_th);
+        st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);
+        pr2 += (xv - xt) * (xv - xt);
+        double dd = xt - prev;
+        du2 += dd * dd;
+      }
+    }
+  }
+  admm_ws_free(&w);
+  *pr2_out = pr2;
+  *du2_out = du2;
+}
+
 /* ------------------------------------------------- multi-period ADMM (Sec. 7, readings)
  * The generator component spans the periods: its T active-power outputs are one NLP
  * (OT_OBJ_GENRAMP) with the ramp penalty, solved by the same TRON; everything else is
