@@ -288,6 +288,15 @@ const char* tron_version(void);
  * for).  Enqueued on `stream`; TRON_EINVAL for a null array with n > 0. */
 tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void* stream);
 
+/* Measurement hook (the paper has no counterpart): FP64 fused multiply-add throughput.
+ * Launches `blocks` CTAs of `threads` threads; every thread runs 8 independent chains of
+ * `iters` dependent FMAs and writes its result to d_out[thread] (caller-owned device
+ * array of blocks * threads doubles), so one launch performs 16 * iters * blocks *
+ * threads floating-point operations; the caller times it (CUDA events on `stream`).
+ * TRON_EINVAL for non-positive sizes, threads > 1024 or threads not a multiple of 32. */
+tron_err_t tron_bench_fp64_fma(double* d_out, int32_t blocks, int32_t threads, int64_t iters,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

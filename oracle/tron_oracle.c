@@ -1109,18 +1109,93 @@ static void admm_ws_free(admm_ws* w) {
   free(w->tprev);
 }
 
-/* closed-form generator update: minimiser of the box-clipped scalar quadratics; only q
- * when active_power is 0 (the multi-period update sets p) */
-static void admm_gen_update(const ot_net* net, ot_state* st, int active_power) {
+/* closed-form generator update of generator g: minimiser of the box-clipped scalar
+ * quadratics; only q when active_power is 0 (the multi-period update sets p) */
+static void gen_update_one(const ot_net* net, ot_state* st, int g, int active_power) {
   double rho = net->rho;
-  for (int g = 0; g < net->ngen; g++) {
-    double pt = st->gen_tilde[2 * g], qt = st->gen_tilde[2 * g + 1];
-    double lp = st->gen_lam[2 * g], lq = st->gen_lam[2 * g + 1];
-    double p = (rho * pt - lp - net->gen_c1[g]) / (2.0 * net->gen_c2[g] + rho);
-    double q = qt - lq / rho;
-    if (active_power) st->gen_pq[2 * g] = proj1(p, net->gen_pmin[g], net->gen_pmax[g]);
-    st->gen_pq[2 * g + 1] = proj1(q, net->gen_qmin[g], net->gen_qmax[g]);
+  double pt = st->gen_tilde[2 * g], qt = st->gen_tilde[2 * g + 1];
+  double lp = st->gen_lam[2 * g], lq = st->gen_lam[2 * g + 1];
+  double p = (rho * pt - lp - net->gen_c1[g]) / (2.0 * net->gen_c2[g] + rho);
+  double q = qt - lq / rho;
+  if (active_power) st->gen_pq[2 * g] = proj1(p, net->gen_pmin[g], net->gen_pmax[g]);
+  st->gen_pq[2 * g + 1] = proj1(q, net->gen_qmin[g], net->gen_qmax[g]);
+}
+
+static void admm_gen_update(const ot_net* net, ot_state* st, int active_power) {
+  for (int g = 0; g < net->ngen; g++) gen_update_one(net, st, g, active_power);
+}
+
+/* bus update of bus b: minimise sum rho/2 (xt - a)^2 with a = x + lambda/rho subject to
+ * the bus balance equations (eqs. PowerBalanceReal/Reactive); x = a - D^-1 A' mu with
+ * (A D^-1 A') mu = A a - (p_d, q_d); writes the bus-side copies of its generators and
+ * incident branch ends and its w, theta */
+static void bus_update_one(const ot_net* net, ot_state* st, const admm_ws* w, int b) {
+  double rho = net->rho;
+  const int *ep = w->ep, *gp = w->gp, *el = w->el, *gl = w->gl;
+  double rhsP = -net->bus_pd[b], rhsQ = -net->bus_qd[b];
+  double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
+  for (int t = gp[b]; t < gp[b + 1]; t++) {
+    int g = gl[t];
+    rhsP += st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho;
+    rhsQ += st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho;
+    sinv += 1.0 / rho;
   }
+  for (int t = ep[b]; t < ep[b + 1]; t++) {
+    int e = el[t], k = e / 2, side = e % 2;
+    const double* val = st->br_val + 8 * (size_t)k;
+    const double* lam = st->br_lam + 8 * (size_t)k;
+    int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
+    rhsP -= val[kp] + lam[kp] / rho;
+    rhsQ -= val[kq] + lam[kq] / rho;
+    sinv += 1.0 / rho;
+    Dw += rho;
+    awn += rho * (val[kw] + lam[kw] / rho);
+    athn += rho * (val[kt] + lam[kt] / rho);
+  }
+  double gsh = net->bus_gsh[b], bsh = net->bus_bsh[b];
+  double aw = Dw > 0.0 ? awn / Dw : st->bus_w[b];
+  rhsP -= gsh * aw;
+  rhsQ += bsh * aw;
+  double M11 = sinv, M22 = sinv, M12 = 0.0;
+  if (Dw > 0.0) {
+    M11 += gsh * gsh / Dw;
+    M22 += bsh * bsh / Dw;
+    M12 = -gsh * bsh / Dw;
+  }
+  double det = M11 * M22 - M12 * M12;
+  double mu1 = 0.0, mu2 = 0.0;
+  if (det != 0.0) {
+    mu1 = (M22 * rhsP - M12 * rhsQ) / det;
+    mu2 = (M11 * rhsQ - M12 * rhsP) / det;
+  }
+  for (int t = gp[b]; t < gp[b + 1]; t++) {
+    int g = gl[t];
+    st->gen_tilde[2 * g] = st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho - mu1 / rho;
+    st->gen_tilde[2 * g + 1] =
+        st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho - mu2 / rho;
+  }
+  for (int t = ep[b]; t < ep[b + 1]; t++) {
+    int e = el[t], k = e / 2, side = e % 2;
+    const double* val = st->br_val + 8 * (size_t)k;
+    const double* lam = st->br_lam + 8 * (size_t)k;
+    int kp = side ? 2 : 0, kq = kp + 1;
+    st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho + mu1 / rho;
+    st->br_tilde[4 * (size_t)k + kq] = val[kq] + lam[kq] / rho + mu2 / rho;
+  }
+  if (Dw > 0.0) {
+    st->bus_w[b] = aw - (-gsh * mu1 + bsh * mu2) / Dw;
+    st->bus_th[b] = athn / Dw;
+  }
+}
+
+/* multiplier update lambda += rho (x - xt) of one pair, and its squared primal and
+ * (unscaled) dual residual terms */
+static void pair_update(double* lam, double xv, double xt, double prev, double rho,
+                        double* pr2, double* du2) {
+  *lam += rho * (xv - xt);
+  *pr2 += (xv - xt) * (xv - xt);
+  double dd = xt - prev;
+  *du2 += dd * dd;
 }
 
 /* one ADMM iteration after the generator update: branch updates, bus updates,
@@ -1130,7 +1205,6 @@ static void admm_after_gens(const ot_net* net, ot_state* st, const ot_opts* o, i
                             double* pr2_out, double* du2_out) {
   int nb = net->nbus, nl = net->nbranch, ng = net->ngen;
   double rho = net->rho;
-  int *ep = w->ep, *gp = w->gp, *el = w->el, *gl = w->gl;
   double* tprev = w->tprev;
   /* branch update: TRON on eq. exp-branch, warm started from the previous x, delta */
   for (int k = 0; k < nl; k++) ot_admm_branch_record(net, st, k, w->recs + 36 * (size_t)k);
@@ -1149,85 +1223,17 @@ static void admm_after_gens(const ot_net* net, ot_state* st, const ot_opts* o, i
   }
   for (int k = 0; k < nl; k++)
     for (int a = 0; a < 8; a++) tprev[2 * ng + 8 * k + a] = pair_tilde(net, st, k, a);
-  /* bus update: minimise sum rho/2 (xt - a)^2 with a = x + lambda/rho subject to the
-   * bus balance equations (eqs. PowerBalanceReal/Reactive); x = a - D^-1 A' mu with
-   * (A D^-1 A') mu = A a - (p_d, q_d) */
-  for (int b = 0; b < nb; b++) {
-    double rhsP = -net->bus_pd[b], rhsQ = -net->bus_qd[b];
-    double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
-    for (int t = gp[b]; t < gp[b + 1]; t++) {
-      int g = gl[t];
-      rhsP += st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho;
-      rhsQ += st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho;
-      sinv += 1.0 / rho;
-    }
-    for (int t = ep[b]; t < ep[b + 1]; t++) {
-      int e = el[t], k = e / 2, side = e % 2;
-      const double* val = st->br_val + 8 * (size_t)k;
-      const double* lam = st->br_lam + 8 * (size_t)k;
-      int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
-      rhsP -= val[kp] + lam[kp] / rho;
-      rhsQ -= val[kq] + lam[kq] / rho;
-      sinv += 1.0 / rho;
-      Dw += rho;
-      awn += rho * (val[kw] + lam[kw] / rho);
-      athn += rho * (val[kt] + lam[kt] / rho);
-    }
-    double gsh = net->bus_gsh[b], bsh = net->bus_bsh[b];
-    double aw = Dw > 0.0 ? awn / Dw : st->bus_w[b];
-    rhsP -= gsh * aw;
-    rhsQ += bsh * aw;
-    double M11 = sinv, M22 = sinv, M12 = 0.0;
-    if (Dw > 0.0) {
-      M11 += gsh * gsh / Dw;
-      M22 += bsh * bsh / Dw;
-      M12 = -gsh * bsh / Dw;
-    }
-    double det = M11 * M22 - M12 * M12;
-    double mu1 = 0.0, mu2 = 0.0;
-    if (det != 0.0) {
-      mu1 = (M22 * rhsP - M12 * rhsQ) / det;
-      mu2 = (M11 * rhsQ - M12 * rhsP) / det;
-    }
-    for (int t = gp[b]; t < gp[b + 1]; t++) {
-      int g = gl[t];
-      st->gen_tilde[2 * g] = st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho - mu1 / rho;
-      st->gen_tilde[2 * g + 1] =
-          st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho - mu2 / rho;
-    }
-    for (int t = ep[b]; t < ep[b + 1]; t++) {
-      int e = el[t], k = e / 2, side = e % 2;
-      const double* val = st->br_val + 8 * (size_t)k;
-      const double* lam = st->br_lam + 8 * (size_t)k;
-      int kp = side ? 2 : 0, kq = kp + 1;
-      st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho + mu1 / rho;
-      st->br_tilde[4 * (size_t)k + kq] = val[kq] + lam[kq] / rho + mu2 / rho;
-    }
-    if (Dw > 0.0) {
-      st->bus_w[b] = aw - (-gsh * mu1 + bsh * mu2) / Dw;
-      st->bus_th[b] = athn / Dw;
-    }
-  }
-  /* multipliers lambda += rho (x - xt); primal ||x - xt||, dual rho ||xt - xt_prev|| */
+  /* bus updates, then the multipliers and residuals of every pair */
+  for (int b = 0; b < nb; b++) bus_update_one(net, st, w, b);
   double pr2 = 0.0, du2 = 0.0;
-  for (int g = 0; g < ng; g++) {
-    for (int a = 0; a < 2; a++) {
-      double xv = st->gen_pq[2 * g + a], xt = st->gen_tilde[2 * g + a];
-      st->gen_lam[2 * g + a] += rho * (xv - xt);
-      pr2 += (xv - xt) * (xv - xt);
-      double dd = xt - tprev[2 * g + a];
-      du2 += dd * dd;
-    }
-  }
-  for (int k = 0; k < nl; k++) {
-    for (int a = 0; a < 8; a++) {
-      double xv = st->br_val[8 * (size_t)k + a], xt = pair_tilde(net, st, k, a);
-      st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);
-      pr2 += (xv - xt) * (xv - xt);
-      double dd = xt - tprev[2 * ng + 8 * k + a];
-      du2 += dd * dd;
-    }
-  }
+  for (int g = 0; g < ng; g++)
+    for (int a = 0; a < 2; a++)
+      pair_update(&st->gen_lam[2 * g + a], st->gen_pq[2 * g + a], st->gen_tilde[2 * g + a],
+                  tprev[2 * g + a], rho, &pr2, &du2);
+  for (int k = 0; k < nl; k++)
+    for (int a = 0; a < 8; a++)
+      pair_update(&st->br_lam[8 * (size_t)k + a], st->br_val[8 * (size_t)k + a],
+                  pair_tilde(net, st, k, a), tprev[2 * ng + 8 * k + a], rho, &pr2, &du2);
   *pr2_out = pr2;
   *du2_out = du2;
 }
@@ -1259,16 +1265,8 @@ void ot_admm_run(const ot_net* net, ot_state* st, const ot_opts* o, int niters, 
 void ot_admm_phase_components(const ot_net* net, ot_state* st, const ot_opts* o,
                               int nthreads, const uint8_t* gen_mask,
                               const uint8_t* br_mask, ot_counters* total) {
-  double rho = net->rho;
-  for (int g = 0; g < net->ngen; g++) {
-    if (!gen_mask[g]) continue;
-    double pt = st->gen_tilde[2 * g], qt = st->gen_tilde[2 * g + 1];
-    double lp = st->gen_lam[2 * g], lq = st->gen_lam[2 * g + 1];
-    double p = (rho * pt - lp - net->gen_c1[g]) / (2.0 * net->gen_c2[g] + rho);
-    double q = qt - lq / rho;
-    st->gen_pq[2 * g] = proj1(p, net->gen_pmin[g], net->gen_pmax[g]);
-    st->gen_pq[2 * g + 1] = proj1(q, net->gen_qmin[g], net->gen_qmax[g]);
-  }
+  for (int g = 0; g < net->ngen; g++)
+    if (gen_mask[g]) gen_update_one(net, st, g, 1);
   int nl = net->nbranch, m = 0;
   int* ids = (int*)malloc(sizeof(int) * (size_t)(nl + 1));
   for (int k = 0; k < nl; k++)
@@ -1348,70 +1346,13 @@ void ot_admm_phase_buses(const ot_net* net, ot_state* st, const uint8_t* bus_mas
       w.tprev[2 * net->ngen + 8 * k + kp] = st->br_tilde[4 * (size_t)k + kp];
       w.tprev[2 * net->ngen + 8 * k + kp + 1] = st->br_tilde[4 * (size_t)k + kp + 1];
     }
-    double rhsP = -net->bus_pd[b], rhsQ = -net->bus_qd[b];
-    double sinv = 0.0, Dw = 0.0, awn = 0.0, athn = 0.0;
-    for (int t = w.gp[b]; t < w.gp[b + 1]; t++) {
-      int g = w.gl[t];
-      rhsP += st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho;
-      rhsQ += st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho;
-      sinv += 1.0 / rho;
-    }
-    for (int t = w.ep[b]; t < w.ep[b + 1]; t++) {
-      int e = w.el[t], k = e / 2, side = e % 2;
-      const double* val = st->br_val + 8 * (size_t)k;
-      const double* lam = st->br_lam + 8 * (size_t)k;
-      int kp = side ? 2 : 0, kq = kp + 1, kw = side ? 5 : 4, kt = side ? 7 : 6;
-      rhsP -= val[kp] + lam[kp] / rho;
-      rhsQ -= val[kq] + lam[kq] / rho;
-      sinv += 1.0 / rho;
-      Dw += rho;
-      awn += rho * (val[kw] + lam[kw] / rho);
-      athn += rho * (val[kt] + lam[kt] / rho);
-    }
-    double gsh = net->bus_gsh[b], bsh = net->bus_bsh[b];
-    double aw = Dw > 0.0 ? awn / Dw : st->bus_w[b];
-    rhsP -= gsh * aw;
-    rhsQ += bsh * aw;
-    double M11 = sinv, M22 = sinv, M12 = 0.0;
-    if (Dw > 0.0) {
-      M11 += gsh * gsh / Dw;
-      M22 += bsh * bsh / Dw;
-      M12 = -gsh * bsh / Dw;
-    }
-    double det = M11 * M22 - M12 * M12;
-    double mu1 = 0.0, mu2 = 0.0;
-    if (det != 0.0) {
-      mu1 = (M22 * rhsP - M12 * rhsQ) / det;
-      mu2 = (M11 * rhsQ - M12 * rhsP) / det;
-    }
-    for (int t = w.gp[b]; t < w.gp[b + 1]; t++) {
-      int g = w.gl[t];
-      st->gen_tilde[2 * g] = st->gen_pq[2 * g] + st->gen_lam[2 * g] / rho - mu1 / rho;
-      st->gen_tilde[2 * g + 1] =
-          st->gen_pq[2 * g + 1] + st->gen_lam[2 * g + 1] / rho - mu2 / rho;
-    }
-    for (int t = w.ep[b]; t < w.ep[b + 1]; t++) {
-      int e = w.el[t], k = e / 2, side = e % 2;
-      const double* val = st->br_val + 8 * (size_t)k;
-      const double* lam = st->br_lam + 8 * (size_t)k;
-      int kp = side ? 2 : 0, kq = kp + 1;
-      st->br_tilde[4 * (size_t)k + kp] = val[kp] + lam[kp] / rho + mu1 / rho;
-      st->br_tilde[4 * (size_t)k + kq] = val[kq] + lam[kq] / rho + mu2 / rho;
-    }
-    if (Dw > 0.0) {
-      st->bus_w[b] = aw - (-gsh * mu1 + bsh * mu2) / Dw;
-      st->bus_th[b] = athn / Dw;
-    }
+    bus_update_one(net, st, &w, b);
     /* multipliers and residual terms of the pairs whose copies this bus holds */
     for (int t = w.gp[b]; t < w.gp[b + 1]; t++) {
       int g = w.gl[t];
-      for (int a = 0; a < 2; a++) {
-        double xv = st->gen_pq[2 * g + a], xt = st->gen_tilde[2 * g + a];
-        st->gen_lam[2 * g + a] += rho * (xv - xt);
-        pr2 += (xv - xt) * (xv - xt);
-        double dd = xt - w.tprev[2 * g + a];
-        du2 += dd * dd;
-      }
+      for (int a = 0; a < 2; a++)
+        pair_update(&st->gen_lam[2 * g + a], st->gen_pq[2 * g + a], st->gen_tilde[2 * g + a],
+                    w.tprev[2 * g + a], rho, &pr2, &du2);
     }
     for (int t = w.ep[b]; t < w.ep[b + 1]; t++) {
       int e = w.el[t], k = e / 2, side = e % 2;
@@ -1419,12 +1360,9 @@ void ot_admm_phase_buses(const ot_net* net, ot_state* st, const uint8_t* bus_mas
       int as[4] = {kp, kp + 1, side ? 5 : 4, side ? 7 : 6};
       for (int q = 0; q < 4; q++) {
         int a = as[q];
-        double xv = st->br_val[8 * (size_t)k + a], xt = pair_tilde(net, st, k, a);
         double prev = q < 2 ? w.tprev[2 * net->ngen + 8 * k + a] : (q == 2 ? prev_w : prev_th);
-        st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);
-        pr2 += (xv - xt) * (xv - xt);
-        double dd = xt - prev;
-        du2 += dd * dd;
+        pair_update(&st->br_lam[8 * (size_t)k + a], st->br_val[8 * (size_t)k + a],
+                    pair_tilde(net, st, k, a), prev, rho, &pr2, &du2);
       }
     }
   }

@@ -363,6 +363,24 @@ __global__ void k_pivot_rcp(const double* a, double* out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = pivot_rcp(a[i]);
 }
+
+// FP64 FMA throughput: 8 independent dependent chains per thread (enough to cover the
+// FMA latency with a few warps per SM sub-partition); the factor and increment keep the
+// values bounded, and the result is written so nothing is eliminated
+__global__ void k_fp64_fma(double* out, int64_t iters) {
+  const double a = 0.9999999, b = 1e-7;
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = (double)(threadIdx.x + k);
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fma(v[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += v[k];
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 }  // namespace xt
 
 static tron_err_t check_options(const tron_options_t* o) {
@@ -387,6 +405,17 @@ extern "C" {
 
 const char* tron_last_error(void) { return g_err.c_str(); }
 const char* tron_version(void) { return "exatron-gb300 0.1 (sm_103a, FP64)"; }
+
+tron_err_t tron_bench_fp64_fma(double* d_out, int32_t blocks, int32_t threads, int64_t iters,
+                               void* stream) {
+  clear_error();
+  XT_REQUIRE(d_out != nullptr, TRON_EINVAL, "tron_bench_fp64_fma: d_out is NULL");
+  XT_REQUIRE(blocks > 0 && threads > 0 && threads <= 1024 && threads % 32 == 0 && iters > 0,
+             TRON_EINVAL, "tron_bench_fp64_fma: bad launch size");
+  xt::k_fp64_fma<<<(unsigned)blocks, (unsigned)threads, 0, (cudaStream_t)stream>>>(d_out, iters);
+  XT_CUDA(cudaGetLastError());
+  return TRON_OK;
+}
 
 tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void* stream) {
   clear_error();

@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
             "tron_last_error": (C.c_char_p, []),
             "tron_version": (C.c_char_p, []),
             "tron_test_pivot_rcp": (I32, [P, P, I64, P]),
+            "tron_bench_fp64_fma": (I32, [P, I32, I32, I64, P]),
             "admm_create": (I32, [C.POINTER(P), C.POINTER(AdmmNetwork), C.POINTER(TronOptions),
                                   P]),
             "admm_step": (I32, [P, I32, P, P, P]),

@@ -42,9 +42,10 @@ class AdmmServer:
         self.max_iters = int(max_iters)
 
     def run(self, requests, clock=time.perf_counter, keep_state: bool = False):
-        """requests: list of dict(t=arrival offset in s, net=network dict, id=...).
-        Returns one record per request: arrival, admitted, finished (s from the start),
-        iterations, residuals, converged."""
+        """requests: list of dict(t=arrival offset in s, net=network dict, id=..., and
+        optionally rho, the instance's penalty).  Returns one record per request:
+        arrival, admitted, finished (s from the start), iterations, residuals,
+        converged."""
         pending = collections.deque(sorted(requests, key=lambda r: r["t"]))
         live = {}
         done = []
@@ -53,7 +54,9 @@ class AdmmServer:
         while pending or live:
             now = clock() - t0
             while pending and pending[0]["t"] <= now:
-                inst = self.pool.add(pending[0]["net"])
+                req0 = pending[0]
+                inst = (self.pool.add(req0["net"], rho=req0["rho"]) if "rho" in req0
+                        else self.pool.add(req0["net"]))
                 if inst is None:
                     break  # no room until some instance retires
                 req = pending.popleft()
@@ -92,7 +95,7 @@ def serial_plain(requests, chunk: int = 8, tol: float = 1e-4, max_iters: int = 2
     out = []
     t_free = 0.0
     for req in sorted(requests, key=lambda r: r["t"]):
-        a = Admm(req["net"])
+        a = Admm(req["net"], rho=req.get("rho", 400.0))
         torch.cuda.synchronize()
         s0 = clock()
         its, conv = 0, False

@@ -241,10 +241,11 @@ def genramp_batch(B: int = 3000, T: int = 24, seed_index: int = 8, rho: float = 
 
 
 def serving_stream(duration_s: float = 60.0, rate_hz: float = 200.0, seed_index: int = 4,
-                   bus_lo: int = 500, bus_hi: int = 20000):
+                   bus_lo: int = 500, bus_hi: int = 20000, load_lo: float = 0.8,
+                   load_hi: float = 1.2):
     """Poisson arrivals of independent ADMM instances: arrival times, bus counts
     log-uniform in [bus_lo, bus_hi] (branches 1.3x, generators 0.3x), load scaling
-    U[0.8, 1.2] and a per-instance seed."""
+    U[load_lo, load_hi] and a per-instance seed."""
     rng = rng_for(seed_index)
     t, out = 0.0, []
     while True:
@@ -254,7 +255,7 @@ def serving_stream(duration_s: float = 60.0, rate_hz: float = 200.0, seed_index:
         nb = int(round(math.exp(rng.uniform(math.log(bus_lo), math.log(bus_hi)))))
         out.append(dict(t=t, nbus=nb, nchord=int(round(0.3 * nb)),
                         ngen=max(1, int(round(0.3 * nb))),
-                        load_scale=float(rng.uniform(0.8, 1.2)),
+                        load_scale=float(rng.uniform(load_lo, load_hi)),
                         seed=int(rng.integers(0, 2**31 - 1))))
     return out
 

@@ -62,8 +62,8 @@ MUTATIONS = [
      "double p = (rho * pt - lp) / (2.0 * net->gen_c2[g] + rho);",
      [pins.test_admm_generator_update_is_scalar_qp_minimiser]),
     ("ADMM multiplier update sign",
-     "st->br_lam[8 * (size_t)k + a] += rho * (xv - xt);",
-     "st->br_lam[8 * (size_t)k + a] -= rho * (xv - xt);",
+     "*lam += rho * (xv - xt);",
+     "*lam -= rho * (xv - xt);",
      [pins.test_admm_bus_update_kkt_and_multipliers]),
     ("generator chain: sign of the ramp gradient",
      "g[t] += rr * e * s;", "g[t] -= rr * e * s;",
