@@ -650,6 +650,8 @@ def summary(line: dict) -> dict:
                 "p50_s": r(x["served"]["p50_s"], 3), "p99_s": r(x["served"]["p99_s"], 3),
                 "serial_p50_s": r(x["serial_plain"]["p50_s"], 3),
                 "serial_p99_s": r(x["serial_plain"]["p99_s"], 3),
+                "p50_converged_s": r(x["served"]["p50_converged_s"], 3),
+                "serial_p50_converged_s": r(x["serial_plain"]["p50_converged_s"], 3),
                 "iters_per_s": r(x["served"]["agg_iters_per_s"]),
                 "serial_iters_per_s": r(x["serial_plain"]["agg_iters_per_s"])}
     return out

@@ -59,6 +59,28 @@ def test_admm_long_trajectory_matches_oracle(group, nb, seed, K):
     g.close()
 
 
+def test_admm_light_load_rho10_converges_where_the_oracle_does():
+    # an instance of the serving benchmark's convergent request set (515 buses, a tenth
+    # of the stated load, rho 10): the GPU trajectory follows the oracle's through
+    # convergence, and both first reach primal and dual <= 1e-4 at the same iteration
+    specs = synth.serving_stream(duration_s=0.5, rate_hz=200.0, seed_index=5, bus_lo=500,
+                                 bus_hi=2000, load_lo=0.08, load_hi=0.12)
+    spec = specs[78]
+    assert spec["nbus"] == 515
+    net = synth.instance_network(spec)
+    K = 1200
+    g = Admm(net, rho=10.0)
+    g.step(K)
+    hp_g, hd_g = g.history(0, K)
+    g.close()
+    hp_o, hd_o = oracle.Admm(net, rho=10.0).run(K, nthreads=8)
+    np.testing.assert_allclose(hp_g, hp_o, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(hd_g, hd_o, rtol=1e-6, atol=0)
+    first_g = np.nonzero((hp_g <= 1e-4) & (hd_g <= 1e-4))[0]
+    first_o = np.nonzero((hp_o <= 1e-4) & (hd_o <= 1e-4))[0]
+    assert first_o.size and first_g.size and first_g[0] == first_o[0]
+
+
 def test_admm_2000_bus_trajectory_matches_oracle():
     net = small_net(2000, 13)
     K = 150
