@@ -967,3 +967,24 @@ def test_branch_solves_at_an_admm_state_all_converge():
                           nthreads=4)
     assert np.all(r["status"] == oracle.CONVERGED), np.bincount(r["status"])
     assert np.all(r["pg"] <= 1e-6)
+
+
+def test_admm_phases_on_masks_reproduce_the_iteration():
+    # the phase entry points (components on a mask; buses on a mask, each with the
+    # multipliers of the pairs it holds) performed over all components -- the buses in
+    # two disjoint masks -- give the undivided iteration's iterates bit for bit, and its
+    # residuals up to the order of the sums
+    net = synth.network(150, 40, 50, rng=np.random.default_rng(17))
+    nl, ng, nb = len(net["br_from"]), len(net["gen_bus"]), net["nbus"]
+    ref = oracle.Admm(net)
+    hp, hd = ref.run(25)
+    ph = oracle.Admm(net)
+    half = np.arange(nb) % 2 == 0
+    for it in range(25):
+        ph.phase_components(np.ones(ng), np.ones(nl))
+        p1, d1 = ph.phase_buses(half)
+        p2, d2 = ph.phase_buses(~half)
+        assert abs(math.sqrt(p1 + p2) - hp[it]) <= 1e-12 * hp[it]
+        assert abs(400.0 * math.sqrt(d1 + d2) - hd[it]) <= 1e-12 * hd[it]
+    for k in ref.arrays:
+        np.testing.assert_array_equal(ph.arrays[k], ref.arrays[k], err_msg=k)
