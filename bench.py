@@ -53,7 +53,7 @@ def hbm_peak_gbs():
 # executes (thread-level DFMA x 2 + DADD + DMUL: 301.9 Mflop per 2,000 problems).
 TRAFFIC_BYTES_PER_PROBLEM = 19.080448e6 / 2000
 EXEC_FLOPS_PER_PROBLEM = (2 * 128644296 + 25309882 + 19319289) / 2000
-TRAFFIC_SOURCES_SHA1 = "5b4c638fb4e512bc71ddeb541852d9897074178c"
+TRAFFIC_SOURCES_SHA1 = "72af9b8588737b2d42e479d7d0844746ce5fe616"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 

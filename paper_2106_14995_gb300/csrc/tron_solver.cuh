@@ -602,11 +602,12 @@ struct Solver {
   // for step: the same step lengths (rhat'rhat = res'M^-1 res, phat'Ahat phat = p'Ap)
   // and the same exits.  Algorithm 1's trust region bounds the CG iterate,
   // ||s||_2 = ||w||_M <= delta (options.tr_norm 0); its M-inner products come from the
-  // recurrences of preconditioned CG, with no product by M:
-  //   ||w + alpha p||_M^2 = ww + 2 alpha wp + alpha^2 pp,
-  //   <w', p'>_M = beta (wp + alpha pp),   ||p'||_M^2 = res''M^-1 res' + beta^2 pp,
-  // which hold because res' is orthogonal to every earlier direction (w' lies in their
-  // span and M p' = res' + beta M p).  tr_norm 1 bounds ||w||_2 instead.  When alpha = 0,
+  // recurrences of preconditioned CG, with no product by M (w1, p1, res1: the next
+  // iterate, direction and residual):
+  //   ||w1||_M^2 = ||w + alpha p||_M^2 = ww + 2 alpha wp + alpha^2 pp,
+  //   <w1, p1>_M = beta (wp + alpha pp),   ||p1||_M^2 = res1' M^-1 res1 + beta^2 pp,
+  // which hold because res1 is orthogonal to every earlier direction (w1 lies in their
+  // span, and M p1 = res1 + beta M p).  tr_norm 1 bounds ||w||_2 instead.  When alpha = 0,
   // M = A and Ahat = I: the first step, of length 1 along M^-1 res, is the minimiser and
   // leaves a zero residual, so it is taken without forming A p; its length is
   // ||M^-1 res||_M^2 = res'M^-1 res.
