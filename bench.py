@@ -53,7 +53,7 @@ def hbm_peak_gbs():
 # executes (thread-level DFMA x 2 + DADD + DMUL: 301.9 Mflop per 2,000 problems).
 TRAFFIC_BYTES_PER_PROBLEM = 19.080448e6 / 2000
 EXEC_FLOPS_PER_PROBLEM = (2 * 128644296 + 25309882 + 19319289) / 2000
-TRAFFIC_SOURCES_SHA1 = "72af9b8588737b2d42e479d7d0844746ce5fe616"
+TRAFFIC_SOURCES_SHA1 = "5688f08d527231c425041422c615fe202dbffa6f"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
@@ -301,8 +301,8 @@ def bench_admm(args, dev, peak_measured):
     net = synth.network(10000, 3000, 3000, seed_index=2)
     nl, ng, nb = len(net["br_from"]), len(net["gen_bus"]), int(net["nbus"])
 
-    def run(group, tr_norm=0):
-        a = Admm(net, opts=options(group=group, tr_norm=tr_norm))
+    def run(group, tr_norm=0, cauchy_norm=0):
+        a = Admm(net, opts=options(group=group, tr_norm=tr_norm, cauchy_norm=cauchy_norm))
         grp = a.branch_group
         a.step(16)  # graph capture and the first iterations, untimed
         torch.cuda.synchronize(dev)
@@ -317,6 +317,7 @@ def bench_admm(args, dev, peak_measured):
     pr, du, dt, counts, grp = run(0)
     _, _, dt_o, _, grp_o = run(4 if grp == 1 else 1)
     _, _, dt_e, _, _ = run(0, tr_norm=1)  # the other reading of the PCG's norm
+    _, _, dt_h, _, _ = run(0, cauchy_norm=1)  # the Cauchy test in the Hessian's norm
     cores = os.cpu_count() or 1
     o = oracle.Admm(net)
     o.run(16, nthreads=cores)  # the iterations the GPU run did untimed
@@ -336,6 +337,8 @@ def bench_admm(args, dev, peak_measured):
                               "value": args.admm_iters / dt_o, "unit": "ADMM iters/s"},
             "euclidean_reading": {"value": args.admm_iters / dt_e, "unit": "ADMM iters/s",
                                   "note": "options.tr_norm = 1 (PCG step bounded in ||w||_2)"},
+            "hessian_cauchy": {"value": args.admm_iters / dt_h, "unit": "ADMM iters/s",
+                               "note": "options.cauchy_norm = 1 (Cauchy test in (s'Hs)^(1/2))"},
             "roofline": fp64_roofline(flops_it, sec_it, peak_measured,
                                       f"k_admm_branch_gen<{grp}> + k_admm_bus",
                                       {"flops_per_iter": flops_it,
@@ -417,9 +420,10 @@ def bench_branch256(args, dev, peak_measured):
     P, L, U, X0, D0 = t(d["params"]), t(d["l"]), t(d["u"]), t(d["x0"]), t(d["delta0"])
     scrub = torch.zeros(2 * L2_BYTES // 8, dtype=torch.float64, device=dev)
     res = {}
-    for name, grp, trn in (("default", 0, 0), ("one_lane", 1, 0), ("four_lanes", 4, 0),
-                           ("euclidean_reading", 0, 1)):
-        tb = TronBatch(1, B, n=4, opts=options(group=grp, tr_norm=trn))
+    for name, grp, trn, cn in (("default", 0, 0, 0), ("one_lane", 1, 0, 0),
+                               ("four_lanes", 4, 0, 0), ("euclidean_reading", 0, 1, 0),
+                               ("hessian_cauchy", 0, 0, 1)):
+        tb = TronBatch(1, B, n=4, opts=options(group=grp, tr_norm=trn, cauchy_norm=cn))
         ts = []
         for rep in range(12):
             x, de = X0.clone(), D0.clone()
@@ -550,13 +554,16 @@ def bench_multiperiod(args, dev, peak_measured):
     T = 24
     scale = synth.load_profile(T)
     ramp = 0.05 * net["gen_pmax"]
-    ge = AdmmMultiPeriod(net, scale, ramp=ramp, rho_ramp=1e4, opts=options(tr_norm=1))
-    ge.step(4)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    ge.step(args.mp_iters)
-    dt_e = time.perf_counter() - t0
-    ge.close()
+    alt = {}
+    for key, opt in (("euclidean_reading", options(tr_norm=1)),
+                     ("hessian_cauchy", options(cauchy_norm=1))):
+        ge = AdmmMultiPeriod(net, scale, ramp=ramp, rho_ramp=1e4, opts=opt)
+        ge.step(4)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ge.step(args.mp_iters)
+        alt[key] = time.perf_counter() - t0
+        ge.close()
     g = AdmmMultiPeriod(net, scale, ramp=ramp, rho_ramp=1e4)
     g.step(4)  # graph capture and the first iterations, untimed
     torch.cuda.synchronize(dev)
@@ -584,8 +591,10 @@ def bench_multiperiod(args, dev, peak_measured):
             "gen_status_last_iter": counts,
             "max_ramp_step_over_limit": float(np.max(np.abs(np.diff(p, axis=0)) -
                                                      ramp[None, :])),
-            "euclidean_reading": {"value": args.mp_iters / dt_e, "unit": "ADMM iters/s",
-                                  "note": "options.tr_norm = 1"},
+            "euclidean_reading": {"value": args.mp_iters / alt["euclidean_reading"],
+                                  "unit": "ADMM iters/s", "note": "options.tr_norm = 1"},
+            "hessian_cauchy": {"value": args.mp_iters / alt["hessian_cauchy"],
+                               "unit": "ADMM iters/s", "note": "options.cauchy_norm = 1"},
             "roofline": fp64_roofline(flops_it, sec_it, peak_measured,
                                       "branch + generator-chain + bus kernels",
                                       {"flops_per_iter": flops_it,
@@ -688,12 +697,14 @@ def summary(line: dict) -> dict:
         out["branch256"] = {"ms": r(b["ms"]), "subproblems_per_s": r(b["value"]),
                             "e2e_ms": r(b["e2e_ms"]),
                             "euclidean_ms": r(b["mappings"]["euclidean_reading"]["ms"]),
+                            "hessian_cauchy_ms": r(b["mappings"]["hessian_cauchy"]["ms"]),
                             "cpu": r(b["cpu_baseline"]["value"])}
     a = line.get("admm")
     if a:
         out["admm10k"] = {"iters_per_s": r(a["value"]), "frac": r(a["roofline"]["frac"], 3),
                           "other_mapping": r(a["other_mapping"]["value"]),
                           "euclidean": r(a["euclidean_reading"]["value"]),
+                          "hessian_cauchy": r(a["hessian_cauchy"]["value"]),
                           "cpu": r(a["cpu_baseline"]["value"])}
     u = line.get("uneven")
     if u:
@@ -706,6 +717,7 @@ def summary(line: dict) -> dict:
     if m:
         out["multiperiod"] = {"iters_per_s": r(m["value"]),
                               "euclidean": r(m["euclidean_reading"]["value"]),
+                              "hessian_cauchy": r(m["hessian_cauchy"]["value"]),
                               "cpu": r(m["cpu_baseline"]["value"])}
     sv = line.get("serving")
     if sv:

@@ -136,7 +136,12 @@ typedef struct tron_options {
                                     each subspace search step beta w in ||L^T .||_2);
                                     1 = the step itself, ||w||_2 <= delta, with the radius
                                     update on ||x+ - x||_2                                 */
-  int32_t reserved[4];    /* must be zero                                                */
+  int32_t cauchy_norm;    /* 0      norm of the Cauchy step's trust-region test: 0 = ||s||_2;
+                                    1 = the model Hessian's norm (s'Hs)^(1/2) where s'Hs > 0
+                                    (else ||s||_2), the norm in which the PCG's bound
+                                    ||L^T w|| is nearly stated, so one radius suits both
+                                    steps (with tr_norm 0)                                */
+  int32_t reserved[3];    /* must be zero                                                */
 } tron_options_t;
 
 typedef struct tron_batch tron_batch_t;

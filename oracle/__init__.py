@@ -57,6 +57,7 @@ class Opts(C.Structure):
         ("sigma1", C.c_double), ("sigma3", C.c_double), ("delta_max", C.c_double),
         ("delta_min_rel", C.c_double), ("cg_rtol", C.c_double), ("shift_frac", C.c_double),
         ("max_shift", C.c_int32), ("tr_norm", C.c_int32), ("ared_guard", C.c_double),
+        ("cauchy_norm", C.c_int32), ("pad1", C.c_int32),
     ]
 
 

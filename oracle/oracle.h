@@ -50,6 +50,9 @@ typedef struct ot_opts {
                                    of the preconditioned system, ||s|| = ||L^T w|| (Algorithm 1),
                                    1 = the step itself, ||w|| */
   double ared_guard;            /* rounding guard of the ratio, times max(1, magnitude of the terms of f) */
+  int32_t cauchy_norm;          /* norm of the Cauchy step's trust-region test: 0 = ||s||_2,
+                                   1 = ||s||_H = (s'Hs)^(1/2) where s'Hs > 0, else ||s||_2 */
+  int32_t pad1;
 } ot_opts;
 
 typedef struct ot_counters {

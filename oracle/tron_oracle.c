@@ -52,6 +52,8 @@ void ot_default_opts(ot_opts* o) {
   o->max_shift = 30;
   o->tr_norm = 0;
   o->ared_guard = 1e-13;
+  o->cauchy_norm = 0;
+  o->pad1 = 0;
 }
 
 /* ------------------------------------------------------------ Figure 2 core operations */
@@ -626,6 +628,18 @@ double ot_fscale(int kind, int n, const double* params, const double* x) {
   return S;
 }
 
+/* length of a Cauchy trial s for its trust-region test: ||s||_2, or (cauchy_norm 1) the
+ * norm of the model's Hessian, (s'Hs)^(1/2), where s'Hs > 0; Hs = H s is given */
+static double cauchy_len(int n, const double* s, const double* Hs, const ot_opts* o,
+                         ot_counters* c) {
+  if (o->cauchy_norm == 1) {
+    double h = dot(n, s, Hs, NULL);  /* s'Hs: the model value's product, already counted */
+    if (c) c->flops += 1.0;
+    if (h > 0.0) return sqrt(h);
+  }
+  return nrm2(n, s, c);
+}
+
 static int all_finite(int n, const double* v) {
   for (int i = 0; i < n; i++)
     if (!isfinite(v[i])) return 0;
@@ -715,7 +729,7 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
       gemv(n, H, n, s, Hd, c);
       double gts = dot(n, g, s, c);
       double q = gts + 0.5 * dot(n, s, Hd, c);
-      ok = (q <= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta);
+      ok = (q <= o->mu0 * gts) && (cauchy_len(n, s, Hd, o, c) <= o->mu1 * delta);
       c->cauchy_trials++;
     }
     if (ok) {
@@ -731,7 +745,7 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
         double gts = dot(n, g, s, c);
         double q = gts + 0.5 * dot(n, s, Hd, c);
         c->cauchy_trials++;
-        if (!((q <= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta))) break;
+        if (!((q <= o->mu0 * gts) && (cauchy_len(n, s, Hd, o, c) <= o->mu1 * delta))) break;
         alpha = a2;
       }
     } else {
@@ -742,7 +756,7 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
         double gts = dot(n, g, s, c);
         double q = gts + 0.5 * dot(n, s, Hd, c);
         c->cauchy_trials++;
-        if ((q <= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta)) break;
+        if ((q <= o->mu0 * gts) && (cauchy_len(n, s, Hd, o, c) <= o->mu1 * delta)) break;
       }
     }
     alpha_c = alpha;
@@ -754,7 +768,8 @@ int ot_tron_solve(int kind, int n, const double* params, const double* l, const 
     double nu = 0.0;
     if (o->tr_norm == 0) {
       for (int i = 0; i < n; i++) d[i] = y[i] - x[i];
-      nu = nrm2(n, d, c);
+      if (o->cauchy_norm == 1) gemv(n, H, n, d, yt, NULL);  /* H s of the accepted trial */
+      nu = cauchy_len(n, d, yt, o, c);
     }
 
     /* ---- Algorithm 1's subspace step, repeated on the current face: free set, shifted complete

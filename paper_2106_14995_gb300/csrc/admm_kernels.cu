@@ -678,6 +678,8 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
              "admm: options.group must be 0, 1 or 4");
   XT_REQUIRE(!opt || opt->tr_norm == 0 || opt->tr_norm == 1, TRON_EINVAL,
              "admm: options.tr_norm must be 0 or 1");
+  XT_REQUIRE(!opt || opt->cauchy_norm == 0 || opt->cauchy_norm == 1, TRON_EINVAL,
+             "admm: options.cauchy_norm must be 0 or 1");
   admm_pool* p = new admm_pool();
   memset(&p->d, 0, sizeof(p->d));
   p->cap_stream = nullptr;

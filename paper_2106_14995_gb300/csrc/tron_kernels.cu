@@ -398,6 +398,8 @@ static tron_err_t check_options(const tron_options_t* o) {
              "options.cholesky must be 0, 1 or 2");
   XT_REQUIRE(o->ctas_per_sm >= 0, TRON_EINVAL, "options.ctas_per_sm must be >= 0");
   XT_REQUIRE(o->tr_norm == 0 || o->tr_norm == 1, TRON_EINVAL, "options.tr_norm must be 0 or 1");
+  XT_REQUIRE(o->cauchy_norm == 0 || o->cauchy_norm == 1, TRON_EINVAL,
+             "options.cauchy_norm must be 0 or 1");
   return TRON_OK;
 }
 

@@ -698,7 +698,9 @@ struct Solver {
     return info;
   }
 
-  // Cauchy trial s(alpha) = P[x - alpha g] - x: q(s) <= mu0 g's and ||s|| <= mu1 delta.
+  // Cauchy trial s(alpha) = P[x - alpha g] - x: q(s) <= mu0 g's and ||s|| <= mu1 delta
+  // (||s||_2, or with options.cauchy_norm 1 the model Hessian's norm (s'Hs)^(1/2) where
+  // s'Hs > 0).
   // kap = 0 for the first trial of a search (full product); otherwise alpha is kap times
   // the step length of the trial held in s, Hs, cl (clipped coordinates), and H s is
   // rescaled from it.  inside: alpha is below the largest breakpoint along -g (breakpt of
@@ -739,10 +741,13 @@ struct Solver {
       ss = fma(s[r], s[r], ss);
     }
     gp.sum3(gts, sHs, ss);
-    ssq = ss;
+    // squared length for the trust-region test: ||s||_2^2, or (cauchy_norm 1) s'Hs where
+    // it is positive
+    const double len2 = (o.cauchy_norm == 1 && okey(sHs) > 0) ? sHs : ss;
+    ssq = len2;
     const double q = gts + 0.5 * sHs;
     const double bound = o.mu1 * delta;
-    return le(q, o.mu0 * gts) && le(ss, bound * bound);
+    return le(q, o.mu0 * gts) && le(len2, bound * bound);
   }
 
   __device__ __forceinline__ bool all_finite(const double (&v)[R]) const {
@@ -848,7 +853,7 @@ struct Solver {
       bool cl[R];
       double alpha = alpha_c;
       bool inside;
-      double ssc;  // squared length of the accepted Cauchy step
+      double ssc;  // squared length of the accepted Cauchy step (in the test's norm)
       if (cauchy_try(alpha, x, g, delta, s, Hs, cl, 0.0, inside, ssc)) {
         double sb[R], Hsb[R];
 #pragma unroll

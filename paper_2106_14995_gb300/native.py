@@ -34,7 +34,8 @@ class TronOptions(C.Structure):
         ("cg_rtol", C.c_double), ("shift_frac", C.c_double), ("max_shift", C.c_int32),
         ("group", C.c_int32), ("ared_guard", C.c_double), ("schedule", C.c_int32),
         ("warps_per_block", C.c_int32), ("layout", C.c_int32), ("cholesky", C.c_int32),
-        ("ctas_per_sm", C.c_int32), ("tr_norm", C.c_int32), ("reserved", C.c_int32 * 4),
+        ("ctas_per_sm", C.c_int32), ("tr_norm", C.c_int32), ("cauchy_norm", C.c_int32),
+        ("reserved", C.c_int32 * 3),
     ]
 
 

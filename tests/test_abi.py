@@ -44,7 +44,8 @@ def test_options_defaults_match_oracle_readings():
     r = oracle.default_opts()
     for f in ("gtol", "max_outer", "max_trials", "mu0", "mu1", "interpf", "extrapf",
               "proj_shrink", "eta0", "eta1", "eta2", "sigma1", "sigma3", "delta_max",
-              "delta_min_rel", "cg_rtol", "shift_frac", "max_shift", "ared_guard", "tr_norm"):
+              "delta_min_rel", "cg_rtol", "shift_frac", "max_shift", "ared_guard", "tr_norm",
+              "cauchy_norm"):
         assert getattr(o, f) == getattr(r, f), f
     assert o.group == 0 and o.schedule == native.TRON_SCHED_PLAIN
 

@@ -59,6 +59,19 @@ def test_admm_long_trajectory_matches_oracle(group, nb, seed, K):
     g.close()
 
 
+@pytest.mark.parametrize("group", [1, 4])
+def test_admm_with_the_hessian_norm_cauchy_option_matches_oracle(group):
+    net = small_net(120, 11)
+    K = 300
+    g = Admm(net, opts=options(group=group, cauchy_norm=1))
+    g.step(K)
+    hp_g, hd_g = g.history(0, K)
+    g.close()
+    hp_o, hd_o = oracle.Admm(net).run(K, opts=oracle.default_opts(cauchy_norm=1), nthreads=8)
+    np.testing.assert_allclose(hp_g, hp_o, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(hd_g, hd_o, rtol=1e-6, atol=0)
+
+
 def test_admm_light_load_rho10_converges_where_the_oracle_does():
     # an instance of the serving benchmark's convergent request set (515 buses, a tenth
     # of the stated load, rho 10): the GPU trajectory follows the oracle's through

@@ -43,8 +43,8 @@ MUTATIONS = [
      "res[i] -= alpha * q[i];", "res[i] -= 0.0 * q[i];",
      [pins.test_steihaug_one_iteration_on_pd]),
     ("Cauchy search: sufficient-decrease test reversed",
-     "ok = (q <= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta);",
-     "ok = (q >= o->mu0 * gts) && (nrm2(n, s, c) <= o->mu1 * delta);",
+     "ok = (q <= o->mu0 * gts) && (cauchy_len(n, s, Hd, o, c) <= o->mu1 * delta);",
+     "ok = (q >= o->mu0 * gts) && (cauchy_len(n, s, Hd, o, c) <= o->mu1 * delta);",
      [pins.test_separable_quadratic_closed_form, pins.test_newton_step_solves_an_interior_quadratic_in_one_iteration]),
     ("back transform: direction sign",
      "for (int a = 0; a < m; a++) w[F[a]] = sh[a];",
@@ -132,6 +132,12 @@ MUTATIONS = [
      "double fl = o->ared_guard * (fs > 1.0 ? fs : 1.0);",
      "double fl = o->ared_guard * (fabs(f) > 1.0 ? fabs(f) : 1.0);",
      [pins.test_branch_solves_at_an_admm_state_all_converge]),
+    ("Hessian-norm Cauchy test: no fallback where s'Hs <= 0",
+     "    if (h > 0.0) return sqrt(h);\n", "    return sqrt(fabs(h));\n",
+     [pins.test_cauchy_test_in_the_hessian_norm_option]),
+    ("Hessian-norm Cauchy test: the option ignored",
+     "  if (o->cauchy_norm == 1) {\n    double h", "  if (o->cauchy_norm == 7) {\n    double h",
+     [pins.test_cauchy_test_in_the_hessian_norm_option]),
     ("guard scale: the branch flows' own terms left out",
      "mag += fabs(lam[k] * r) + 0.5 * rh[k] * r * r + (fabs(lam[k]) + rh[k] * fabs(r)) * M[k];",
      "mag += fabs(lam[k] * r) + 0.5 * rh[k] * r * r;",

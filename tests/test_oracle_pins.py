@@ -988,3 +988,33 @@ def test_admm_phases_on_masks_reproduce_the_iteration():
         assert abs(400.0 * math.sqrt(d1 + d2) - hd[it]) <= 1e-12 * hd[it]
     for k in ref.arrays:
         np.testing.assert_array_equal(ph.arrays[k], ref.arrays[k], err_msg=k)
+
+
+def test_cauchy_test_in_the_hessian_norm_option():
+    # options cauchy_norm = 1: the Cauchy trial's trust-region test uses
+    # ||s||_H = (s'Hs)^(1/2).  f = 5 x^2 - x, x0 = 0, delta = 0.015 (H = 10):
+    # alpha = 1, 0.1, 0.01 give ||s||_H = sqrt(10) |s| = 3.16, 0.316, 0.0316 > delta;
+    # alpha = 0.001 gives 0.00316: four trials, x_c = 0.001.  PCG: r = -1 + 10 x_c = -0.99,
+    # the CG iterate's Newton length 0.99/sqrt(10) > delta, so w = delta/sqrt(10) on the
+    # boundary; x1 = 0.001 + 0.015/sqrt(10), rho = 1 and the step reached the boundary in
+    # the PCG's norm: delta = 0.06
+    r = _dense1([10.0], [-1.0], [0.0], [0.0], 0.015, cauchy_norm=1)
+    assert r["status"] == oracle.MAX_ITER and r["iters"] == 1
+    assert r["counters"]["cauchy_trials"] == 4
+    assert abs(r["x"][0] - (0.001 + 0.015 / math.sqrt(10.0))) < 1e-15
+    assert r["delta"] == 0.06
+    # where s'Hs <= 0 (negative curvature along -g) the test falls back to ||s||_2:
+    # f = -0.02 x^2 - x on [-100, 100] from 0, delta = 25: alpha = 1 and 10 hold
+    # (||s||_2 = 1, 10), alpha = 100 does not (100 > 25): x_c = 10 after three trials,
+    # exactly as with cauchy_norm = 0.  The subspace step follows the negative curvature
+    # to the PCG's boundary (length 25 = delta in its norm) and the projected search to
+    # the bound x = 100; the step reached the radius, rho = 1: delta = 4 * 25.  (A test on
+    # |s'Hs|^(1/2) = 0.2 |s| would accept alpha = 100, leave no free variable and keep
+    # delta = 25.)
+    kw = dict(l=-100.0, u=100.0)
+    a = _dense1([-0.04], [-1.0], [0.0], [0.0], 25.0, cauchy_norm=1, **kw)
+    b = _dense1([-0.04], [-1.0], [0.0], [0.0], 25.0, cauchy_norm=0, **kw)
+    assert a["counters"]["cauchy_trials"] == b["counters"]["cauchy_trials"] == 3
+    assert a["counters"]["subspace_passes"] == b["counters"]["subspace_passes"] == 1
+    np.testing.assert_array_equal(a["x"], b["x"])
+    assert a["delta"] == b["delta"] == 100.0

@@ -158,6 +158,29 @@ def test_trust_region_norm_readings_match_oracle(tr_norm):
         assert np.mean(g["iters"] == r["iters"]) >= 0.95
 
 
+def test_hessian_norm_cauchy_option_matches_oracle():
+    # options.cauchy_norm = 1: the Cauchy trial's trust-region test in the model
+    # Hessian's norm (s'Hs)^(1/2) where s'Hs > 0, against the oracle with the same option
+    d = synth.dense_batch(160, 32, seed_index=17)
+    g = gpu_solve(d, n=32, cauchy_norm=1)
+    r = oracle_solve(d, cauchy_norm=1)
+    assert_convex_parity(g, r, d["l"], d["u"])
+    assert np.mean(g["iters"] == r["iters"]) >= 0.95
+    br = synth.branch_batch(160, seed_index=19)
+    for group in (1, 4):
+        g = gpu_solve(br, n=4, group=group, cauchy_norm=1)
+        r = oracle_solve(br, cauchy_norm=1)
+        assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
+        same = np.all(np.abs(g["x"] - r["x"]) <= 1e-6, axis=1)
+        assert same.mean() >= 0.98
+        assert np.mean(g["iters"] == r["iters"]) >= 0.95
+    gr = synth.genramp_batch(96, 24, seed_index=21)
+    g = gpu_solve(gr, n=24, cauchy_norm=1)
+    r = oracle_solve(gr, cauchy_norm=1)
+    assert np.all(g["status"] == native.TRON_CONVERGED) and np.all(r["status"] == 0)
+    np.testing.assert_allclose(g["x"], r["x"], rtol=0, atol=1e-6)
+
+
 def test_branch_default_group_follows_batch_size():
     # the library's mapping of the branch problems: four lanes per problem up to 40
     # problems per SM sub-partition, one lane beyond; an explicit group wins
