@@ -289,8 +289,9 @@ def admm_bytes_per_iteration(nl, ng, nb):
 
 def bench_admm(args, dev, peak_measured):
     """Component ADMM on a 10,000-bus network (13,000 branches, 3,000 generators):
-    ADMM iterations/s over args.admm_iters iterations (two launches per iteration,
-    replayed CUDA graphs), with both branch mappings; the oracle runs the same
+    ADMM iterations/s over args.admm_iters iterations (two launches per iteration, three
+    when one-lane solves finish on four lanes; replayed CUDA graphs), with both branch
+    mappings; the oracle runs the same
     iterations on the host cores (its time is the CPU baseline and its flop count the
     roofline's algorithmic work; the two trajectories agree to rounding)."""
     import torch
@@ -304,6 +305,7 @@ def bench_admm(args, dev, peak_measured):
     def run(group, tr_norm=0, cauchy_norm=0):
         a = Admm(net, opts=options(group=group, tr_norm=tr_norm, cauchy_norm=cauchy_norm))
         grp = a.branch_group
+        lpi = a.launches_per_iteration
         a.step(16)  # graph capture and the first iterations, untimed
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -311,13 +313,13 @@ def bench_admm(args, dev, peak_measured):
         dt = time.perf_counter() - t0
         counts = a.branch_status_counts().tolist()
         a.close()
-        return pr, du, dt, counts, grp
+        return pr, du, dt, counts, grp, lpi
 
     # the library's mapping (chosen by the branch count), then the other one
-    pr, du, dt, counts, grp = run(0)
-    _, _, dt_o, _, grp_o = run(4 if grp == 1 else 1)
-    _, _, dt_e, _, _ = run(0, tr_norm=1)  # the other reading of the PCG's norm
-    _, _, dt_h, _, _ = run(0, cauchy_norm=1)  # the Cauchy test in the Hessian's norm
+    pr, du, dt, counts, grp, lpi = run(0)
+    _, _, dt_o, _, grp_o, _ = run(4 if grp == 1 else 1)
+    _, _, dt_e, _, _, _ = run(0, tr_norm=1)  # the other reading of the PCG's norm
+    _, _, dt_h, _, _, _ = run(0, cauchy_norm=1)  # the Cauchy test in the Hessian's norm
     cores = os.cpu_count() or 1
     o = oracle.Admm(net)
     o.run(16, nthreads=cores)  # the iterations the GPU run did untimed
@@ -330,7 +332,7 @@ def bench_admm(args, dev, peak_measured):
     return {"value": args.admm_iters / dt, "unit": "ADMM iters/s",
             "workload": "10,000 buses, 13,000 branches, 3,000 generators, rho=400",
             "iterations": args.admm_iters, "ms_per_iter": sec_it * 1e3,
-            "gpu_launches": 2 * args.admm_iters, "final_primal": pr, "final_dual": du,
+            "gpu_launches": lpi * args.admm_iters, "final_primal": pr, "final_dual": du,
             "oracle_final": [float(hp[-1]), float(hd[-1])],
             "branch_status_last_iter": counts, "branch_lanes_per_problem": grp,
             "other_mapping": {"branch_lanes_per_problem": grp_o,
@@ -544,7 +546,9 @@ def bench_multiperiod(args, dev, peak_measured):
     """Multi-period ADMM: 24 periods of a 2,000-bus network (2,600 branches, 600
     generators), loads on a synthetic daily profile, generators coupled by ramp limits of
     5 % of p_max (penalty 1e4): iterations/s over args.mp_iters iterations (five launches
-    each); the oracle runs the same iterations on the host cores."""
+    each: branches, the generator chains' gather, solve and scatter on a side stream
+    beside them, buses; six with options.split_outer, which adds the branches' four-lane
+    continuation); the oracle runs the same iterations on the host cores."""
     import torch
     import oracle
     from paper_2106_14995_gb300 import synth
@@ -556,7 +560,8 @@ def bench_multiperiod(args, dev, peak_measured):
     ramp = 0.05 * net["gen_pmax"]
     alt = {}
     for key, opt in (("euclidean_reading", options(tr_norm=1)),
-                     ("hessian_cauchy", options(cauchy_norm=1))):
+                     ("hessian_cauchy", options(cauchy_norm=1)),
+                     ("split_after_3", options(split_outer=3))):
         ge = AdmmMultiPeriod(net, scale, ramp=ramp, rho_ramp=1e4, opts=opt)
         ge.step(4)
         torch.cuda.synchronize(dev)
@@ -565,7 +570,8 @@ def bench_multiperiod(args, dev, peak_measured):
         alt[key] = time.perf_counter() - t0
         ge.close()
     g = AdmmMultiPeriod(net, scale, ramp=ramp, rho_ramp=1e4)
-    g.step(4)  # graph capture and the first iterations, untimed
+    lpi = g.launches_per_iteration
+    g.step(4)  # the first iterations, untimed
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     pr, du = g.step(args.mp_iters)
@@ -587,7 +593,7 @@ def bench_multiperiod(args, dev, peak_measured):
             "workload": "24 periods x (2,000 buses, 2,600 branches, 600 generators), "
                         "ramp 5 % of p_max, rho=400, rho_ramp=1e4",
             "iterations": args.mp_iters, "ms_per_iter": sec_it * 1e3,
-            "gpu_launches": 5 * args.mp_iters, "final_primal": pr, "final_dual": du,
+            "gpu_launches": lpi * args.mp_iters, "final_primal": pr, "final_dual": du,
             "gen_status_last_iter": counts,
             "max_ramp_step_over_limit": float(np.max(np.abs(np.diff(p, axis=0)) -
                                                      ramp[None, :])),
@@ -595,6 +601,10 @@ def bench_multiperiod(args, dev, peak_measured):
                                   "unit": "ADMM iters/s", "note": "options.tr_norm = 1"},
             "hessian_cauchy": {"value": args.mp_iters / alt["hessian_cauchy"],
                                "unit": "ADMM iters/s", "note": "options.cauchy_norm = 1"},
+            "split_after_3": {"value": args.mp_iters / alt["split_after_3"],
+                              "unit": "ADMM iters/s",
+                              "note": "options.split_outer = 3: one-lane branch solves "
+                                      "unfinished after 3 TRON iterations end on 4 lanes"},
             "roofline": fp64_roofline(flops_it, sec_it, peak_measured,
                                       "branch + generator-chain + bus kernels",
                                       {"flops_per_iter": flops_it,
@@ -718,6 +728,7 @@ def summary(line: dict) -> dict:
         out["multiperiod"] = {"iters_per_s": r(m["value"]),
                               "euclidean": r(m["euclidean_reading"]["value"]),
                               "hessian_cauchy": r(m["hessian_cauchy"]["value"]),
+                              "split_after_3": r(m["split_after_3"]["value"]),
                               "cpu": r(m["cpu_baseline"]["value"])}
     sv = line.get("serving")
     if sv:

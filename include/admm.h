@@ -109,7 +109,9 @@ tron_err_t admm_branch_status_counts(admm_t* a, int64_t* h_counts6, void* stream
 
 int64_t admm_iterations(const admm_t* a);
 int64_t admm_history_capacity(const admm_t* a);
-/* GPU kernel launches one iteration performs (inside the replayed graph). */
+/* GPU kernel launches one iteration performs (inside the replayed graph) with four
+ * lanes per branch: 2.  A pool with one lane per branch that finishes its slow solves
+ * on four lanes (options.split_outer) performs 3: admm_pool_launches_per_iteration. */
 int32_t admm_launches_per_iteration(void);
 void admm_destroy(admm_t* a);
 
@@ -122,6 +124,10 @@ void admm_destroy(admm_t* a);
 tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_branch,
                             int32_t cap_gen, int32_t cap_instances, int32_t history_len,
                             const tron_options_t* opt, void* stream);
+
+/* GPU kernel launches of one iteration of this pool (or of an admm_t, which is one):
+ * 3 with one lane per branch and options.split_outer > 0, else 2; 0 for NULL. */
+int32_t admm_pool_launches_per_iteration(const admm_pool_t* p);
 
 /* Admit an instance: returns TRON_ENOMEM (and *id = -1) when no free ranges can hold
  * it — nothing is allocated here, the pool's slots are reused.  The new instance
@@ -177,6 +183,11 @@ tron_err_t admm_mp_create(admm_mp_t** out, const admm_network_t* net, int32_t T,
                           const tron_options_t* opt, void* stream);
 tron_err_t admm_mp_step(admm_mp_t* mp, int32_t n_iters, double* h_primal, double* h_dual,
                         void* stream);
+
+/* GPU kernel launches of one admm_mp_step iteration: the pool's branch launch (3 with
+ * the four-lane continuation of one-lane pools, else 2, counting the bus launch) plus the
+ * generator chains' gather, solve and scatter when there are generators; 0 for NULL. */
+int32_t admm_mp_launches_per_iteration(const admm_mp_t* mp);
 tron_err_t admm_mp_get_state(admm_mp_t* mp, int32_t period, admm_state_view_t* host,
                              void* stream);
 tron_err_t admm_mp_gen_status_counts(admm_mp_t* mp, int64_t* h_counts6, void* stream);

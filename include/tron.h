@@ -141,7 +141,15 @@ typedef struct tron_options {
                                     (else ||s||_2), the norm in which the PCG's bound
                                     ||L^T w|| is nearly stated, so one radius suits both
                                     steps (with tr_norm 0)                                */
-  int32_t reserved[3];    /* must be zero                                                */
+  int32_t split_outer;    /* 0      ADMM branch solves on one lane per problem (the pool's
+                                    mapping for many branches per SM sub-partition): K > 0
+                                    = the TRON iteration after which a solve that has not
+                                    finished continues on four lanes, in a second launch
+                                    over the unfinished solves only; <= 0 = never.  The
+                                    continuation resumes Algorithm 1 at the same x, radius
+                                    and Cauchy step, so it is the same iteration up to
+                                    rounding.  Ignored by tron_batch_* and four-lane pools */
+  int32_t reserved[2];    /* must be zero                                                */
 } tron_options_t;
 
 typedef struct tron_batch tron_batch_t;
@@ -292,6 +300,17 @@ const char* tron_version(void);
  * device arrays of n doubles (n >= 0; positive normal values are the pivots it is made
  * for).  Enqueued on `stream`; TRON_EINVAL for a null array with n > 0. */
 tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void* stream);
+
+/* Test hook of the solver's quotient and square root (the CG step lengths alpha and
+ * beta, trqsol's root, the radius update of Algorithm 1): op 1, d_out[i] = d_a[i] /
+ * d_b[i]; op 2, d_out[i] = sqrt(d_a[i]) (d_b unused, may be NULL) -- each computed as the
+ * solver computes it, by refinement of the hardware reciprocal (square-root) estimate
+ * with IEEE division (sqrt) outside its range; the result is within one ulp of the
+ * correctly rounded one.  d_a, d_b, d_out: caller-owned device arrays of n doubles
+ * (n >= 0).  Enqueued on `stream`; TRON_EINVAL for another op, or a null array with
+ * n > 0. */
+tron_err_t tron_test_arith(int32_t op, const double* d_a, const double* d_b, double* d_out,
+                           int64_t n, void* stream);
 
 /* Measurement hook (the paper has no counterpart): FP64 fused multiply-add throughput.
  * Launches `blocks` CTAs of `threads` threads; every thread runs 8 independent chains of

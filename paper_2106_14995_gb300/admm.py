@@ -106,6 +106,12 @@ class Admm:
         """Lanes per branch problem in the branch launch (1 or 4)."""
         return int(self._lib.admm_pool_branch_group(self._h))
 
+    @property
+    def launches_per_iteration(self) -> int:
+        """GPU kernel launches of one iteration: 2, or 3 when one-lane branch solves
+        are finished on four lanes (options.split_outer > 0)."""
+        return int(self._lib.admm_pool_launches_per_iteration(self._h))
+
     def get_state(self) -> dict:
         bufs = _state_buffers(self.sizes)
         v = _view(bufs)
@@ -213,6 +219,12 @@ class AdmmPool:
         """Lanes per branch problem in the branch launch (1 or 4)."""
         return int(self._lib.admm_pool_branch_group(self._h))
 
+    @property
+    def launches_per_iteration(self) -> int:
+        """GPU kernel launches of one iteration: 2, or 3 when one-lane branch solves
+        are finished on four lanes (options.split_outer > 0)."""
+        return int(self._lib.admm_pool_launches_per_iteration(self._h))
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             self._lib.admm_pool_destroy(self._h)
@@ -248,6 +260,13 @@ class AdmmMultiPeriod:
                                           nt.stream_handle(stream)), "admm_mp_create")
         self._h = h
         self.stream = stream
+
+    @property
+    def launches_per_iteration(self) -> int:
+        """GPU kernel launches of one iteration: the periods' branch launch (and its
+        four-lane continuation), the generator chains with their gather and scatter, and
+        the bus launch."""
+        return int(self._lib.admm_mp_launches_per_iteration(self._h))
 
     def step(self, n_iters: int, residuals: bool = True):
         pr = C.c_double()

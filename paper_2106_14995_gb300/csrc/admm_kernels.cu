@@ -8,6 +8,9 @@
 //                       started; the branch record is gathered on the fly from the
 //                       multipliers and the bus copies, the pair values at the new
 //                       point are written back)
+//   (k_admm_branch_tail: with one lane per branch, a third launch between the two that
+//                       finishes on four lanes the solves still running after a few
+//                       TRON iterations)
 //   k_admm_bus        : per bus, the closed-form equality-constrained QP over its copies
 //                       (power balance, eqs. PowerBalanceReal/Reactive), the multiplier
 //                       update of every pair it owns and the residual partial sums; the
@@ -53,6 +56,9 @@ struct PoolDev {
   double* br_tilde;
   int32_t* br_status;
   int32_t* br_iters;
+  double* br_alpc;          // Cauchy step of a solve paused after the one-lane launch
+  int32_t* split_list;      // slots of the paused solves, in no particular order
+  unsigned int* split_cnt;  // their number (reset by the bus kernel)
   // generator slots
   int32_t* gen_bus;
   int32_t* gen_inst;
@@ -97,8 +103,10 @@ struct PoolDev {
 struct AdmmArgs {
   PoolDev d;
   tron_options_t opt;
-  int32_t nbb;    // branch CTAs (warps_per_block warps of 32 / G branches each)
-  int32_t ngb;    // generator CTAs
+  int32_t nbb;       // branch CTAs (warps_per_block warps of 32 / G branches each)
+  int32_t ngb;       // generator CTAs
+  int32_t pause_at;  // one-lane branch solves stop after this many TRON iterations and
+                     // are finished by k_admm_branch_tail (INT_MAX: no split)
 };
 
 template <int G>
@@ -108,7 +116,7 @@ using BranchSolver = Solver<BranchObj<G>, 4, G>;
 // lane t owns variable t, flow t and the pair terms t and t + 4)
 template <int G>
 __device__ __forceinline__ void branch_update(const PoolDev& d, const tron_options_t& opt,
-                                              double* wsm, int k) {
+                                              double* wsm, int k, int pause_at, bool resume) {
   using S = BranchSolver<G>;
   const int inst = d.br_inst[k];
   if (inst < 0 || !d.inst_active[inst]) return;
@@ -160,7 +168,19 @@ __device__ __forceinline__ void branch_update(const PoolDev& d, const tron_optio
     double delta = d.br_delta[k];
     double f, pg;
     int it;
+    sv.pause_at = pause_at;
     const int st = sv.run(x, delta, f, pg, it, fin);
+    if (st == kTronPaused) {
+      // unfinished after pause_at iterations: the state for the four-lane continuation,
+      // and the slot on the list of k_admm_branch_tail
+#pragma unroll
+      for (int q = 0; q < 4; ++q) d.br_x[4 * (size_t)k + q] = x[q];
+      d.br_delta[k] = delta;
+      d.br_alpc[k] = sv.alpha_out;
+      d.br_iters[k] = it;
+      d.split_list[atomicAdd(d.split_cnt, 1u)] = k;
+      return;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       d.br_x[4 * (size_t)k + q] = x[q];
@@ -201,6 +221,10 @@ __device__ __forceinline__ void branch_update(const PoolDev& d, const tron_optio
     fin = !sv.gp.any(!fin);
     double x[1] = {d.br_x[4 * (size_t)k + t]};
     double delta = d.br_delta[k];
+    if (resume) {  // the continuation of a paused one-lane solve
+      sv.k_start = d.br_iters[k];
+      sv.alpha0 = d.br_alpc[k];
+    }
     double f, pg;
     int it;
     const int st = sv.run(x, delta, f, pg, it, fin);
@@ -223,7 +247,8 @@ __global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = ((int)blockIdx.x * (int)(blockDim.x >> 5) + warp) * (32 / G) + lane / G;
     if (k >= d.cap_br) return;
-    branch_update<G>(d, a.opt, smem + (size_t)warp * BranchSolver<G>::WARP_DOUBLES, k);
+    branch_update<G>(d, a.opt, smem + (size_t)warp * BranchSolver<G>::WARP_DOUBLES, k,
+                     G == 1 ? a.pause_at : 0x7FFFFFFF, false);
   } else {
     const int g = ((int)blockIdx.x - a.nbb) * (int)blockDim.x + (int)threadIdx.x;
     if (g >= d.cap_gen) return;
@@ -241,6 +266,20 @@ __global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
     d.gen_pq[2 * g] = p;
     d.gen_pq[2 * g + 1] = q;
   }
+}
+
+// The continuation of the one-lane solves that k_admm_branch_gen<1> paused: four lanes
+// per solve (each TRON iteration about half as long as on one lane), the paused slots
+// taken from the list in order by the groups of a grid of one-warp CTAs.  Only the few
+// slow solves of an iteration get here, so they no longer hold one-lane warps (and their
+// SMs) to the end of the branch launch.
+__global__ void __launch_bounds__(32) k_admm_branch_tail(const AdmmArgs a) {
+  const PoolDev& d = a.d;
+  extern __shared__ double smem[];
+  const unsigned cnt = *d.split_cnt;  // written by the previous launch
+  const unsigned ng = gridDim.x * 8u;
+  for (unsigned e = blockIdx.x * 8u + (threadIdx.x >> 2); e < cnt; e += ng)
+    branch_update<4>(d, a.opt, smem, d.split_list[e], 0x7FFFFFFF, true);
 }
 
 // the branch kernel and its shared memory per warp for branch group size G (1 or 4)
@@ -449,7 +488,10 @@ __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
       d.inst_iter[i] = it + 1;
     }
   }
-  if (threadIdx.x == 0) *d.done = 0u;
+  if (threadIdx.x == 0) {
+    *d.done = 0u;
+    *d.split_cnt = 0u;
+  }
 }
 
 // initial point of a newly admitted instance (v = 1, theta = 0, generators at box
@@ -586,6 +628,8 @@ struct admm_pool {
   int nbb, ngb, nbusb;
   int bw;   // warps per branch CTA
   int grp;  // lanes per branch problem (1 or 4)
+  int split;  // one-lane pools: TRON iterations before a solve moves to four lanes (0: never)
+  int ntb;    // CTAs of k_admm_branch_tail
   RangeAlloc ab, al, ag;
   struct Inst {
     bool live;
@@ -625,6 +669,7 @@ static AdmmArgs make_args(const admm_pool* p) {
   a.opt = p->opt;
   a.nbb = p->nbb;
   a.ngb = p->ngb;
+  a.pause_at = p->split > 0 ? p->split : 0x7FFFFFFF;
   return a;
 }
 
@@ -636,6 +681,9 @@ static tron_err_t launch_iteration(admm_pool* p, cudaStream_t st) {
   // owns its slice of the shared memory), a generator CTA updates one generator per thread
   XT_CUDA(cudaLaunchKernel(branch_kernel(p->grp), dim3(p->nbb + p->ngb),
                            dim3(p->bw * 32), args, smem, st));
+  if (p->split > 0)
+    XT_CUDA(cudaLaunchKernel((const void*)k_admm_branch_tail, dim3(p->ntb), dim3(32), args,
+                             branch_warp_bytes(4), st));
   XT_CUDA(cudaLaunchKernel((const void*)k_admm_bus, dim3(p->nbusb), dim3(kBusThreads), args, 0,
                            st));
   return TRON_OK;
@@ -665,6 +713,10 @@ extern "C" {
 
 int32_t admm_launches_per_iteration(void) { return 2; }
 
+int32_t admm_pool_launches_per_iteration(const admm_pool_t* p) {
+  return p ? (p->split > 0 ? 3 : 2) : 0;
+}
+
 tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_branch,
                             int32_t cap_gen, int32_t cap_instances, int32_t history_len,
                             const tron_options_t* opt, void* stream) {
@@ -692,16 +744,22 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
   // lanes per branch problem: options.group 1 or 4, or (0) chosen by the branch slots
   // per SM sub-partition; fixed for the pool's life, so an instance's results do not
   // depend on its co-residents
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    nsm = 0;
   if (p->opt.group == 0) {
-    int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      nsm = 0;
     p->grp = (nsm > 0 && (long long)cl <= (long long)kG4BranchesPerSmsp * 4 * nsm) ? 4 : 1;
   } else {
     p->grp = p->opt.group;
   }
   p->opt.group = p->grp;
+  // with options.split_outer = K > 0, one-lane pools finish the solves still running
+  // after K iterations on four lanes, in a grid of one-warp CTAs that holds the usual
+  // number of them with one group each (16 resident per SM); more paused solves are
+  // taken in turn
+  p->split = (p->grp == 1 && p->opt.split_outer > 0) ? p->opt.split_outer : 0;
+  p->ntb = std::max(1, std::min((cl + 7) / 8, 16 * std::max(nsm, 1)));
   p->d.cap_bus = cb;
   p->d.cap_br = cl;
   p->d.cap_gen = cg;
@@ -726,6 +784,9 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
   PA(br_tilde, 4 * (size_t)cl);
   PA(br_status, cl);
   PA(br_iters, cl);
+  PA(br_alpc, cl);
+  PA(split_list, cl);
+  PA(split_cnt, 1);
   PA(gen_bus, cg);
   PA(gen_inst, cg);
   PA(gen_c2, cg);
@@ -779,6 +840,7 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
       cudaMemsetAsync(p->d.inst_iter, 0, sizeof(int64_t) * cap_instances, st) ||
       cudaMemsetAsync(p->d.inst_param, 0, sizeof(double) * 4 * cap_instances, st) ||
       cudaMemsetAsync(p->d.done, 0, sizeof(unsigned int), st) ||
+      cudaMemsetAsync(p->d.split_cnt, 0, sizeof(unsigned int), st) ||
       cudaMemsetAsync(p->d.part, 0, sizeof(double) * 2 * p->nbusb, st))
     return fail("workspace initialisation");
   const size_t smem = (size_t)p->bw * branch_warp_bytes(p->grp);
@@ -1145,6 +1207,11 @@ struct admm_mp {
   tron_batch_t* tb;            // the generator chains: ngen problems of T periods
   double *d_rec, *d_lo, *d_hi, *d_x, *d_delta, *d_f, *d_pg;
   int32_t *d_iters, *d_status;
+  // the generator chains run on a side stream beside the branch launch (the two touch
+  // disjoint data: the flagged periods' generators are skipped by the branch kernel), and
+  // the bus kernel waits for both
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
   std::vector<void*> allocs;
 };
 
@@ -1155,6 +1222,9 @@ void admm_mp_destroy(admm_mp_t* mp) {
   if (mp->tb) tron_batch_destroy(mp->tb);
   if (mp->pool) admm_pool_destroy(mp->pool);
   for (void* a : mp->allocs) cudaFree(a);
+  if (mp->ev_fork) cudaEventDestroy(mp->ev_fork);
+  if (mp->ev_join) cudaEventDestroy(mp->ev_join);
+  if (mp->side) cudaStreamDestroy(mp->side);
   delete mp;
 }
 
@@ -1176,6 +1246,9 @@ tron_err_t admm_mp_create(admm_mp_t** out, const admm_network_t* net, int32_t T,
   admm_mp* mp = new admm_mp();
   mp->pool = nullptr;
   mp->tb = nullptr;
+  mp->side = nullptr;
+  mp->ev_fork = nullptr;
+  mp->ev_join = nullptr;
   mp->T = T;
   mp->ngen = ng;
   auto fail = [&](tron_err_t e) {
@@ -1259,8 +1332,19 @@ tron_err_t admm_mp_create(admm_mp_t** out, const admm_network_t* net, int32_t T,
     e = tron_batch_create(&mp->tb, TRON_OBJ_GEN_RAMP, ng, nullptr, T, &o, stream);
     if (e != TRON_OK) return fail(e);
   }
+  if (cudaStreamCreateWithFlags(&mp->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&mp->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&mp->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    set_error("admm_mp_create: stream or event creation failed");
+    return fail(TRON_ECUDA);
+  }
   *out = mp;
   return TRON_OK;
+}
+
+int32_t admm_mp_launches_per_iteration(const admm_mp_t* mp) {
+  if (!mp) return 0;
+  return admm_pool_launches_per_iteration(mp->pool) + (mp->ngen > 0 ? 3 : 0);
 }
 
 tron_err_t admm_mp_step(admm_mp_t* mp, int32_t n_iters, double* h_primal, double* h_dual,
@@ -1274,23 +1358,30 @@ tron_err_t admm_mp_step(admm_mp_t* mp, int32_t n_iters, double* h_primal, double
   const size_t smem = (size_t)p->bw * branch_warp_bytes(p->grp);
   const int nthr = mp->ngen * mp->T;
   for (int it = 0; it < n_iters; ++it) {
-    // branches (the flagged periods' generators are skipped there) ...
-    XT_CUDA(cudaLaunchKernel(branch_kernel(p->grp), dim3(p->nbb + p->ngb),
-                             dim3(p->bw * 32), args, smem, st));
-    // ... generators over all periods ...
+    // the generator chains of all periods on the side stream ...
     if (nthr > 0) {
-      k_mp_gather<<<(nthr + 127) / 128, 128, 0, st>>>(p->d, mp->d_g0, mp->T, mp->ngen,
-                                                      mp->d_rec, mp->d_x);
+      XT_CUDA(cudaEventRecord(mp->ev_fork, st));
+      XT_CUDA(cudaStreamWaitEvent(mp->side, mp->ev_fork, 0));
+      k_mp_gather<<<(nthr + 127) / 128, 128, 0, mp->side>>>(p->d, mp->d_g0, mp->T, mp->ngen,
+                                                            mp->d_rec, mp->d_x);
       XT_CUDA(cudaGetLastError());
       tron_err_t e = tron_batch_solve(mp->tb, mp->d_rec, mp->d_lo, mp->d_hi, mp->d_x,
                                       mp->d_delta, mp->d_f, mp->d_pg, mp->d_iters,
-                                      mp->d_status, stream);
+                                      mp->d_status, (void*)mp->side);
       if (e != TRON_OK) return e;
-      k_mp_scatter<<<(nthr + 127) / 128, 128, 0, st>>>(p->d, mp->d_g0, mp->T, mp->ngen,
-                                                       mp->d_x);
+      k_mp_scatter<<<(nthr + 127) / 128, 128, 0, mp->side>>>(p->d, mp->d_g0, mp->T, mp->ngen,
+                                                             mp->d_x);
       XT_CUDA(cudaGetLastError());
+      XT_CUDA(cudaEventRecord(mp->ev_join, mp->side));
     }
-    // ... then the buses, multipliers and residuals of every period
+    // ... beside the branches (the flagged periods' generators are skipped there) ...
+    XT_CUDA(cudaLaunchKernel(branch_kernel(p->grp), dim3(p->nbb + p->ngb),
+                             dim3(p->bw * 32), args, smem, st));
+    if (p->split > 0)
+      XT_CUDA(cudaLaunchKernel((const void*)k_admm_branch_tail, dim3(p->ntb), dim3(32), args,
+                               branch_warp_bytes(4), st));
+    // ... then the buses, multipliers and residuals of every period, after both
+    if (nthr > 0) XT_CUDA(cudaStreamWaitEvent(st, mp->ev_join, 0));
     XT_CUDA(cudaLaunchKernel((const void*)k_admm_bus, dim3(p->nbusb), dim3(kBusThreads), args,
                              0, st));
   }

@@ -293,4 +293,54 @@ __device__ __forceinline__ double pivot_rcp(double a) {
   return fma(y, fma(-a, y, 1.0), y);
 }
 
+// On this GPU an IEEE double division or square root is a sequence about nine FP64
+// instructions deep, and every FP64 warp instruction holds the sub-partition's FP64 unit
+// for a fixed time whatever the number of active lanes.  The two below take six or seven,
+// from the hardware approximations.  Both are faithful (error below one ulp) and, with a
+// seed accurate to 2^-20, round correctly in all but rare cases near a rounding midpoint;
+// operands outside their range take the IEEE operation.
+//
+// a / b: Markstein's scheme (P. Markstein, IBM J. Res. Develop. 34(1), 1990): the
+// reciprocal seed y0 with e = 1 - b y0 gives y = y0 (1 + e + e^2), relative error e^3;
+// the remainder r = a - b q0 of the first quotient q0 = a y0 is exact up to its own
+// rounding, and q0 + r y is the quotient.  Fast path: a and b normal, a away from the
+// bottom of the range (r stays normal), 1/b normal, the quotient's exponent within
+// 1000 of zero; zeros (signed), subnormals, infinities and NaNs take a / b.
+__device__ __forceinline__ double quotient(double a, double b) {
+  const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+  const int ea = (int)((ba >> 52) & 0x7FF), eb = (int)((bb >> 52) & 0x7FF);
+  const int dq = ea - eb;
+  if (ea >= 64 && ea <= 2046 && eb >= 2 && eb <= 2044 && dq >= -1000 && dq <= 1000) {
+    double y0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(b));
+    const double e = fma(-b, y0, 1.0);
+    const double q0 = a * y0;
+    const double e2 = fma(e, e, e);
+    const double r = fma(-b, q0, a);
+    const double y = fma(y0, e2, y0);
+    return fma(r, y, q0);
+  }
+  return a / b;
+}
+
+// sqrt(x): Goldschmidt's iteration from the reciprocal square-root seed y0 (s = x y0,
+// h = y0 / 2, r = 1/2 - s h; s += s r, h += h r), then one Newton correction of s with
+// the exact residual x - s^2 (Markstein, ibid.).  Fast path: x positive and normal with
+// exponent field in [64, 1980) (so y0 / 2 is an exponent decrement); otherwise sqrt.
+__device__ __forceinline__ double square_root(double x) {
+  const long long bx = __double_as_longlong(x);
+  if (bx >= (64LL << 52) && bx < (1980LL << 52)) {
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
+    const double s0 = x * y0;
+    const double h0 = __longlong_as_double(__double_as_longlong(y0) - (1LL << 52));
+    const double r = fma(-s0, h0, 0.5);
+    const double s1 = fma(s0, r, s0);
+    const double h1 = fma(h0, r, h0);
+    const double d = fma(-s1, s1, x);
+    return fma(d, h1, s1);
+  }
+  return sqrt(x);
+}
+
 }  // namespace xt

@@ -364,6 +364,11 @@ __global__ void k_pivot_rcp(const double* a, double* out, int64_t n) {
   if (i < n) out[i] = pivot_rcp(a[i]);
 }
 
+__global__ void k_arith(int op, const double* a, const double* b, double* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = op == 1 ? quotient(a[i], b[i]) : square_root(a[i]);
+}
+
 // FP64 FMA throughput: 8 independent dependent chains per thread (enough to cover the
 // FMA latency with a few warps per SM sub-partition); the factor and increment keep the
 // values bounded, and the result is written so nothing is eliminated
@@ -427,6 +432,20 @@ tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void
   const int64_t blocks = (n + 255) / 256;
   XT_REQUIRE(blocks < (1ll << 31), TRON_EINVAL, "tron_test_pivot_rcp: n too large");
   xt::k_pivot_rcp<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d_a, d_out, n);
+  XT_CUDA(cudaGetLastError());
+  return TRON_OK;
+}
+
+tron_err_t tron_test_arith(int32_t op, const double* d_a, const double* d_b, double* d_out,
+                           int64_t n, void* stream) {
+  clear_error();
+  XT_REQUIRE(op == 1 || op == 2, TRON_EINVAL, "tron_test_arith: op must be 1 or 2");
+  XT_REQUIRE(n >= 0, TRON_EINVAL, "tron_test_arith: n < 0");
+  if (n == 0) return TRON_OK;
+  XT_REQUIRE(d_a && d_out && (op == 2 || d_b), TRON_EINVAL, "tron_test_arith: null device array");
+  const int64_t blocks = (n + 255) / 256;
+  XT_REQUIRE(blocks < (1ll << 31), TRON_EINVAL, "tron_test_arith: n too large");
+  xt::k_arith<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(op, d_a, d_b, d_out, n);
   XT_CUDA(cudaGetLastError());
   return TRON_OK;
 }

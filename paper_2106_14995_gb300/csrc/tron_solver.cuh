@@ -34,6 +34,9 @@ namespace xt {
 
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+// status of a run stopped by Solver::pause_at (never reported: the run is resumed)
+constexpr int kTronPaused = 64;
+
 // PK selects the storage of the factor: false = full N x (N+1) array with L^T mirrored
 // into the upper triangle (Sec. 4.4); true = packed lower triangle, row c at c(c+1)/2,
 // half the shared memory.  Both keep every warp access conflict free: in the packed
@@ -71,6 +74,14 @@ struct Solver {
   SV<G, int> Fi;
   double l[R], u[R];
   long long kl[R], ku[R];  // integer keys of the bounds
+  // a run split in two launches: the first stops after pause_at iterations with
+  // kTronPaused (x, delta, the iteration count and the Cauchy step alpha_c are then the
+  // whole state of Algorithm 1 between iterations; f, g and H follow from x), and the
+  // second resumes from them with k_start and alpha0
+  int pause_at = 0x7FFFFFFF;
+  int k_start = 0;
+  double alpha0 = 1.0;
+  double alpha_out = 1.0;
 
   __device__ __forceinline__ Solver(const tron_options_t& opt, double* warp_smem) : o(opt) {
     double* base = (G == 1) ? warp_smem + gp.lane
@@ -526,7 +537,7 @@ struct Solver {
       gp.sync();
       // options.cholesky: 1 left-looking, 2 right-looking, 0 the size class's default
       const bool right = o.cholesky != 1;
-      if (right ? chol_right(m) : chol_left(m)) return alpha == 0.0 ? 1 : 2;
+      if (right ? chol_right(m) : chol_left(m)) return nonzero_bits(alpha) ? 2 : 1;
       if (!have_beta) shift_stats();
       alpha = fmax(2.0 * alpha, beta);
     }
@@ -578,9 +589,9 @@ struct Solver {
                                                    double delta) {
     const double dsq = delta * delta;
     double rad = xp * xp + pp * (dsq - xx);
-    if (rad < 0.0) rad = 0.0;
-    rad = sqrt(rad);
-    return (xp >= 0.0) ? (dsq - xx) / (xp + rad) : (rad - xp) / pp;
+    if (okey(rad) < 0) rad = 0.0;
+    rad = square_root(rad);
+    return (okey(xp) >= 0) ? quotient(dsq - xx, xp + rad) : quotient(rad - xp, pp);
   }
   // trqsol (Figure 2): sigma >= 0 with ||x + sigma p||_2 = delta
   __device__ __forceinline__ double trqsol(const double (&x)[R], const double (&p)[R],
@@ -634,7 +645,7 @@ struct Solver {
     if (exact) {
       const double zz = pre ? dotv(res, z) : dotv(z, z);
       const bool bnd = le(dsq, zz);
-      const double sg = bnd ? delta / sqrt(zz) : 1.0;
+      const double sg = bnd ? quotient(delta, square_root(zz)) : 1.0;
 #pragma unroll
       for (int r = 0; r < R; ++r) w[r] = sg * z[r];
       wscale = sg;  // A w = -sg rF
@@ -651,7 +662,7 @@ struct Solver {
     double ww = 0.0, wp = 0.0, pp = rz;
     int info = 1;
     for (int it = 0; it < m; ++it) {
-      if (rz <= tol2) {
+      if (le(rz, tol2)) {
         info = 0;
         break;
       }
@@ -669,13 +680,14 @@ struct Solver {
       }
       hv_free(m, p, q);
       const double kappa = dotv(p, q);
-      const double alpha = rz / kappa;
+      const double alpha = quotient(rz, kappa);
       // negative curvature, or the step leaves the region: to the boundary along p
-      if (kappa <= 0.0 || le(dsq, fma(alpha, fma(alpha, pp, 2.0 * wp), ww))) {
+      const bool negc = !(okey(kappa) > 0);
+      if (negc || le(dsq, fma(alpha, fma(alpha, pp, 2.0 * wp), ww))) {
         const double sg = trqsol3(wp, pp, ww, delta);
 #pragma unroll
         for (int r = 0; r < R; ++r) w[r] = fma(sg, p[r], w[r]);
-        info = (kappa <= 0.0) ? 3 : 2;
+        info = negc ? 3 : 2;
         break;
       }
       ww = fma(alpha, fma(alpha, pp, 2.0 * wp), ww);
@@ -687,7 +699,7 @@ struct Solver {
       }
       precond(m, z);
       const double rzn = dotv(res, z);
-      const double beta = rzn / rz;
+      const double beta = quotient(rzn, rz);
       rz = rzn;
       wp = beta * fma(alpha, pp, wp);
       pp = fma(beta * beta, pp, rz);
@@ -708,7 +720,7 @@ struct Solver {
   // x - alpha g: decided on the trial's own integer keys, without the breakpoints'
   // divisions.
   __device__ __forceinline__ bool cauchy_try(double alpha, const double (&x)[R],
-                                             const double (&g)[R], double delta,
+                                             const double (&g)[R], double bound2,
                                              double (&s)[R], double (&Hs)[R], bool (&cl)[R],
                                              double kap, bool& inside, double& ssq) {
     double sn[R];
@@ -746,8 +758,7 @@ struct Solver {
     const double len2 = (o.cauchy_norm == 1 && okey(sHs) > 0) ? sHs : ss;
     ssq = len2;
     const double q = gts + 0.5 * sHs;
-    const double bound = o.mu1 * delta;
-    return le(q, o.mu0 * gts) && le(len2, bound * bound);
+    return le(q, o.mu0 * gts) && le(len2, bound2);
   }
 
   __device__ __forceinline__ bool all_finite(const double (&v)[R]) const {
@@ -798,7 +809,7 @@ struct Solver {
   // ------------------------------------------------------------------- Algorithm 1
   __device__ int run(double (&x)[R], double& delta, double& f, double& pg, int& k,
                      bool params_finite) {
-    k = 0;
+    k = k_start;
     {
       bool bad = false;
 #pragma unroll
@@ -827,12 +838,18 @@ struct Solver {
       delta = sqrt(dotv(s, s));
       if (delta == 0.0) delta = 1.0;
     }
-    double alpha_c = 1.0;
+    double alpha_c = alpha0;
     int status = TRON_MAX_ITER;
     // ||x||^2 <= xb2 for every x in the box (infinite when a bound is)
     double xb2 = 0.0;
 #pragma unroll
-    for (int r = 0; r < R; ++r) xb2 = fma(fmax(fabs(l[r]), fabs(u[r])), fmax(fabs(l[r]), fabs(u[r])), xb2);
+    for (int r = 0; r < R; ++r) {
+      // max(|l_i|, |u_i|) on the magnitude bits (the bounds are not NaN past the test above)
+      const long long ml = __double_as_longlong(l[r]) & 0x7FFFFFFFFFFFFFFFLL;
+      const long long mu = __double_as_longlong(u[r]) & 0x7FFFFFFFFFFFFFFFLL;
+      const double mb = __longlong_as_double(ml > mu ? ml : mu);
+      xb2 = fma(mb, mb, xb2);
+    }
     xb2 = gp.sum(xb2);
 
     for (;;) {
@@ -846,15 +863,21 @@ struct Solver {
         status = TRON_MAX_ITER;
         break;
       }
+      if (k >= pause_at) {
+        status = kTronPaused;
+        break;
+      }
       ++k;
 
       // ---- Cauchy point
       double s[R], Hs[R];
       bool cl[R];
       double alpha = alpha_c;
+      const double bmu = o.mu1 * delta;
+      const double bound2 = bmu * bmu;  // (mu1 delta)^2 of the trials' length test
       bool inside;
       double ssc;  // squared length of the accepted Cauchy step (in the test's norm)
-      if (cauchy_try(alpha, x, g, delta, s, Hs, cl, 0.0, inside, ssc)) {
+      if (cauchy_try(alpha, x, g, bound2, s, Hs, cl, 0.0, inside, ssc)) {
         double sb[R], Hsb[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -865,7 +888,7 @@ struct Solver {
         for (int t = 0; t < o.max_trials; ++t) {
           if (!inside) break;  // alpha at or beyond the largest breakpoint
           const double a2 = alpha * o.extrapf;
-          if (!cauchy_try(a2, x, g, delta, s, Hs, cl, o.extrapf, inside, ssc)) break;
+          if (!cauchy_try(a2, x, g, bound2, s, Hs, cl, o.extrapf, inside, ssc)) break;
           alpha = a2;
           ssb = ssc;
 #pragma unroll
@@ -883,7 +906,7 @@ struct Solver {
       } else {
         for (int t = 0; t < o.max_trials; ++t) {
           alpha = alpha * o.interpf;
-          if (cauchy_try(alpha, x, g, delta, s, Hs, cl, o.interpf, inside, ssc)) break;
+          if (cauchy_try(alpha, x, g, bound2, s, Hs, cl, o.interpf, inside, ssc)) break;
         }
       }
       // squared length of the step in the norms of the trust regions that bounded its
@@ -993,7 +1016,10 @@ struct Solver {
           beta = beta * o.proj_shrink;
         }
         if (!found) break;
-        nu2 = fmax(nu2, (beta * beta) * tl2);
+        {
+          const double c = (beta * beta) * tl2;
+          if (lt(nu2, c)) nu2 = c;
+        }
         bool na = false;
         double ss = 0.0;
 #pragma unroll
@@ -1018,7 +1044,7 @@ struct Solver {
         } else {
           rFn2 = gp.sum(rFn2);
         }
-        if (rFn2 <= (o.cg_rtol * o.cg_rtol) * rF0) break;
+        if (le(rFn2, (o.cg_rtol * o.cg_rtol) * rF0)) break;
       }
       if (status == TRON_CHOL_FAIL) break;
 
@@ -1070,9 +1096,11 @@ struct Solver {
       const double sl2 = (o.tr_norm == 0) ? nu2 : ss2;
       const double d99 = 0.99 * delta;
       if (below1) {
-        delta = o.sigma1 * fmin(sqrt(sl2), delta);
+        const double sl = square_root(sl2);
+        delta = o.sigma1 * (lt(sl, delta) ? sl : delta);
       } else if (above2 && le(d99 * d99, sl2)) {
-        delta = fmin(o.sigma3 * delta, o.delta_max);
+        const double dg = o.sigma3 * delta;
+        delta = lt(o.delta_max, dg) ? o.delta_max : dg;
       }
       // delta < c (1 + ||x||), decided without a square root:
       // delta - c < 0, or (delta - c)^2 < c^2 ||x||^2; ||x|| is reduced only when the
@@ -1084,6 +1112,8 @@ struct Solver {
         break;
       }
     }
+    alpha_out = alpha_c;
+    if (status == kTronPaused) return status;
     pg = pgnorm(x, g);
     return status;
   }

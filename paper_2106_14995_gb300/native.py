@@ -35,7 +35,8 @@ class TronOptions(C.Structure):
         ("group", C.c_int32), ("ared_guard", C.c_double), ("schedule", C.c_int32),
         ("warps_per_block", C.c_int32), ("layout", C.c_int32), ("cholesky", C.c_int32),
         ("ctas_per_sm", C.c_int32), ("tr_norm", C.c_int32), ("cauchy_norm", C.c_int32),
-        ("reserved", C.c_int32 * 3),
+        ("split_outer", C.c_int32),
+        ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -97,6 +98,7 @@ def load(build_if_missing: bool = True):
             "tron_last_error": (C.c_char_p, []),
             "tron_version": (C.c_char_p, []),
             "tron_test_pivot_rcp": (I32, [P, P, I64, P]),
+            "tron_test_arith": (I32, [I32, P, P, P, I64, P]),
             "tron_bench_fp64_fma": (I32, [P, I32, I32, I64, P]),
             "admm_create": (I32, [C.POINTER(P), C.POINTER(AdmmNetwork), C.POINTER(TronOptions),
                                   P]),
@@ -108,6 +110,8 @@ def load(build_if_missing: bool = True):
             "admm_iterations": (I64, [P]),
             "admm_history_capacity": (I64, [P]),
             "admm_launches_per_iteration": (I32, []),
+            "admm_pool_launches_per_iteration": (I32, [P]),
+            "admm_mp_launches_per_iteration": (I32, [P]),
             "admm_destroy": (None, [P]),
             "admm_pool_create": (I32, [C.POINTER(P), I32, I32, I32, I32, I32,
                                        C.POINTER(TronOptions), P]),

@@ -48,6 +48,7 @@ def test_options_defaults_match_oracle_readings():
               "cauchy_norm"):
         assert getattr(o, f) == getattr(r, f), f
     assert o.group == 0 and o.schedule == native.TRON_SCHED_PLAIN
+    assert o.split_outer == 0 and list(o.reserved) == [0, 0]
 
 
 def test_status_numbering_matches_oracle():

@@ -72,6 +72,39 @@ def test_admm_with_the_hessian_norm_cauchy_option_matches_oracle(group):
     np.testing.assert_allclose(hd_g, hd_o, rtol=1e-6, atol=0)
 
 
+@pytest.mark.parametrize("split", [1, -1])
+def test_one_lane_split_continuation_matches_oracle(split):
+    # one lane per branch problem; split 1: every solve still running after one TRON
+    # iteration is finished on four lanes by the third launch (so nearly every solve
+    # resumes from x, delta, its iteration count and Cauchy step), -1: never split
+    net = small_net(120, 11)
+    K = 400
+    g = Admm(net, opts=options(group=1, split_outer=split))
+    assert g.branch_group == 1
+    assert g.launches_per_iteration == (3 if split > 0 else 2)
+    g.step(K)
+    hp_g, hd_g = g.history(0, K)
+    s = g.get_state()
+    counts = g.branch_status_counts()
+    g.close()
+    # every solve ended with a reported status (none left paused)
+    assert counts.sum() == len(net["br_from"])
+    o = oracle.Admm(net)
+    hp_o, hd_o = o.run(K, nthreads=8)
+    np.testing.assert_allclose(hp_g, hp_o, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(hd_g, hd_o, rtol=1e-6, atol=0)
+    for k in ("br_x", "br_val", "br_tilde", "bus_w", "bus_th", "gen_pq"):
+        np.testing.assert_allclose(s[k], o.arrays[k], rtol=1e-6, atol=1e-8, err_msg=k)
+
+
+def test_launches_per_iteration_follow_the_branch_mapping():
+    net = small_net(60, 3)
+    for grp, split, want in ((4, 0, 2), (4, 2, 2), (1, 0, 2), (1, 2, 3), (1, -1, 2)):
+        a = Admm(net, opts=options(group=grp, split_outer=split))
+        assert a.launches_per_iteration == want, (grp, split)
+        a.close()
+
+
 def test_admm_light_load_rho10_converges_where_the_oracle_does():
     # an instance of the serving benchmark's convergent request set (515 buses, a tenth
     # of the stated load, rho 10): the GPU trajectory follows the oracle's through

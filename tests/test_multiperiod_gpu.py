@@ -83,6 +83,26 @@ def test_multiperiod_admm_matches_oracle():
     g.close()
 
 
+def test_multiperiod_one_lane_split_matches_oracle():
+    # one lane per branch with every solve still running after one TRON iteration
+    # finished on four lanes, and the generator chains on the side stream beside them
+    net = _small_net(40, 50)
+    scale = synth.load_profile(4)
+    kw = dict(ramp=0.02, rho_ramp=1e4)
+    o = oracle.MultiPeriodAdmm(net, scale, **kw)
+    hp, hd = o.run(40, nthreads=8)
+    g = AdmmMultiPeriod(net, scale, opts=options(group=1, split_outer=1), **kw)
+    assert g.launches_per_iteration == 6
+    res = np.array([g.step(1) for _ in range(40)])
+    np.testing.assert_allclose(res[:, 0], hp, rtol=1e-6)
+    np.testing.assert_allclose(res[:, 1], hd, rtol=1e-6)
+    for t in range(4):
+        s = g.get_state(t)
+        for k in ("gen_pq", "bus_w", "bus_th", "br_x"):
+            np.testing.assert_allclose(s[k], o.state(t)[k], rtol=1e-6, atol=1e-8, err_msg=k)
+    g.close()
+
+
 def test_multiperiod_without_binding_ramps_equals_single_period_runs():
     net = _small_net(50, 51)
     scale = [0.9, 1.0, 1.1]

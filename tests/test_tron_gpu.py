@@ -519,3 +519,69 @@ def test_pivot_reciprocal_against_ieee_division():
     # from 2^1022 up the hook divides: exact
     big = a >= 2.0 ** 1022
     np.testing.assert_array_equal(got[big], ref[big])
+
+
+def _arith(op, a, b=None):
+    lib = native.load()
+    d_a = _t(a)
+    d_b = _t(b) if b is not None else None
+    d_out = torch.empty_like(d_a)
+    assert lib.tron_test_arith(op, d_a.data_ptr(), d_b.data_ptr() if d_b is not None else None,
+                               d_out.data_ptr(), a.size,
+                               torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    return d_out.cpu().numpy()
+
+
+def _within_one_ulp(got, ref):
+    # got is one of the two doubles around the exact value when it is within one ulp of
+    # the correctly rounded ref (the spacing at |ref|, the larger one at a power of two)
+    with np.errstate(over="ignore"):
+        return np.abs(got - ref) <= np.spacing(np.abs(ref))
+
+
+def test_solver_quotient_against_ieee_division():
+    # the CG step lengths, trqsol's root and the radius update divide with the refined
+    # hardware reciprocal: faithful everywhere, correctly rounded but for rare midpoint
+    # cases, and exactly IEEE (signed zeros, infinities, NaN, subnormals) outside its range
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    a = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-1000, 1000, n)) * rng.choice([-1.0, 1.0], n)
+    b = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-1000, 1000, n)) * rng.choice([-1.0, 1.0], n)
+    sp = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, -5e-324, np.finfo(float).tiny,
+                   np.finfo(float).max, 1.0, -1.0, 3.0, 2.0 ** 1022, 2.0 ** -1021, 1e-300, 1e300])
+    sa, sb = np.meshgrid(sp, sp)
+    a = np.concatenate([a, sa.ravel(), np.ldexp(1.0, np.arange(-1000, 1000)), rng.normal(size=4096)])
+    b = np.concatenate([b, sb.ravel(), np.full(2000, 3.0), rng.normal(size=4096)])
+    with np.errstate(all="ignore"):
+        ref = a / b
+    got = _arith(1, a, b)
+    fin = np.isfinite(ref) & (ref != 0.0)
+    assert np.all(_within_one_ulp(got[fin], ref[fin])), a[fin][~_within_one_ulp(got[fin], ref[fin])][:4]
+    assert np.mean(got[fin] != ref[fin]) <= 1e-3
+    # NaN where IEEE gives NaN; zeros and infinities with their signs
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    rest = ~fin & ~np.isnan(ref)
+    np.testing.assert_array_equal(got[rest].view(np.int64), ref[rest].view(np.int64))
+
+
+def test_solver_square_root_against_ieee_sqrt():
+    rng = np.random.default_rng(12)
+    n = 1 << 20
+    x = np.ldexp(rng.uniform(1.0, 4.0, n), 2 * rng.integers(-511, 511, n))
+    sp = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, -1.0, 5e-324, np.finfo(float).tiny,
+                   np.finfo(float).max, 1.0, 2.0, 4.0, 0.25, 1e-300, 1e300])
+    sq = rng.uniform(0.5, 2.0, 4096)
+    x = np.concatenate([x, sp, np.ldexp(1.0, np.arange(-1074, 1024)), sq * sq])
+    with np.errstate(all="ignore"):
+        ref = np.sqrt(x)
+    got = _arith(2, x)
+    fin = np.isfinite(ref) & (ref > 0.0)
+    assert np.all(_within_one_ulp(got[fin], ref[fin])), x[fin][~_within_one_ulp(got[fin], ref[fin])][:4]
+    assert np.mean(got[fin] != ref[fin]) <= 1e-3
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    rest = ~fin & ~np.isnan(ref)
+    np.testing.assert_array_equal(got[rest].view(np.int64), ref[rest].view(np.int64))
+    # exact squares: powers of two have exact roots, which a faithful result must hit
+    p2 = np.ldexp(1.0, 2 * np.arange(-500, 500))
+    np.testing.assert_array_equal(_arith(2, p2), np.ldexp(1.0, np.arange(-500, 500)))
