@@ -50,10 +50,10 @@ def hbm_peak_gbs():
 # From one ncu capture of the timed kernel (profiles/tron_dense32_n10000.md, 2,000
 # problems, scaled per problem to the launch), valid only for the kernel sources it was
 # taken on: DRAM bytes (19.08 MB per 2,000 problems) and the FP64 flops the kernel
-# executes (thread-level DFMA x 2 + DADD + DMUL: 301.9 Mflop per 2,000 problems).
-TRAFFIC_BYTES_PER_PROBLEM = 19.080448e6 / 2000
-EXEC_FLOPS_PER_PROBLEM = (2 * 128644296 + 25309882 + 19319289) / 2000
-TRAFFIC_SOURCES_SHA1 = "5688f08d527231c425041422c615fe202dbffa6f"
+# executes (thread-level DFMA x 2 + DADD + DMUL: 301.2 Mflop per 2,000 problems).
+TRAFFIC_BYTES_PER_PROBLEM = 19.082496e6 / 2000
+EXEC_FLOPS_PER_PROBLEM = (2 * 128374664 + 25437882 + 19049401) / 2000
+TRAFFIC_SOURCES_SHA1 = "1f9c8990b2b6adcb826e89d16971581dc1ae6330"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
