@@ -485,8 +485,9 @@ def bench_branch256(args, dev, peak_measured):
 def bench_uneven(args, dev, peak_measured):
     """100,000 dense problems, n in {4,...,128} with probabilities (0.4, ..., 0.02):
     plain schedule (one launch per size class, in turn), persistent schedule (all
-    classes concurrently, device work counters) and persistent after autotuning; the
-    roofline's work is the oracle's flop count over the whole batch."""
+    classes concurrently, device work counters) and persistent after autotuning, and the
+    last with the two other trust-region readings (options.tr_norm = 1, cauchy_norm = 1);
+    the roofline's work is the oracle's flop count over the whole batch."""
     import torch
     import oracle
     from paper_2106_14995_gb300 import native, synth
@@ -500,10 +501,13 @@ def bench_uneven(args, dev, peak_measured):
 
     P, L, U, X0, D0 = t(d["params"]), t(d["l"]), t(d["u"]), t(d["x0"]), t(d["delta0"])
     res = {}
-    for name, sched, tune in (("plain", native.TRON_SCHED_PLAIN, False),
-                              ("persistent", native.TRON_SCHED_PERSISTENT, False),
-                              ("persistent_autotuned", native.TRON_SCHED_PERSISTENT, True)):
-        tb = TronBatch(2, B, n_list=nv, opts=options(schedule=sched))
+    for name, sched, tune, extra in (
+            ("plain", native.TRON_SCHED_PLAIN, False, {}),
+            ("persistent", native.TRON_SCHED_PERSISTENT, False, {}),
+            ("persistent_autotuned", native.TRON_SCHED_PERSISTENT, True, {}),
+            ("euclidean_reading", native.TRON_SCHED_PERSISTENT, True, {"tr_norm": 1}),
+            ("hessian_cauchy", native.TRON_SCHED_PERSISTENT, True, {"cauchy_norm": 1})):
+        tb = TronBatch(2, B, n_list=nv, opts=options(schedule=sched, **extra))
         if tune:
             tb.autotune(P, L, U, X0, D0, sample=8192)
         ts = []
@@ -522,6 +526,8 @@ def bench_uneven(args, dev, peak_measured):
         res[name] = {"value": B / (np.median(ts) * 1e-3), "unit": UNIT,
                      "ms": float(np.median(ts)), "launches": tb.last_launches,
                      "all_converged": ok}
+        if extra:
+            res[name]["note"] = ", ".join(f"options.{k} = {v}" for k, v in extra.items())
         # the kernel variant per size class (group/layout/warps per CTA) on stderr only
         print(f"uneven {name}: " + ", ".join(
             f"n={c['N']}:g{c['group']}/l{c['layout']}/w{c['warps_per_block']}"
@@ -721,6 +727,8 @@ def summary(line: dict) -> dict:
         out["uneven100k_ms"] = {"plain": r(u["plain"]["ms"]),
                                 "persistent": r(u["persistent"]["ms"]),
                                 "autotuned": r(u["persistent_autotuned"]["ms"]),
+                                "euclidean": r(u["euclidean_reading"]["ms"]),
+                                "hessian_cauchy": r(u["hessian_cauchy"]["ms"]),
                                 "frac": r(u["roofline"]["frac"], 3),
                                 "frac_measured": r(u["roofline"].get("frac_measured"), 3)}
     m = line.get("multiperiod")
