@@ -142,6 +142,15 @@ def parse():
     ap.add_argument("--admm-iters", type=int, default=1000)
     ap.add_argument("--mp-iters", type=int, default=200)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-cap-seconds", type=float, default=1.0 / 3.0,
+                    help="the pool holds the buses, branches and generators offered in this "
+                         "many seconds of arrivals (at least the largest instance)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="arrivals per second")
+    ap.add_argument("--serve-sets", default="stated,convergent",
+                    help="request sets to serve: stated, convergent")
+    ap.add_argument("--serve-serial-prefix", type=int, default=0,
+                    help="solve only the first N requests one at a time (FIFO latencies of a "
+                         "prefix are exact); 0 = all")
     ap.add_argument("--serve-max-iters", type=int, default=200)
     ap.add_argument("--serve-conv-max-iters", type=int, default=6000)
     return ap.parse_args()
@@ -621,10 +630,13 @@ def bench_multiperiod(args, dev, peak_measured):
                              "sample": f"the same {args.mp_iters} iterations"}}
 
 
-def _serve(reqs, tol, max_iters, chunk, cap_frac):
+def _serve(reqs, tol, max_iters, chunk, cap_frac, serial_prefix=0):
     """Continuous batching of `reqs` in a pool that holds about cap_frac of their total
     buses, branches and generators (at least the largest instance), so arrivals wait for
-    retirements; then the same requests one at a time (serial plain)."""
+    retirements; then the same requests one at a time (serial plain), or the first
+    serial_prefix of them (a FIFO queue's latency of a request depends only on the
+    requests before it, so the prefix's figures are exact; the served ones are then
+    reported over the whole stream and over the same prefix)."""
     from paper_2106_14995_gb300.serving import AdmmServer, serial_plain, summarize
     tot = [sum(len(r["net"][k]) if k != "nbus" else r["net"][k] for r in reqs)
            for k in ("nbus", "br_from", "gen_bus")]
@@ -640,17 +652,27 @@ def _serve(reqs, tol, max_iters, chunk, cap_frac):
     served["waited_for_admission"] = waited
     served["pool_capacity_buses"] = cap[0]
     served["offered_buses"] = tot[0]
-    serial = summarize(serial_plain(reqs, chunk=chunk, tol=tol, max_iters=max_iters))
-    return {"served": served, "serial_plain": serial,
-            "speedup_p50": serial["p50_s"] / served["p50_s"],
-            "speedup_p99": serial["p99_s"] / served["p99_s"],
-            "speedup_agg_iters": served["agg_iters_per_s"] / serial["agg_iters_per_s"]}
+    order = sorted(reqs, key=lambda q: q["t"])
+    sreqs = order[:serial_prefix] if 0 < serial_prefix < len(order) else order
+    serial = summarize(serial_plain(sreqs, chunk=chunk, tol=tol, max_iters=max_iters))
+    out = {"served": served, "serial_plain": serial}
+    ref = served
+    if len(sreqs) < len(order):
+        ids = {q["id"] for q in sreqs}
+        ref = summarize([r for r in recs if r["id"] in ids])
+        out["served_on_serial_prefix"] = ref
+        out["serial_prefix"] = len(sreqs)
+    out.update({"speedup_p50": serial["p50_s"] / ref["p50_s"],
+                "speedup_p99": serial["p99_s"] / ref["p99_s"],
+                "speedup_agg_iters": served["agg_iters_per_s"] / serial["agg_iters_per_s"]})
+    return out
 
 
 def bench_serving(args, dev):
     """Poisson arrivals (200/s over args.serve_seconds) of independent ADMM instances,
-    served with continuous batching in a pool that holds about a third of the offered
-    instances at once, against the same requests solved one at a time.
+    served with continuous batching in a pool that holds the instances offered in
+    args.serve_cap_seconds of arrivals (a third of a second by default), against the same
+    requests solved one at a time (or the first args.serve_serial_prefix of them).
 
     * stated: bus counts log-uniform in [500, 20000] (branches 1.3x, generators 0.3x),
       load scaling U[0.8, 1.2], rho = 400, stop at both residuals <= 1e-4 or
@@ -661,22 +683,29 @@ def bench_serving(args, dev):
       solution."""
     from paper_2106_14995_gb300 import synth
     out = {"unit": "s (time to solution)"}
-    specs = synth.serving_stream(duration_s=args.serve_seconds, rate_hz=200.0)
-    reqs = [dict(id=k, t=s["t"], net=synth.instance_network(s)) for k, s in enumerate(specs)]
-    r = _serve(reqs, 1e-4, args.serve_max_iters, 10, 1.0 / 3.0)
-    r["workload"] = (f"{len(reqs)} instances over {args.serve_seconds} s at 200/s, buses "
-                     f"log-U[500, 20000], load x U[0.8, 1.2], rho 400, stop at residuals "
-                     f"<= 1e-4 or {args.serve_max_iters} iterations")
-    out["stated"] = r
-    specs = synth.serving_stream(duration_s=args.serve_seconds, rate_hz=200.0, seed_index=5,
-                                 bus_lo=500, bus_hi=2000, load_lo=0.08, load_hi=0.12)
-    reqs = [dict(id=k, t=s["t"], net=synth.instance_network(s), rho=10.0)
-            for k, s in enumerate(specs)]
-    r = _serve(reqs, 1e-4, args.serve_conv_max_iters, 20, 1.0 / 3.0)
-    r["workload"] = (f"{len(reqs)} instances over {args.serve_seconds} s at 200/s, buses "
-                     f"log-U[500, 2000], load x U[0.08, 0.12], rho 10, stop at residuals "
-                     f"<= 1e-4 (cap {args.serve_conv_max_iters})")
-    out["convergent"] = r
+    sets = set(args.serve_sets.split(","))
+    rate, secs = args.serve_rate, args.serve_seconds
+    cap_frac = min(1.0, args.serve_cap_seconds / secs)
+    if "stated" in sets:
+        specs = synth.serving_stream(duration_s=secs, rate_hz=rate)
+        reqs = [dict(id=k, t=s["t"], net=synth.instance_network(s)) for k, s in enumerate(specs)]
+        r = _serve(reqs, 1e-4, args.serve_max_iters, 10, cap_frac, args.serve_serial_prefix)
+        r["workload"] = (f"{len(reqs)} instances over {secs} s at {rate:g}/s, buses "
+                         f"log-U[500, 20000], load x U[0.8, 1.2], rho 400, stop at residuals "
+                         f"<= 1e-4 or {args.serve_max_iters} iterations; pool for "
+                         f"{args.serve_cap_seconds:.3g} s of arrivals")
+        out["stated"] = r
+    if "convergent" in sets:
+        specs = synth.serving_stream(duration_s=secs, rate_hz=rate, seed_index=5,
+                                     bus_lo=500, bus_hi=2000, load_lo=0.08, load_hi=0.12)
+        reqs = [dict(id=k, t=s["t"], net=synth.instance_network(s), rho=10.0)
+                for k, s in enumerate(specs)]
+        r = _serve(reqs, 1e-4, args.serve_conv_max_iters, 20, cap_frac, args.serve_serial_prefix)
+        r["workload"] = (f"{len(reqs)} instances over {secs} s at {rate:g}/s, buses "
+                         f"log-U[500, 2000], load x U[0.08, 0.12], rho 10, stop at residuals "
+                         f"<= 1e-4 (cap {args.serve_conv_max_iters}); pool for "
+                         f"{args.serve_cap_seconds:.3g} s of arrivals")
+        out["convergent"] = r
     return out
 
 
@@ -741,6 +770,8 @@ def summary(line: dict) -> dict:
     sv = line.get("serving")
     if sv:
         for k in ("stated", "convergent"):
+            if k not in sv:
+                continue
             x = sv[k]
             out["serving_" + k] = {
                 "n": x["served"]["instances"], "converged": x["served"]["converged"],
