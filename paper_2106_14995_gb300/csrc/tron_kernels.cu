@@ -70,7 +70,7 @@ struct KArgs {
   int64_t count;
   int64_t pstride;
   int32_t n_uniform;
-  int32_t pad;
+  int32_t ppw;  // problems per warp for groups of a warp or less (0: as many as it holds)
   unsigned long long* counter;  // persistent schedule work counter
   tron_options_t opt;
 };
@@ -131,8 +131,11 @@ __global__ void __launch_bounds__(256) k_tron_plain(const KArgs a) {
   } else {
     const int warp = threadIdx.x >> 5;
     double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
+    const int ppw = a.ppw > 0 ? a.ppw : S::PROBS_PER_WARP;
+    const int grp = (threadIdx.x & 31) / G;
+    if (grp >= ppw) return;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    const int64_t idx = gw * S::PROBS_PER_WARP + (threadIdx.x & 31) / G;
+    const int64_t idx = gw * ppw + grp;
     if (idx >= a.count) return;
     solve_problem<Obj, N, G, PK>(a, idx, wsm);
   }
@@ -157,13 +160,14 @@ __global__ void __launch_bounds__(256) k_tron_persistent(const KArgs a) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     double* wsm = smem + (size_t)warp * S::WARP_DOUBLES;
+    const int ppw = a.ppw > 0 ? a.ppw : S::PROBS_PER_WARP;
     for (;;) {
       unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)S::PROBS_PER_WARP);
+      if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)ppw);
       base = __shfl_sync(0xffffffffu, base, 0);
       if ((int64_t)base >= a.count) break;
       const int64_t idx = (int64_t)base + lane / G;
-      if (idx < a.count) solve_problem<Obj, N, G, PK>(a, idx, wsm);
+      if (lane / G < ppw && idx < a.count) solve_problem<Obj, N, G, PK>(a, idx, wsm);
       __syncwarp();
     }
   }
@@ -702,6 +706,19 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
     a.counter = b->d_counter + 8 * cs + bi;
     a.opt = b->opt;
     if (bk.tuned && b->opt.group == 0 && b->opt.cholesky == 0) a.opt.cholesky = bk.tuned_chol;
+    // a class too small to give every SM sub-partition a warp holds fewer problems per
+    // warp (as few as one): each FP64 warp instruction costs the same whatever its active
+    // lanes, so the warps stay one per sub-partition while the problems sharing a warp,
+    // whose divergent paths that warp runs one after another, become fewer
+    int64_t per_cta = geo.per_cta;
+    if (ke->G <= 32 && ke->probs_per_warp > 1) {
+      const int64_t smsp = 4 * (int64_t)b->sms;
+      const int64_t want = (bk.count + smsp - 1) / smsp;
+      if (want < ke->probs_per_warp) {
+        a.ppw = (int32_t)std::max<int64_t>(1, want);
+        per_cta = (int64_t)geo.wpb * a.ppw;
+      }
+    }
     const size_t smem = geo.smem;
     const void* fn = persistent ? ke->persistent : ke->plain;
     {
@@ -721,10 +738,10 @@ tron_err_t tron_batch_solve(tron_batch_t* b, const double* d_params, const doubl
       }
       XT_REQUIRE(occ > 0, TRON_EUNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
       if (b->opt.ctas_per_sm > 0) occ = std::min(occ, (int)b->opt.ctas_per_sm);
-      grid = std::min<int64_t>((int64_t)occ * b->sms, (bk.count + geo.per_cta - 1) / geo.per_cta);
+      grid = std::min<int64_t>((int64_t)occ * b->sms, (bk.count + per_cta - 1) / per_cta);
       XT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), ls));
     } else {
-      grid = (bk.count + geo.per_cta - 1) / geo.per_cta;
+      grid = (bk.count + per_cta - 1) / per_cta;
     }
     void* args[] = {&a};
     XT_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(geo.threads), args, smem, ls));

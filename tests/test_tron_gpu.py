@@ -585,3 +585,21 @@ def test_solver_square_root_against_ieee_sqrt():
     # exact squares: powers of two have exact roots, which a faithful result must hit
     p2 = np.ldexp(1.0, 2 * np.arange(-500, 500))
     np.testing.assert_array_equal(_arith(2, p2), np.ldexp(1.0, np.arange(-500, 500)))
+
+
+@pytest.mark.parametrize("group", [1, 4])
+@pytest.mark.parametrize("sched", ["plain", "persistent"])
+def test_small_batch_spread_over_warps_gives_the_same_bits(group, sched):
+    # 256 problems alone: fewer problems per warp (one per warp here), so that each SM
+    # sub-partition holds one warp; the same 256 inside a batch of 8,192 are packed as
+    # many per warp as fit.  A problem's arithmetic does not depend on its place.
+    big = synth.branch_batch(8192, seed_index=41)
+    keys = ("params", "l", "u", "x0", "delta0")
+    small = {k: big[k][:256] for k in keys}
+    small["kind"] = big["kind"]
+    s = native.TRON_SCHED_PLAIN if sched == "plain" else native.TRON_SCHED_PERSISTENT
+    g_small = gpu_solve(small, n=4, group=group, schedule=s)
+    g_big = gpu_solve(big, n=4, group=group, schedule=s)
+    for k in ("x", "f", "pg", "delta", "iters", "status"):
+        np.testing.assert_array_equal(g_small[k], g_big[k][:256], err_msg=k)
+    assert np.all(g_small["status"] == native.TRON_CONVERGED)
