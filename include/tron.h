@@ -301,14 +301,15 @@ const char* tron_version(void);
  * for).  Enqueued on `stream`; TRON_EINVAL for a null array with n > 0. */
 tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void* stream);
 
-/* Test hook of the solver's quotient and square root (the CG step lengths alpha and
- * beta, trqsol's root, the radius update of Algorithm 1): op 1, d_out[i] = d_a[i] /
- * d_b[i]; op 2, d_out[i] = sqrt(d_a[i]) (d_b unused, may be NULL) -- each computed as the
- * solver computes it, by refinement of the hardware reciprocal (square-root) estimate
- * with IEEE division (sqrt) outside its range; the result is within one ulp of the
- * correctly rounded one.  d_a, d_b, d_out: caller-owned device arrays of n doubles
- * (n >= 0).  Enqueued on `stream`; TRON_EINVAL for another op, or a null array with
- * n > 0. */
+/* Test hook of the solver's own arithmetic: op 1, d_out[i] = d_a[i] / d_b[i]; op 2,
+ * sqrt(d_a[i]) -- the CG step lengths alpha and beta, trqsol's root and the radius update
+ * of Algorithm 1, by refinement of the hardware reciprocal (square-root) estimate, IEEE
+ * division (sqrt) outside its range; op 3, sin(d_a[i]), op 4, cos(d_a[i]) -- the branch
+ * objective's sine and cosine of theta_i - theta_j (eq. exp-branch), a Taylor series for
+ * |x| <= pi/4, the library's sin and cos outside.  Each result is within one ulp of the
+ * correctly rounded one.  d_b is read for op 1 only (may be NULL otherwise).  d_a, d_b,
+ * d_out: caller-owned device arrays of n doubles (n >= 0).  Enqueued on `stream`;
+ * TRON_EINVAL for another op, or a null array with n > 0. */
 tron_err_t tron_test_arith(int32_t op, const double* d_a, const double* d_b, double* d_out,
                            int64_t n, void* stream);
 

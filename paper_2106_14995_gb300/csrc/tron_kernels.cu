@@ -370,7 +370,12 @@ __global__ void k_pivot_rcp(const double* a, double* out, int64_t n) {
 
 __global__ void k_arith(int op, const double* a, const double* b, double* out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = op == 1 ? quotient(a[i], b[i]) : square_root(a[i]);
+  if (i >= n) return;
+  const double v = a[i];
+  if (op == 1) out[i] = quotient(v, b[i]);
+  else if (op == 2) out[i] = square_root(v);
+  else if (op == 3) out[i] = small_angle(v) ? sin_cos_small(v, false) : sin(v);
+  else out[i] = small_angle(v) ? sin_cos_small(v, true) : cos(v);
 }
 
 // FP64 FMA throughput: 8 independent dependent chains per thread (enough to cover the
@@ -443,10 +448,10 @@ tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void
 tron_err_t tron_test_arith(int32_t op, const double* d_a, const double* d_b, double* d_out,
                            int64_t n, void* stream) {
   clear_error();
-  XT_REQUIRE(op == 1 || op == 2, TRON_EINVAL, "tron_test_arith: op must be 1 or 2");
+  XT_REQUIRE(op >= 1 && op <= 4, TRON_EINVAL, "tron_test_arith: op must be 1, 2, 3 or 4");
   XT_REQUIRE(n >= 0, TRON_EINVAL, "tron_test_arith: n < 0");
   if (n == 0) return TRON_OK;
-  XT_REQUIRE(d_a && d_out && (op == 2 || d_b), TRON_EINVAL, "tron_test_arith: null device array");
+  XT_REQUIRE(d_a && d_out && (op != 1 || d_b), TRON_EINVAL, "tron_test_arith: null device array");
   const int64_t blocks = (n + 255) / 256;
   XT_REQUIRE(blocks < (1ll << 31), TRON_EINVAL, "tron_test_arith: n too large");
   xt::k_arith<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(op, d_a, d_b, d_out, n);

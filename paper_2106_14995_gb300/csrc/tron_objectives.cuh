@@ -264,7 +264,13 @@ struct BranchObj<1> {
   }
 
   __device__ __forceinline__ double eval_f(const Grp<1>&, const double (&y)[4]) {
-    sincos(y[2] - y[3], &sn, &cs);
+    const double dth = y[2] - y[3];
+    if (small_angle(dth)) {  // the usual case: the series (see sin_cos_small)
+      sn = sin_cos_small(dth, false);
+      cs = sin_cos_small(dth, true);
+    } else {
+      sincos(dth, &sn, &cs);
+    }
     const double vi = y[0], vj = y[1];
     const double wi = vi * vi, wj = vj * vj;
     const double vv = vi * vj;
@@ -487,7 +493,11 @@ struct BranchObj<4> {
     vj = gp.bcast(y[0], 1);
     const double thi = gp.bcast(y[0], 2), thj = gp.bcast(y[0], 3);
     const double dth = thi - thj;
-    const double sc = sin((t & 1) ? dth + 1.5707963267948966 : dth);
+    // even ranks the sine, odd ranks the cosine of the angle difference: by the series
+    // for |dth| <= pi/4 (one instruction stream for both), else as the library's sine
+    // of the argument shifted by pi/2 on odd ranks (again one stream)
+    const double sc = small_angle(dth) ? sin_cos_small(dth, (t & 1) != 0)
+                                       : sin((t & 1) ? dth + 1.5707963267948966 : dth);
     sn = gp.bcast(sc, 0);
     cs = gp.bcast(sc, 1);
     const double vv = vi * vj;

@@ -603,3 +603,24 @@ def test_small_batch_spread_over_warps_gives_the_same_bits(group, sched):
     for k in ("x", "f", "pg", "delta", "iters", "status"):
         np.testing.assert_array_equal(g_small[k], g_big[k][:256], err_msg=k)
     assert np.all(g_small["status"] == native.TRON_CONVERGED)
+
+
+def test_branch_sine_and_cosine_against_the_library():
+    # the branch objective's sin and cos of theta_i - theta_j: a Taylor series for
+    # |x| <= pi/4, the library's functions outside; within one ulp of the correctly
+    # rounded value everywhere (numpy's as the reference), signed zero kept
+    rng = np.random.default_rng(13)
+    q = np.pi / 4
+    x = np.concatenate([rng.uniform(-q, q, 1 << 20), rng.uniform(-4 * np.pi, 4 * np.pi, 1 << 16),
+                        np.ldexp(1.0, -np.arange(1, 1000)), -np.ldexp(1.0, -np.arange(1, 1000)),
+                        [0.0, -0.0, q, -q, np.nextafter(q, 1.0), np.nextafter(q, 0.0), 1e5]])
+    for op, fn in ((3, np.sin), (4, np.cos)):
+        got = _arith(op, x)
+        ref = fn(x)
+        ok = np.abs(got - ref) <= np.spacing(np.abs(ref))
+        assert np.all(ok), (op, x[~ok][:4], got[~ok][:4], ref[~ok][:4])
+        inside = np.abs(x) <= q
+        assert np.mean(got[inside] != ref[inside]) <= 0.05
+    s0 = _arith(3, np.array([0.0, -0.0]))
+    assert s0[0] == 0.0 and s0[1] == 0.0 and np.signbit(s0[1]) and not np.signbit(s0[0])
+    np.testing.assert_array_equal(_arith(4, np.array([0.0, -0.0])), [1.0, 1.0])
