@@ -624,3 +624,38 @@ def test_branch_sine_and_cosine_against_the_library():
     s0 = _arith(3, np.array([0.0, -0.0]))
     assert s0[0] == 0.0 and s0[1] == 0.0 and np.signbit(s0[1]) and not np.signbit(s0[0])
     np.testing.assert_array_equal(_arith(4, np.array([0.0, -0.0])), [1.0, 1.0])
+
+
+def test_full_size_uneven_workload_sampled():
+    # the bench's uneven workload (100,000 problems, n in {4, 6, 8, 16, 32, 64, 128}) in
+    # the bench's launch configuration: persistent schedule, autotuned variants, every
+    # size class at once; the oracle solves a stratified sample, 40 problems per class
+    d = synth.uneven_batch(100000, seed_index=3)
+    nv = d["nvec"]
+    tb = TronBatch(2, nv.size, n_list=nv, opts=options(schedule=native.TRON_SCHED_PERSISTENT))
+    P, L, U, X0, D0 = (_t(d["params"]), _t(d["l"]), _t(d["u"]), _t(d["x0"]), _t(d["delta0"]))
+    tb.autotune(P, L, U, X0, D0, sample=8192)
+    x, de = X0.clone(), D0.clone()
+    out = tb.solve(P, L, U, x, de)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    xs = x.cpu().numpy()
+    tb.close()
+    assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
+    assert np.all(g["pg"] <= 1e-6)
+    voff = np.concatenate([[0], np.cumsum(nv)])
+    poff = np.concatenate([[0], np.cumsum(nv * nv + 2 * nv)])
+    cls = np.array([min(c for c in (4, 8, 16, 32, 64, 128) if n <= c) for n in nv.tolist()])
+    rng = np.random.default_rng(2)
+    idx = np.sort(np.concatenate([
+        rng.choice(np.flatnonzero(cls == c), min(40, int((cls == c).sum())), replace=False)
+        for c in np.unique(cls)]))
+    vec = lambda a: np.concatenate([a[voff[i]:voff[i + 1]] for i in idx])
+    sub = dict(kind=2, nvec=nv[idx], l=vec(d["l"]), u=vec(d["u"]), x0=vec(d["x0"]),
+               delta0=d["delta0"][idx],
+               params=np.concatenate([d["params"][poff[i]:poff[i + 1]] for i in idx]))
+    r = oracle_solve(sub, n_list=sub["nvec"])
+    assert np.all(r["status"] == oracle.CONVERGED)
+    np.testing.assert_allclose(vec(xs), r["x"], rtol=0, atol=1e-6)
+    rel = np.abs(g["f"][idx] - r["f"]) / np.maximum(1.0, np.abs(r["f"]))
+    assert rel.max() <= 1e-8, rel.max()
