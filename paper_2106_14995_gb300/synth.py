@@ -94,10 +94,17 @@ def haar_orthogonal(rng: np.random.Generator, B: int, n: int) -> np.ndarray:
 
 
 def dense_records(rng: np.random.Generator, B: int, n: int, cond: float = 1e3,
-                  c_sd: float = 4.0, quartic: float = 0.1, diag_only: bool = False):
+                  c_sd: float = 4.0, quartic: float = 0.1, diag_only: bool = False,
+                  neg_frac: float = 0.0):
     """Q = U diag(lam) U' with U Haar, lam log-uniform in [1, cond]; c ~ N(0, c_sd^2);
-    d = quartic; l ~ U[-2, -0.5]; u ~ U[0.5, 2]; x0 = 0."""
+    d = quartic; l ~ U[-2, -0.5]; u ~ U[0.5, 2]; x0 = 0.  neg_frac > 0: that fraction of
+    each problem's eigenvalues (rounded up) is -U[0.5, 50] instead, an indefinite Q (the
+    box and the quartic keep f bounded; the Hessian's shifted factorization and the
+    PCG's negative-curvature exit come into play)."""
     lam = np.exp(rng.uniform(0.0, math.log(cond), (B, n)))
+    if neg_frac > 0.0:
+        k = int(math.ceil(neg_frac * n))
+        lam[:, :k] = -rng.uniform(0.5, 50.0, (B, k))
     if diag_only:
         Q = np.zeros((B, n, n))
         idx = np.arange(n)

@@ -659,3 +659,29 @@ def test_full_size_uneven_workload_sampled():
     np.testing.assert_allclose(vec(xs), r["x"], rtol=0, atol=1e-6)
     rel = np.abs(g["f"][idx] - r["f"]) / np.maximum(1.0, np.abs(r["f"]))
     assert rel.max() <= 1e-8, rel.max()
+
+
+@pytest.mark.parametrize("n,B", [(16, 300), (32, 300), (128, 40)])
+def test_dense_indefinite_shifted_factorization_and_negative_curvature(n, B):
+    # indefinite Q (a quarter of the eigenvalues in -[0.5, 50]): the factorization needs
+    # shifts and the PCG exits on negative curvature (the oracle's counters show both);
+    # several local minima can be correct, so every GPU result must be a KKT point by
+    # the oracle's own gradient, and where GPU and oracle took the same path (the same
+    # iteration count) they must agree as on convex problems
+    d = synth.dense_batch(B, n, seed_index=60 + n, neg_frac=0.25)
+    g = gpu_solve(d, n=n)
+    r = oracle_solve(d)
+    c = r["counters"]
+    assert c["chol_calls"] > c["subspace_passes"], c   # shift retries happened
+    assert c["cg_iters"] > 0, c
+    assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
+    assert np.all(r["status"] == oracle.CONVERGED)
+    assert np.all(g["x"] >= d["l"]) and np.all(g["x"] <= d["u"])
+    for p in range(B):
+        _, gr, _ = oracle.eval_obj(oracle.OBJ_DENSE, d["params"][p], g["x"][p])
+        assert oracle.pgnorm(g["x"][p], gr, d["l"][p], d["u"][p]) <= 1e-6 * 1.01
+    same = g["iters"] == r["iters"]
+    assert same.mean() >= 0.8, same.mean()
+    np.testing.assert_allclose(g["x"][same], r["x"][same], rtol=0, atol=1e-6)
+    rel = np.abs(g["f"][same] - r["f"][same]) / np.maximum(1.0, np.abs(r["f"][same]))
+    assert rel.max() <= 1e-8
