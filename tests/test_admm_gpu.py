@@ -359,3 +359,31 @@ def test_admm_edge_network_isolated_and_multi_generator_buses():
     # the isolated bus keeps its voltage (no branch copies to average)
     assert s["bus_w"][3] == 1.0 and s["bus_th"][3] == 0.0
     g.close()
+
+
+@pytest.mark.parametrize("group", [4, 1])
+def test_pool_instances_with_their_own_penalties_and_boxes(group):
+    # instances that differ in rho, the line penalty and the voltage box share every
+    # launch; each equals its own run alone bit for bit and follows the oracle's
+    # trajectory for its parameters
+    cases = [(small_net(40, 21), dict(rho=10.0, rho_line=10.0, vmin=0.9, vmax=1.1)),
+             (small_net(60, 22), dict(rho=400.0, rho_line=1000.0, vmin=0.95, vmax=1.05)),
+             (small_net(30, 23), dict(rho=1000.0, rho_line=200.0, vmin=0.85, vmax=1.15))]
+    K = 60
+    pool = AdmmPool(2000, 2000, 1000, 3, opts=options(group=group))
+    ids = [pool.add(net, **kw) for net, kw in cases]
+    pool.step(K)
+    for i, (net, kw) in zip(ids, cases):
+        st = pool.get_state(i)
+        hp, hd = pool.history(i, 0, K)
+        solo = AdmmPool(2000, 2000, 1000, 1, opts=options(group=group))
+        j = solo.add(net, **kw)
+        solo.step(K)
+        ref = solo.get_state(j)
+        for k in ref:
+            np.testing.assert_array_equal(st[k], ref[k], err_msg=k)
+        solo.close()
+        hp_o, hd_o = oracle.Admm(net, **kw).run(K, nthreads=4)
+        np.testing.assert_allclose(hp, hp_o, rtol=1e-6, atol=0)
+        np.testing.assert_allclose(hd, hd_o, rtol=1e-6, atol=0)
+    pool.close()
