@@ -144,3 +144,18 @@ def test_multiperiod_benchmark_size_tracks_oracle():
         np.testing.assert_allclose(g.get_state(t)["gen_pq"], o.state(t)["gen_pq"], rtol=1e-6,
                                    atol=1e-8)
     g.close()
+
+
+@pytest.mark.parametrize("T", [1, 32])
+def test_multiperiod_edge_period_counts_match_oracle(T):
+    # one period (the chains reduce to single generators) and the most periods a chain
+    # holds (32, one per lane of a warp)
+    net = _small_net(30, 53)
+    scale = synth.load_profile(T)
+    kw = dict(ramp=0.03, rho_ramp=1e4)
+    hp, hd = oracle.MultiPeriodAdmm(net, scale, **kw).run(12, nthreads=8)
+    g = AdmmMultiPeriod(net, scale, **kw)
+    res = np.array([g.step(1) for _ in range(12)])
+    np.testing.assert_allclose(res[:, 0], hp, rtol=1e-6)
+    np.testing.assert_allclose(res[:, 1], hd, rtol=1e-6)
+    g.close()
