@@ -155,7 +155,7 @@ tron_err_t admm_pool_get_state(admm_pool_t* p, int32_t id, admm_state_view_t* ho
 tron_err_t admm_pool_set_state(admm_pool_t* p, int32_t id, const admm_state_view_t* host,
                                void* stream);
 int32_t admm_pool_live(const admm_pool_t* p);
-/* Lanes per branch problem the pool's branch launch uses (1 or 4); 0 for NULL. */
+/* Lanes per branch problem the pool's branch launch uses (1, 2 or 4); 0 for NULL. */
 int32_t admm_pool_branch_group(const admm_pool_t* p);
 void admm_pool_destroy(admm_pool_t* p);
 

@@ -109,8 +109,8 @@ typedef struct tron_options {
   int32_t max_shift;      /* 30     shift retries before TRON_CHOL_FAIL                  */
   int32_t group;          /* 0      threads per problem: 0 = library's table, or
                                     1, 2, 4, 8, 16, 32 (must divide the size class); the
-                                    table's choice for the branch problems is 4 up to 40
-                                    problems per SM sub-partition, 1 beyond            */
+                                    table's choice for the branch problems is 4 up to 96
+                                    problems per SM sub-partition, 2 beyond            */
   double ared_guard;      /* 1e-13  rounding guard of the reduction ratio,
                                     rho = (ared + e) / (pred + e), e = ared_guard * max(1, S)
                                     with S the sum of the magnitudes of the terms of f */

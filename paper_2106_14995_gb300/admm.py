@@ -103,7 +103,7 @@ class Admm:
 
     @property
     def branch_group(self) -> int:
-        """Lanes per branch problem in the branch launch (1 or 4)."""
+        """Lanes per branch problem in the branch launch (1, 2 or 4)."""
         return int(self._lib.admm_pool_branch_group(self._h))
 
     @property
@@ -216,7 +216,7 @@ class AdmmPool:
 
     @property
     def branch_group(self) -> int:
-        """Lanes per branch problem in the branch launch (1 or 4)."""
+        """Lanes per branch problem in the branch launch (1, 2 or 4)."""
         return int(self._lib.admm_pool_branch_group(self._h))
 
     @property

@@ -193,6 +193,53 @@ __device__ __forceinline__ void branch_update(const PoolDev& d, const tron_optio
     d.br_delta[k] = delta;
     d.br_status[k] = st;
     d.br_iters[k] = it;
+  } else if constexpr (G == 2) {
+    // rank t: bus t of the branch, variables (v, theta) of that bus; it stages entries
+    // t, t + 2, t + 4, t + 6 of the coefficients, multipliers, penalties and targets
+    const int t = sv.gp.t;
+    sv.l[0] = vmin;
+    sv.u[0] = vmax;
+    sv.l[1] = -kTwoPi;
+    sv.u[1] = kTwoPi;
+    const int bus = t ? j : i;
+#pragma unroll
+    for (int q = t; q < 8; q += 2) {
+      const double c = d.br_coef[8 * (size_t)k + q];
+      const double l = d.br_lam[8 * (size_t)k + q];
+      fin = fin && finite_bits(c) && finite_bits(l);
+      sv.obj.rec[q] = c;
+      sv.obj.rec[8 + q] = l;
+      sv.obj.rec[24 + q] = rho;
+    }
+    // targets: flows t, t + 2 (branch-side copies), then w and theta of bus t
+    const double tg0 = d.br_tilde[4 * (size_t)k + t], tg1 = d.br_tilde[4 * (size_t)k + t + 2];
+    const double tgw = d.bus_w[bus], tgt = d.bus_th[bus];
+    fin = fin && finite_bits(tg0) && finite_bits(tg1) && finite_bits(tgw) && finite_bits(tgt);
+    sv.obj.rec[16 + t] = tg0;
+    sv.obj.rec[18 + t] = tg1;
+    sv.obj.rec[20 + t] = tgw;
+    sv.obj.rec[22 + t] = tgt;
+    if (t == 0) sv.obj.rec[32] = d.br_smax2[k];
+    if (t == 1) sv.obj.rec[33] = rhol;
+    sv.gp.sync();
+    sv.obj.prepare(t);
+    fin = !sv.gp.any(!fin);
+    double x[2] = {d.br_x[4 * (size_t)k + t], d.br_x[4 * (size_t)k + 2 + t]};
+    double delta = d.br_delta[k];
+    double f, pg;
+    int it;
+    const int st = sv.run(x, delta, f, pg, it, fin);
+    d.br_x[4 * (size_t)k + t] = x[0];
+    d.br_x[4 * (size_t)k + 2 + t] = x[1];
+    d.br_val[8 * (size_t)k + 2 * t] = sv.obj.Fx[0];
+    d.br_val[8 * (size_t)k + 2 * t + 1] = sv.obj.Fx[1];
+    d.br_val[8 * (size_t)k + 4 + t] = x[0] * x[0];
+    d.br_val[8 * (size_t)k + 6 + t] = x[1];
+    if (t == 0) {
+      d.br_delta[k] = delta;
+      d.br_status[k] = st;
+      d.br_iters[k] = it;
+    }
   } else {
     const int t = sv.gp.t;
     sv.l[0] = t < 2 ? vmin : -kTwoPi;
@@ -282,13 +329,15 @@ __global__ void __launch_bounds__(32) k_admm_branch_tail(const AdmmArgs a) {
     branch_update<4>(d, a.opt, smem, d.split_list[e], 0x7FFFFFFF, true);
 }
 
-// the branch kernel and its shared memory per warp for branch group size G (1 or 4)
+// the branch kernel and its shared memory per warp for branch group size G (1, 2 or 4)
 static const void* branch_kernel(int G) {
-  return G == 4 ? (const void*)k_admm_branch_gen<4> : (const void*)k_admm_branch_gen<1>;
+  return G == 4 ? (const void*)k_admm_branch_gen<4>
+                : (G == 2 ? (const void*)k_admm_branch_gen<2> : (const void*)k_admm_branch_gen<1>);
 }
 static size_t branch_warp_bytes(int G) {
   return sizeof(double) * (size_t)(G == 4 ? BranchSolver<4>::WARP_DOUBLES
-                                          : BranchSolver<1>::WARP_DOUBLES);
+                                          : (G == 2 ? BranchSolver<2>::WARP_DOUBLES
+                                                    : BranchSolver<1>::WARP_DOUBLES));
 }
 
 __global__ void __launch_bounds__(kBusThreads) k_admm_bus(const AdmmArgs a) {
@@ -627,7 +676,7 @@ struct admm_pool {
   tron_options_t opt;
   int nbb, ngb, nbusb;
   int bw;   // warps per branch CTA
-  int grp;  // lanes per branch problem (1 or 4)
+  int grp;  // lanes per branch problem (1, 2 or 4)
   int split;  // one-lane pools: TRON iterations before a solve moves to four lanes (0: never)
   int ntb;    // CTAs of k_admm_branch_tail
   RangeAlloc ab, al, ag;
@@ -726,8 +775,8 @@ tron_err_t admm_pool_create(admm_pool_t** out, int32_t cap_bus, int32_t cap_bran
   XT_REQUIRE(cap_bus >= 0 && cap_branch >= 0 && cap_gen >= 0 && cap_instances > 0 &&
                  history_len > 0,
              TRON_EINVAL, "admm_pool_create: bad capacities");
-  XT_REQUIRE(!opt || opt->group == 0 || opt->group == 1 || opt->group == 4, TRON_EINVAL,
-             "admm: options.group must be 0, 1 or 4");
+  XT_REQUIRE(!opt || opt->group == 0 || opt->group == 1 || opt->group == 2 || opt->group == 4,
+             TRON_EINVAL, "admm: options.group must be 0, 1, 2 or 4");
   XT_REQUIRE(!opt || opt->tr_norm == 0 || opt->tr_norm == 1, TRON_EINVAL,
              "admm: options.tr_norm must be 0 or 1");
   XT_REQUIRE(!opt || opt->cauchy_norm == 0 || opt->cauchy_norm == 1, TRON_EINVAL,

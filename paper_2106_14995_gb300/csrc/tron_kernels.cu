@@ -231,6 +231,7 @@ static std::vector<KernelEntry>& table() {
   static std::vector<KernelEntry> t = {
       make_entry<BranchObj<1>, 4, 1, false>(TRON_OBJ_ACOPF_BRANCH, 0),
       make_entry<BranchObj<4>, 4, 4, false>(TRON_OBJ_ACOPF_BRANCH, 0),
+      make_entry<BranchObj<2>, 4, 2, false>(TRON_OBJ_ACOPF_BRANCH, 0),
       make_entry<DenseObj<4, 4>, 4, 4, false>(TRON_OBJ_DENSE_QUARTIC, 0),
       make_entry<DenseObj<4, 1>, 4, 1, false>(TRON_OBJ_DENSE_QUARTIC, 0),
       make_entry<DenseObj<8, 8>, 8, 8, false>(TRON_OBJ_DENSE_QUARTIC, 0),
@@ -294,14 +295,17 @@ static KernelEntry* find_entry(int kind, int N, int G, int layout_opt = 0) {
 }
 // The default mapping of the branch problems follows the batch: four lanes per problem
 // while the class holds at most this many problems per SM sub-partition (the launch then
-// lasts as long as its slowest problem, whose serial chain four lanes shorten), one lane
-// per problem beyond (fewest FP64 instructions per problem).  Measured crossover of
-// cold-started branch batches: between 16,384 and 32,768 problems on 152 SMs.
-constexpr int64_t kG4BranchProblemsPerSmsp = 40;
+// lasts as long as its slowest problem, whose serial chain four lanes shorten), two
+// lanes beyond (half the instructions of four per problem, a chain still far shorter
+// than on one lane).  Cold-started branch batches on 152 SMs, ms with 1 / 2 / 4 lanes:
+// 32,768 problems 1.70 / 1.32 / 1.28, 49,152 2.41 / 1.82 / 1.75, 65,536 1.88 / 1.65 /
+// 1.67, 131,072 3.13 / 2.87 / 2.98, 262,144 5.63 / 5.23 / 5.65; one lane is the slowest
+// throughout (these solves take 5.5 TRON iterations on average, up to 29).
+constexpr int64_t kG4BranchProblemsPerSmsp = 96;
 
 static int default_group(int kind, int N, int64_t count, int sms) {
   if (kind == TRON_OBJ_ACOPF_BRANCH && N == 4)
-    return (sms > 0 && count > 0 && count <= kG4BranchProblemsPerSmsp * 4 * sms) ? 4 : 1;
+    return (sms > 0 && count > 0 && count <= kG4BranchProblemsPerSmsp * 4 * sms) ? 4 : 2;
   KernelEntry* e = find_entry(kind, N, 0);
   return e ? e->G : 1;
 }

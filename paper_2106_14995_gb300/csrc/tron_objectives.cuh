@@ -672,6 +672,233 @@ struct BranchObj<4> {
   }
 };
 
+// Two lanes per problem: rank t holds bus t's variables of the branch, x = (v, theta)
+// of bus i (t = 0) or bus j (t = 1) -- the solver's variables t and t + 2 -- and owns
+// the two flows of its end (p_ij, q_ij or p_ji, q_ji: both use its own w = v^2), its
+// line-limit direction, and the pair terms of those flows and of its w and theta.  The
+// sums over all four flows (the scalars CR, CI and the six distinct Gauss-Newton
+// entries) take one exchange between the two ranks; each rank writes the Hessian rows
+// of its two variables.
+template <>
+struct BranchObj<2> {
+  static constexpr int N = 4;
+  static constexpr int R = 2;
+  static constexpr int SMEM = 36 + 16;  // record, Hessian (row-major)
+  static constexpr bool kHasHd = false;
+  static constexpr bool kStepEval = false;
+
+  SV<2> rec, H;
+  double ca[2], cR[2], cI[2];  // flows 2t, 2t + 1 = ca w + cR wR + cI wI (w: own bus)
+  // at the point of the last eval_f; the first six are the same on both ranks
+  double vi, vj, sn, cs, wR, wI;
+  double F[2], rf[2], rw, rth;  // own flows; residuals of their pair terms, of w, theta
+  double mx;                    // p^2 + q^2 - smax^2 of the own direction
+  double Fx[2];                 // own flows at the point of the last grad_hess
+  double fsc;
+  int n;
+
+  __device__ __forceinline__ void bind(SV<2> base) {
+    rec = base;
+    H = base.at(36);
+  }
+
+  // coefficients of flow f (0..3) as for four lanes:
+  //   F0 = c0 w_i - c2 wR + c3 wI,  F1 = c1 w_i - c3 wR - c2 wI,
+  //   F2 = c4 w_j - c6 wR - c7 wI,  F3 = c5 w_j - c7 wR + c6 wI
+  __device__ __forceinline__ void prepare(int t) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int f = 2 * t + e;
+      ca[e] = rec[f < 2 ? f : f + 2];
+      cR[e] = -rec[f == 0 ? 2 : (f == 1 ? 3 : (f == 2 ? 6 : 7))];
+      const double c = rec[f == 0 ? 3 : (f == 1 ? 2 : (f == 2 ? 7 : 6))];
+      cI[e] = (f == 0 || f == 3) ? c : -c;
+    }
+  }
+
+  template <class GP>
+  __device__ __forceinline__ bool load(const GP& gp, const double* __restrict__ src, int n_) {
+    n = n_;
+    bool fin = true;
+    for (int k = gp.t; k < 34; k += 2) {
+      const double v = __ldg(src + k);
+      if (k < 32) fin = fin && finite_bits(v);  // smax^2, rho_line: only where a line is over
+      rec[k] = v;
+    }
+    gp.sync();
+    prepare(gp.t);
+    return !gp.any(!fin);
+  }
+
+  template <class GP>
+  __device__ __forceinline__ double eval_f(const GP& gp, const double (&y)[2]) {
+    const int t = gp.t;
+    const double vo = y[0], tho = y[1];
+    const double vp = gp.exch(vo, 1), thp = gp.exch(tho, 1);
+    vi = t == 0 ? vo : vp;
+    vj = t == 0 ? vp : vo;
+    const double thi = t == 0 ? tho : thp, thj = t == 0 ? thp : tho;
+    const double dth = thi - thj;
+    // rank 0 the sine, rank 1 the cosine of the angle difference (one stream)
+    const double sc = small_angle(dth) ? sin_cos_small(dth, t == 1)
+                                       : sin(t == 1 ? dth + 1.5707963267948966 : dth);
+    sn = gp.bcast(sc, 0);
+    cs = gp.bcast(sc, 1);
+    const double vv = vi * vj;
+    wR = vv * cs;
+    wI = vv * sn;
+    const double wo = vo * vo;
+    const double aR = fabs(wR), aI = fabs(wI);
+    double val = 0.0, mag = 0.0;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      F[e] = ca[e] * wo + cR[e] * wR + cI[e] * wI;
+      const double M = fabs(ca[e]) * wo + fabs(cR[e]) * aR + fabs(cI[e]) * aI;
+      const int k = 2 * t + e;
+      const double r = F[e] - rec[16 + k];
+      rf[e] = r;
+      const double l = rec[8 + k], p = rec[24 + k];
+      val += l * r + 0.5 * p * r * r;
+      mag += fabs(l * r) + 0.5 * p * r * r + (fabs(l) + p * fabs(r)) * M;
+    }
+    {  // pair terms of the own w (k = 4 + t) and theta (k = 6 + t)
+      rw = wo - rec[20 + t];
+      rth = tho - rec[22 + t];
+      const double lw = rec[12 + t], pw = rec[28 + t];
+      const double lt = rec[14 + t], pt = rec[30 + t];
+      val += lw * rw + 0.5 * pw * rw * rw;
+      mag += fabs(lw * rw) + 0.5 * pw * rw * rw + (fabs(lw) + pw * fabs(rw)) * wo;
+      val += lt * rth + 0.5 * pt * rth * rth;
+      mag += fabs(lt * rth) + 0.5 * pt * rth * rth + (fabs(lt) + pt * fabs(rth)) * fabs(tho);
+    }
+    // line limit of the own direction (both of its flows are this rank's)
+    const double p2q2 = F[0] * F[0] + F[1] * F[1];
+    const double smax2 = rec[32], rhol = rec[33];
+    mx = p2q2 - smax2;
+    if (positive_bits(mx)) {
+      val += 0.5 * rhol * mx * mx;
+      mag += 0.5 * rhol * mx * mx + rhol * mx * (p2q2 + smax2);
+    }
+    gp.sum2(val, mag);
+    fsc = mag;
+    return val;
+  }
+
+  // gradient and Hessian rows of the own variables at the point of the last eval_f
+  template <class GP>
+  __device__ __forceinline__ void grad_hess(const GP& gp, const double (&x)[2], double (&g)[2]) {
+    const int t = gp.t;
+    Fx[0] = F[0];
+    Fx[1] = F[1];
+    const double rhol = rec[33];
+    const bool act = positive_bits(mx);
+    const double h2 = act ? 2.0 * rhol * mx : 0.0;  // line term: 2 rho_l m on F and on W
+    const double vo = x[0];
+    // flows: first-order weights tw, Gauss-Newton weights W, derivative rows
+    // (d0, d1, d2) along (v_i, v_j, theta_i) (theta_j: -d2)
+    double CR = 0.0, CI = 0.0, ab = 0.0;
+    double e00 = 0.0, e01 = 0.0, e02 = 0.0, e11 = 0.0, e12 = 0.0, e22 = 0.0;
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;  // grad m / 2 of the own direction
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k = 2 * t + e;
+      double tw = rec[8 + k] + rec[24 + k] * rf[e];
+      double W = rec[24 + k];
+      if (act) {
+        tw += h2 * F[e];
+        W += h2;
+      }
+      const double h = cR[e] * cs + cI[e] * sn;
+      const double a2 = 2.0 * ca[e];
+      const double d0 = t == 0 ? fma(a2, vi, vj * h) : vj * h;
+      const double d1 = t == 0 ? vi * h : fma(a2, vj, vi * h);
+      const double d2 = cI[e] * wR - cR[e] * wI;
+      ab = fma(tw, ca[e], ab);
+      CR = fma(tw, cR[e], CR);
+      CI = fma(tw, cI[e], CI);
+      const double u0 = W * d0, u1 = W * d1, u2 = W * d2;
+      e00 = fma(d0, u0, e00);
+      e01 = fma(d0, u1, e01);
+      e02 = fma(d0, u2, e02);
+      e11 = fma(d1, u1, e11);
+      e12 = fma(d1, u2, e12);
+      e22 = fma(d2, u2, e22);
+      m0 = fma(F[e], d0, m0);
+      m1 = fma(F[e], d1, m1);
+      m2 = fma(F[e], d2, m2);
+    }
+    if (act) {  // rho_l grad m grad m', grad m = 2 (p dF_p + q dF_q)
+      const double q0 = 2.0 * m0, q1 = 2.0 * m1, q2 = 2.0 * m2;
+      const double r0 = rhol * q0, r1 = rhol * q1, r2 = rhol * q2;
+      e00 = fma(q0, r0, e00);
+      e01 = fma(q0, r1, e01);
+      e02 = fma(q0, r2, e02);
+      e11 = fma(q1, r1, e11);
+      e12 = fma(q1, r2, e12);
+      e22 = fma(q2, r2, e22);
+    }
+    const double tww = rec[12 + t] + rec[28 + t] * rw;  // weight of the own w term
+    const double twt = rec[14 + t] + rec[30 + t] * rth; // of the own theta term
+    ab += tww;  // Aw on rank 0, Bw on rank 1
+    // the other rank's flows
+    CR += gp.exch(CR, 1);
+    CI += gp.exch(CI, 1);
+    e00 += gp.exch(e00, 1);
+    e01 += gp.exch(e01, 1);
+    e02 += gp.exch(e02, 1);
+    e11 += gp.exch(e11, 1);
+    e12 += gp.exch(e12, 1);
+    e22 += gp.exch(e22, 1);
+    // gradient: g_v = 2 v ab + CR dwR/dv + CI dwI/dv (dwR/dv_i = v_j cs, dwI/dv_i =
+    // v_j sn, and i <-> j), g_theta = tw_theta + CR dwR/dtheta + CI dwI/dtheta
+    // (dwR/dtheta_i = -wI, dwI/dtheta_i = wR; theta_j: the opposite)
+    const double vq = t == 0 ? vj : vi;
+    const double x2 = 2.0 * vo;
+    g[0] = x2 * ab + CR * (vq * cs) + CI * (vq * sn);
+    const double dRt = t == 0 ? -wI : wI, dIt = t == 0 ? wR : -wR;
+    g[1] = twt + CR * dRt + CI * dIt;
+    // second derivatives of w_i, w_j, wR, wI times the aggregates (as for four lanes)
+    const double q01 = CR * cs + CI * sn;
+    const double gm = CI * cs - CR * sn;
+    const double aj = vj * gm, ai = vi * gm;
+    const double bb = CR * wR + CI * wI;
+    const double sdv = 2.0 * ab + rec[28 + t] * (x2 * x2);
+    const double sdt = -bb + rec[30 + t];
+    // row of v_own (variable t) and of theta_own (variable t + 2)
+    double rv[4], rt[4];
+    if (t == 0) {
+      rv[0] = e00 + sdv; rv[1] = e01 + q01; rv[2] = e02 + aj; rv[3] = -e02 - aj;
+      rt[0] = e02 + aj;  rt[1] = e12 + ai;  rt[2] = e22 + sdt; rt[3] = -e22 + bb;
+    } else {
+      rv[0] = e01 + q01; rv[1] = e11 + sdv; rv[2] = e12 + ai; rv[3] = -e12 - ai;
+      rt[0] = -e02 - aj; rt[1] = -e12 - ai; rt[2] = -e22 + bb; rt[3] = e22 + sdt;
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      H[4 * t + b] = rv[b];
+      H[4 * (t + 2) + b] = rt[b];
+    }
+    gp.sync();
+  }
+
+  __device__ __forceinline__ double hq(int i, int j) const { return H[4 * i + j]; }
+  __device__ __forceinline__ double hd(int) const { return 0.0; }
+  __device__ __forceinline__ double row_dot(int i, SV<2> v) const {
+    double s = H[4 * i] * v[0];
+    s = fma(H[4 * i + 1], v[1], s);
+    s = fma(H[4 * i + 2], v[2], s);
+    return fma(H[4 * i + 3], v[3], s);
+  }
+  template <class GP>
+  __device__ __forceinline__ bool hess_finite(const GP& gp) const {
+    const int t = gp.t;
+    bool fin = true;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) fin = fin && finite_bits(H[4 * t + b]) && finite_bits(H[4 * (t + 2) + b]);
+    return !gp.any(!fin);
+  }
+};
+
 // --------------------------------------------- multi-period generator (n <= 32 periods)
 // The generator component of the multi-period ADMM: its active power over the periods,
 // f = sum_t c2 p_t^2 + c1 p_t + lambda_t (p_t - target_t) + rho/2 (p_t - target_t)^2

@@ -75,8 +75,8 @@ def test_argument_errors_are_codes(lib):
     rc = L.tron_batch_create(C.byref(h), 2, 10, None, 32, C.byref(o), None)
     assert rc == 1
     assert L.tron_options_default(None) == 1
-    # the ADMM branch launch takes one or four lanes per branch problem
-    o.group = 2
+    # the ADMM branch launch takes one, two or four lanes per branch problem
+    o.group = 3
     rc = L.admm_pool_create(C.byref(h), 10, 10, 10, 1, 16, C.byref(o), None)
     assert rc == 1
     assert b"group" in L.tron_last_error()

@@ -17,7 +17,7 @@ def small_net(nb, seed):
                          rng=np.random.default_rng(seed))
 
 
-@pytest.mark.parametrize("group", [1, 4])
+@pytest.mark.parametrize("group", [1, 2, 4])
 def test_admm_residual_trajectory_matches_oracle(group):
     # group: lanes per branch problem in the branch launch (4 is the default)
     net = small_net(60, 3)
@@ -38,7 +38,7 @@ def test_admm_residual_trajectory_matches_oracle(group):
     g.close()
 
 
-@pytest.mark.parametrize("group", [1, 4])
+@pytest.mark.parametrize("group", [1, 2, 4])
 @pytest.mark.parametrize("nb,seed,K", [(120, 11, 600), (200, 12, 400)])
 def test_admm_long_trajectory_matches_oracle(group, nb, seed, K):
     # past the start-up: the branch solves that need the most TRON iterations (and the
@@ -233,7 +233,7 @@ def _alone(net, iters, group=0):
     return st, hist
 
 
-@pytest.mark.parametrize("group", [4, 1])
+@pytest.mark.parametrize("group", [4, 2, 1])
 def test_pool_results_identical_alone_and_in_the_mix(group):
     # both branch mappings: an instance's results do not depend on its co-residents
     nets = [small_net(40, 11), small_net(130, 12), small_net(25, 13), small_net(70, 14)]
@@ -361,7 +361,7 @@ def test_admm_edge_network_isolated_and_multi_generator_buses():
     g.close()
 
 
-@pytest.mark.parametrize("group", [4, 1])
+@pytest.mark.parametrize("group", [4, 2, 1])
 def test_pool_instances_with_their_own_penalties_and_boxes(group):
     # instances that differ in rho, the line penalty and the voltage box share every
     # launch; each equals its own run alone bit for bit and follows the oracle's

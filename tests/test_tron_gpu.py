@@ -118,7 +118,7 @@ def _branch_kkt(rec, x, l, u):
     return oracle.pgnorm(x, gr, l, u)
 
 
-@pytest.mark.parametrize("B,group", [(256, 1), (256, 4), (301, 4)])
+@pytest.mark.parametrize("B,group", [(256, 1), (256, 2), (256, 4), (301, 2), (301, 4)])
 def test_branch_parity(B, group):
     # group 1: one branch per lane; group 4: one per four lanes (301: a ragged last warp)
     d = synth.branch_batch(B, seed_index=0)
@@ -182,11 +182,11 @@ def test_hessian_norm_cauchy_option_matches_oracle():
 
 
 def test_branch_default_group_follows_batch_size():
-    # the library's mapping of the branch problems: four lanes per problem up to 40
-    # problems per SM sub-partition, one lane beyond; an explicit group wins
+    # the library's mapping of the branch problems: four lanes per problem up to 96
+    # problems per SM sub-partition, two lanes beyond; an explicit group wins
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    lim = 40 * 4 * nsm
-    for B, want in ((256, 4), (lim, 4), (lim + 1, 1)):
+    lim = 96 * 4 * nsm
+    for B, want in ((256, 4), (lim, 4), (lim + 1, 2)):
         tb = TronBatch(native.TRON_OBJ_ACOPF_BRANCH, B, n=4)
         assert tb.choices()[0]["group"] == want, (B, tb.choices())
         tb.close()
