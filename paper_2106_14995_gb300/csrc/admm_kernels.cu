@@ -4,7 +4,7 @@
 // One iteration = two launches, both over the pool's whole capacity:
 //   k_admm_branch_gen : generator updates (closed form) alongside the branch updates
 //                       (the branch NLP of eq. exp-branch solved by the TRON solver of
-//                       tron_solver.cuh, four lanes or one lane per branch, warm
+//                       tron_solver.cuh, one, two or four lanes per branch, warm
 //                       started; the branch record is gathered on the fly from the
 //                       multipliers and the bus copies, the pair values at the new
 //                       point are written back)
