@@ -51,9 +51,9 @@ def hbm_peak_gbs():
 # problems, scaled per problem to the launch), valid only for the kernel sources it was
 # taken on: DRAM bytes (19.08 MB per 2,000 problems) and the FP64 flops the kernel
 # executes (thread-level DFMA x 2 + DADD + DMUL: 301.2 Mflop per 2,000 problems).
-TRAFFIC_BYTES_PER_PROBLEM = 19.082496e6 / 2000
+TRAFFIC_BYTES_PER_PROBLEM = 19.08224e6 / 2000
 EXEC_FLOPS_PER_PROBLEM = (2 * 128374664 + 25437882 + 19049401) / 2000
-TRAFFIC_SOURCES_SHA1 = "1f9c8990b2b6adcb826e89d16971581dc1ae6330"
+TRAFFIC_SOURCES_SHA1 = "8e6fa49cc7411b1a5bc59df4c7610f5843bd5ba9"
 TRAFFIC_SOURCES = ("tron_common.cuh", "tron_objectives.cuh", "tron_solver.cuh")
 
 
