@@ -197,20 +197,23 @@ def test_branch_default_group_follows_batch_size():
 
 def test_branch_groups_agree_with_line_limits_active():
     # tight line limits so the penalty of eq. exp-branch is active on many branches: the
-    # four-lane evaluator (reduce-scatter of the Gauss-Newton terms) and the one-lane one
-    # reach the same points, and both are KKT points by the oracle's gradient
+    # four-lane evaluator (reduce-scatter of the Gauss-Newton terms), the two-lane one
+    # (each lane its own direction's limit) and the one-lane one reach the same points,
+    # and all are KKT points by the oracle's gradient
     d = synth.branch_batch(200, seed_index=83)
     d["params"] = d["params"].copy()
     d["params"][:, 32] *= 0.05
     a = gpu_solve(d, n=4, group=1)
     b = gpu_solve(d, n=4, group=4)
+    c = gpu_solve(d, n=4, group=2)
     r = oracle_solve(d)
-    for g in (a, b):
+    for g in (a, b, c):
         assert np.all(g["status"] == native.TRON_CONVERGED), np.bincount(g["status"])
         for p in range(200):
             assert _branch_kkt(d["params"][p], g["x"][p], d["l"][p], d["u"][p]) <= 1e-6 * 1.01
-    same = np.all(np.abs(a["x"] - b["x"]) <= 1e-6, axis=1)
-    assert same.mean() >= 0.98
+    for g in (a, c):
+        same = np.all(np.abs(g["x"] - b["x"]) <= 1e-6, axis=1)
+        assert same.mean() >= 0.98
     same_r = np.all(np.abs(b["x"] - r["x"]) <= 1e-6, axis=1)
     assert same_r.mean() >= 0.98
 
@@ -387,7 +390,7 @@ def test_edge_cases_status_codes():
     assert np.all(g["iters"][[0, 3, 4]] == 1)
 
 
-@pytest.mark.parametrize("group", [1, 4])
+@pytest.mark.parametrize("group", [1, 2, 4])
 def test_branch_edge_cases_status_codes(group):
     # the branch evaluator on one and four lanes: l > u, a non-finite record, x0 outside
     # the box, an automatic initial radius; status codes as the oracle's, converged
