@@ -145,6 +145,9 @@ def parse():
     ap.add_argument("--serve-cap-seconds", type=float, default=1.0 / 3.0,
                     help="the pool holds the buses, branches and generators offered in this "
                          "many seconds of arrivals (at least the largest instance)")
+    ap.add_argument("--op-latency", action="store_true",
+                    help="print the cycles per dependent FP64 / integer operation (1 and 32 "
+                         "active lanes) as one JSON line instead of the benchmark")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="arrivals per second")
     ap.add_argument("--serve-sets", default="stated,convergent",
                     help="request sets to serve: stated, convergent")
@@ -792,6 +795,14 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+
+    if args.op_latency:
+        from paper_2106_14995_gb300.tron import OP_LATENCY_NAMES, op_latency
+        table = {name: {"lanes_1": round(op_latency(k, 1), 1), "lanes_32": round(op_latency(k, 32), 1)}
+                 for k, name in enumerate(OP_LATENCY_NAMES)}
+        print(json.dumps({"metric": "SM cycles per dependent operation (chain of 2048, one CTA)",
+                          "ops": table}))
+        return 0
 
     import torch
     import torch.distributed as dist

@@ -293,6 +293,20 @@ const char* tron_last_error(void);
 /* Library version string. */
 const char* tron_version(void);
 
+/* Measurement hook (the paper has no counterpart): the cost of one kind of dependent
+ * operation.  One CTA of `lanes` threads (1..1024) runs a chain of
+ * tron_bench_op_chain() operations, each on the previous result, between two clock64
+ * reads; d_cycles[0] (caller-owned device int64) receives the SM cycles of the chain.
+ * op: 0 FP64 fma, 1 FP64 add, 2 FP64 max, 3 FP64 compare and select, 4 int64 compare
+ * and select, 5 the solver's quotient, 6 IEEE division, 7 the solver's square root,
+ * 8 IEEE sqrt, 9 the library's sin, 10 the branch objective's sine series, 11 the
+ * hardware reciprocal estimate, 12 a 64-bit shuffle, 13 the library's cos, 14 its sincos,
+ * 15 an FP32 fma.  Enqueued on `stream`; TRON_EINVAL
+ * for another op, a lane count out of range or a NULL d_cycles. */
+tron_err_t tron_bench_op_latency(int32_t op, int32_t lanes, int64_t* d_cycles, void* stream);
+/* Length of the chain tron_bench_op_latency times (2,048). */
+int32_t tron_bench_op_chain(void);
+
 /* Test hook of the factorization's pivot reciprocal (Sec. 4.3's factorization, computed
  * here square-root free as Lu D Lu^T with one reciprocal per pivot): d_out[i] = the
  * reciprocal of d_a[i] as the factorization forms it -- the hardware estimate refined by

@@ -399,6 +399,71 @@ __global__ void k_fp64_fma(double* out, int64_t iters) {
   for (int k = 0; k < 8; ++k) s += v[k];
   out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// Dependent-operation cost: one CTA of `lanes` threads runs a chain of kOpChain
+// operations of one kind, each on the previous result, between two clock64 reads;
+// thread 0 writes the cycles.  The operands stay finite and in the fast ranges of the
+// solver's own quotient, square root and sine.
+constexpr int kOpChain = 2048;
+template <int OP>
+__global__ void k_op_latency(long long* cyc) {
+  double v = 0.5 + 1e-3 * (double)threadIdx.x;
+  const double a = 0.9999999, b = 1e-7;
+  long long x = __double_as_longlong(v), xb = __double_as_longlong(b);
+  float fv = (float)v;
+  __syncwarp(__activemask());
+  const long long t0 = clock64();
+#pragma unroll 16
+  for (int i = 0; i < kOpChain; ++i) {
+    if (OP == 0) v = fma(v, a, b);
+    if (OP == 1) asm volatile("add.f64 %0, %0, %1;" : "+d"(v) : "d"(b));
+    if (OP == 2) asm volatile("max.f64 %0, %0, %1;" : "+d"(v) : "d"(b));
+    if (OP == 3)
+      asm volatile("{ .reg .pred p; setp.gt.f64 p, %0, %1; selp.f64 %0, %1, %0, p; }"
+                   : "+d"(v) : "d"(b));
+    if (OP == 4)
+      asm volatile("{ .reg .pred p; setp.gt.s64 p, %0, %1; selp.b64 %0, %1, %0, p; }"
+                   : "+l"(x) : "l"(xb));
+    if (OP == 5) v = quotient(a, v);
+    if (OP == 6) v = a / v;
+    if (OP == 7) v = square_root(v);
+    if (OP == 8) v = sqrt(v);
+    if (OP == 9) v = sin(v);
+    if (OP == 10) v = sin_cos_small(v, false);
+    if (OP == 11) asm volatile("rcp.approx.ftz.f64 %0, %0;" : "+d"(v));
+    if (OP == 12) x = __shfl_sync(__activemask(), x, threadIdx.x ^ (blockDim.x > 1 ? 1 : 0));
+    if (OP == 13) v = cos(v);
+    if (OP == 14) {
+      double sn, cs;
+      sincos(v, &sn, &cs);
+      v = fma(cs, 1e-3, sn);
+    }
+    if (OP == 15) fv = fmaf(fv, 0.9999999f, 1e-7f);
+  }
+  const long long t1 = clock64();
+  if (threadIdx.x == 0)
+    cyc[0] = (t1 - t0) + (long long)(v == 12345.0) + (x == 12345 ? 1 : 0) + (fv == 12345.0f ? 1 : 0);
+}
+static const void* op_latency_kernel(int op) {
+  switch (op) {
+    case 0: return (const void*)k_op_latency<0>;
+    case 1: return (const void*)k_op_latency<1>;
+    case 2: return (const void*)k_op_latency<2>;
+    case 3: return (const void*)k_op_latency<3>;
+    case 4: return (const void*)k_op_latency<4>;
+    case 5: return (const void*)k_op_latency<5>;
+    case 6: return (const void*)k_op_latency<6>;
+    case 7: return (const void*)k_op_latency<7>;
+    case 8: return (const void*)k_op_latency<8>;
+    case 9: return (const void*)k_op_latency<9>;
+    case 10: return (const void*)k_op_latency<10>;
+    case 11: return (const void*)k_op_latency<11>;
+    case 12: return (const void*)k_op_latency<12>;
+    case 13: return (const void*)k_op_latency<13>;
+    case 14: return (const void*)k_op_latency<14>;
+    case 15: return (const void*)k_op_latency<15>;
+    default: return nullptr;
+  }
+}
 }  // namespace xt
 
 static tron_err_t check_options(const tron_options_t* o) {
@@ -436,6 +501,20 @@ tron_err_t tron_bench_fp64_fma(double* d_out, int32_t blocks, int32_t threads, i
   XT_CUDA(cudaGetLastError());
   return TRON_OK;
 }
+
+tron_err_t tron_bench_op_latency(int32_t op, int32_t lanes, int64_t* d_cycles, void* stream) {
+  clear_error();
+  XT_REQUIRE(d_cycles != nullptr, TRON_EINVAL, "tron_bench_op_latency: d_cycles is NULL");
+  XT_REQUIRE(lanes >= 1 && lanes <= 1024, TRON_EINVAL, "tron_bench_op_latency: lanes not in [1, 1024]");
+  const void* fn = xt::op_latency_kernel(op);
+  XT_REQUIRE(fn != nullptr, TRON_EINVAL, "tron_bench_op_latency: op not in [0, 15]");
+  long long* cyc = reinterpret_cast<long long*>(d_cycles);
+  void* args[] = {&cyc};
+  XT_CUDA(cudaLaunchKernel(fn, dim3(1), dim3((unsigned)lanes), args, 0, (cudaStream_t)stream));
+  return TRON_OK;
+}
+
+int32_t tron_bench_op_chain(void) { return xt::kOpChain; }
 
 tron_err_t tron_test_pivot_rcp(const double* d_a, double* d_out, int64_t n, void* stream) {
   clear_error();

@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
             "tron_test_pivot_rcp": (I32, [P, P, I64, P]),
             "tron_test_arith": (I32, [I32, P, P, P, I64, P]),
             "tron_bench_fp64_fma": (I32, [P, I32, I32, I64, P]),
+            "tron_bench_op_latency": (I32, [I32, I32, P, P]),
+            "tron_bench_op_chain": (I32, []),
             "admm_create": (I32, [C.POINTER(P), C.POINTER(AdmmNetwork), C.POINTER(TronOptions),
                                   P]),
             "admm_step": (I32, [P, I32, P, P, P]),

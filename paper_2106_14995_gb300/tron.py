@@ -128,3 +128,21 @@ class TronBatch:
             self.close()
         except Exception:
             pass
+
+
+OP_LATENCY_NAMES = ("fp64 fma", "fp64 add", "fp64 max", "fp64 compare+select",
+                    "int64 compare+select", "solver quotient", "ieee division",
+                    "solver square root", "ieee sqrt", "library sin", "sine series",
+                    "reciprocal estimate", "64-bit shuffle", "library cos", "library sincos",
+                    "fp32 fma")
+
+
+def op_latency(op: int, lanes: int = 32, stream=None) -> float:
+    """SM cycles per dependent operation of kind ``op`` (see OP_LATENCY_NAMES) with
+    ``lanes`` active threads in one CTA (tron_bench_op_latency)."""
+    lib = nt.load()
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nt.check(lib.tron_bench_op_latency(int(op), int(lanes), out.data_ptr(),
+                                       nt.stream_handle(stream)), "tron_bench_op_latency")
+    torch.cuda.synchronize()
+    return float(out.item()) / float(lib.tron_bench_op_chain())

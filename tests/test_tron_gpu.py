@@ -688,3 +688,16 @@ def test_dense_indefinite_shifted_factorization_and_negative_curvature(n, B):
     np.testing.assert_allclose(g["x"][same], r["x"][same], rtol=0, atol=1e-6)
     rel = np.abs(g["f"][same] - r["f"][same]) / np.maximum(1.0, np.abs(r["f"][same]))
     assert rel.max() <= 1e-8
+
+
+def test_operation_costs_behind_the_design():
+    # the measured facts the solver is built on: a dependent FP64 instruction costs the
+    # same with 1 or 32 active lanes; FP64 compare-and-select costs more than an FP64 FMA
+    # and far more than the int64 one the solver uses instead; the solver's quotient,
+    # square root and sine series are shorter chains than the library's operations
+    from paper_2106_14995_gb300.tron import op_latency
+    c = {k: op_latency(k, 32) for k in range(13)}
+    one = op_latency(0, 1)
+    assert abs(one - c[0]) <= 0.1 * c[0], (one, c[0])
+    assert c[3] > c[0] and c[4] < 0.5 * c[3], c
+    assert c[5] < c[6] and c[7] < c[8] and c[10] < c[9], c
