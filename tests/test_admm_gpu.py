@@ -222,9 +222,9 @@ def test_admm_checkpoint_resume_is_bitwise():
     g2.close()
 
 
-def _alone(net, iters, group=0):
+def _alone(net, iters, group=0, split=0):
     p = AdmmPool(len(net["bus_pd"]) + 256, len(net["br_from"]) + 256,
-                 len(net["gen_bus"]) + 256, 1, opts=options(group=group))
+                 len(net["gen_bus"]) + 256, 1, opts=options(group=group, split_outer=split))
     i = p.add(net)
     p.step(iters)
     st = p.get_state(i)
@@ -233,12 +233,15 @@ def _alone(net, iters, group=0):
     return st, hist
 
 
-@pytest.mark.parametrize("group", [4, 2, 1])
-def test_pool_results_identical_alone_and_in_the_mix(group):
-    # both branch mappings: an instance's results do not depend on its co-residents
+@pytest.mark.parametrize("group,split", [(4, 0), (2, 0), (1, 0), (1, 1)])
+def test_pool_results_identical_alone_and_in_the_mix(group, split):
+    # every branch mapping: an instance's results do not depend on its co-residents --
+    # with split 1 also when nearly every solve is finished by the tail launch, whose
+    # list of paused solves is filled in whatever order their warps reach it
     nets = [small_net(40, 11), small_net(130, 12), small_net(25, 13), small_net(70, 14)]
-    pool = AdmmPool(4000, 4000, 2000, 4, opts=options(group=group))
+    pool = AdmmPool(4000, 4000, 2000, 4, opts=options(group=group, split_outer=split))
     assert pool.branch_group == group
+    assert pool.launches_per_iteration == (3 if split > 0 else 2)
     a = pool.add(nets[0])
     pool.step(5)
     b = pool.add(nets[1])          # admitted while a is running
@@ -254,7 +257,7 @@ def test_pool_results_identical_alone_and_in_the_mix(group):
     sa2, sd = pool.get_state(a), pool.get_state(d)
     for net, st, iters in ((nets[0], sa, 17), (nets[1], sb, 12), (nets[2], sc, 9),
                            (nets[0], sa2, 21), (nets[3], sd, 4)):
-        ref, _ = _alone(net, iters, group)
+        ref, _ = _alone(net, iters, group, split)
         for k in ref:
             np.testing.assert_array_equal(st[k], ref[k], err_msg=k)
     assert pool.live == 3
