@@ -59,6 +59,7 @@ struct PoolDev {
   double* br_alpc;          // Cauchy step of a solve paused after the one-lane launch
   int32_t* split_list;      // slots of the paused solves, in no particular order
   unsigned int* split_cnt;  // their number (reset by the bus kernel)
+  const int32_t* br_order;  // slot solved by each lane of the branch launch (null: slot order)
   // generator slots
   int32_t* gen_bus;
   int32_t* gen_inst;
@@ -292,8 +293,12 @@ __global__ void __launch_bounds__(256) k_admm_branch_gen(const AdmmArgs a) {
   if ((int)blockIdx.x < a.nbb) {
     extern __shared__ double smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = ((int)blockIdx.x * (int)(blockDim.x >> 5) + warp) * (32 / G) + lane / G;
+    int k = ((int)blockIdx.x * (int)(blockDim.x >> 5) + warp) * (32 / G) + lane / G;
     if (k >= d.cap_br) return;
+    if (d.br_order) {
+      k = d.br_order[k];
+      if (k < 0) return;
+    }
     branch_update<G>(d, a.opt, smem + (size_t)warp * BranchSolver<G>::WARP_DOUBLES, k,
                      G == 1 ? a.pause_at : 0x7FFFFFFF, false);
   } else {
@@ -1340,6 +1345,22 @@ tron_err_t admm_mp_create(admm_mp_t** out, const admm_network_t* net, int32_t T,
     mp->allocs.push_back(*ptr);
     return true;
   };
+  // launch order of the branch slots: the T period copies of each line side by side, so
+  // that a warp's lanes hold the same line under neighbouring loads -- problems that take
+  // nearly the same path through the solver, which the warp then runs together (each
+  // problem's arithmetic, so its bits, do not depend on its lane)
+  {
+    const int cap = mp->pool->d.cap_br, nl = net->nbranch;
+    std::vector<int32_t> ord(cap, -1);
+    for (int r = 0; r < T * nl; ++r) ord[r] = mp->pool->inst[mp->inst[r % T]].l0 + r / T;
+    int32_t* d_ord = nullptr;
+    if (!alloc((void**)&d_ord, 4 * (size_t)cap) ||
+        cudaMemcpy(d_ord, ord.data(), 4 * (size_t)cap, cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("admm_mp_create: order upload failed");
+      return fail(TRON_ECUDA);
+    }
+    mp->pool->d.br_order = d_ord;
+  }
   if (!alloc((void**)&mp->d_g0, 4 * (size_t)T) || !alloc((void**)&mp->d_rec, 8 * rs * ngs) ||
       !alloc((void**)&mp->d_lo, 8 * (size_t)T * ngs) || !alloc((void**)&mp->d_hi, 8 * (size_t)T * ngs) ||
       !alloc((void**)&mp->d_x, 8 * (size_t)T * ngs) || !alloc((void**)&mp->d_delta, 8 * ngs) ||
