@@ -119,6 +119,26 @@ def test_multiperiod_without_binding_ramps_equals_single_period_runs():
     g.close()
 
 
+def test_zero_ramp_penalty_gives_independent_scenarios():
+    # independent load scenarios of one network as one multi-period instance: with
+    # rho_ramp = 0 each generator chain falls apart into its periods' own problems, so the
+    # scenarios equal separate single-period runs -- here with ramp limits that a penalty
+    # would make bind, and load factors drawn as the serving requests' are
+    net = _small_net(60, 53)
+    scale = np.random.default_rng(54).uniform(0.8, 1.2, 8)
+    g = AdmmMultiPeriod(net, scale, ramp=0.01, rho_ramp=0.0)
+    g.step(10)
+    for t, s in enumerate(scale):
+        a = Admm(dict(net, bus_pd=net["bus_pd"] * s, bus_qd=net["bus_qd"] * s))
+        a.step(10)
+        ref = a.get_state()
+        got = g.get_state(t)
+        for k in ("gen_pq", "gen_lam", "bus_w", "br_x", "br_lam"):
+            np.testing.assert_allclose(got[k], ref[k], rtol=1e-9, atol=1e-9, err_msg=k)
+        a.close()
+    g.close()
+
+
 def test_multiperiod_rejects_bad_arguments():
     net = _small_net(20, 52)
     with pytest.raises(native.TronError, match="EINVAL"):
