@@ -170,9 +170,14 @@ void admm_pool_destroy(admm_pool_t* p);
  * TRON launch over all generators, warm started), its reactive powers in closed form;
  * branches and buses are the single-period components of each period (the periods
  * live as instances of one resident pool and share its launches).  Residuals combine
- * all periods: primal sqrt(sum_t primal_t^2), dual sqrt(sum_t dual_t^2).
+ * all periods: primal sqrt(sum_t primal_t^2), dual sqrt(sum_t dual_t^2).  With
+ * rho_ramp = 0 the periods are independent load scenarios of the network (each
+ * generator's T outputs are then T separate problems).  The branch launch takes each
+ * line's T period copies side by side, so the lanes of a warp solve one line under
+ * neighbouring loads.
  *
- * admm_mp_create: copies the network and allocates everything (T <= 32, loads > 0).
+ * admm_mp_create: copies the network and allocates everything (T <= 32, loads > 0,
+ *   rho_ramp >= 0, h_ramp[g] >= 0; TRON_EINVAL otherwise).
  * admm_mp_step: runs n_iters iterations (five launches each); when h_primal / h_dual
  *   are not NULL, synchronises and writes the last iteration's combined residuals.
  * admm_mp_get_state: state of one period, as admm_get_state.
