@@ -1354,8 +1354,11 @@ tron_err_t admm_mp_create(admm_mp_t** out, const admm_network_t* net, int32_t T,
     std::vector<int32_t> ord(cap, -1);
     for (int r = 0; r < T * nl; ++r) ord[r] = mp->pool->inst[mp->inst[r % T]].l0 + r / T;
     int32_t* d_ord = nullptr;
-    if (!alloc((void**)&d_ord, 4 * (size_t)cap) ||
-        cudaMemcpy(d_ord, ord.data(), 4 * (size_t)cap, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (!alloc((void**)&d_ord, 4 * (size_t)cap)) {
+      set_error("admm_mp_create: cudaMalloc failed");
+      return fail(TRON_ENOMEM);
+    }
+    if (cudaMemcpy(d_ord, ord.data(), 4 * (size_t)cap, cudaMemcpyHostToDevice) != cudaSuccess) {
       set_error("admm_mp_create: order upload failed");
       return fail(TRON_ECUDA);
     }
